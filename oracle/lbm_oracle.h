@@ -1,0 +1,129 @@
+/*
+ * lbm_oracle.h -- plain FP64 CPU oracle of the lattice Boltzmann hot path
+ * analysed in arXiv 2512.12213 (Li, "Shear Stress and Fluid-Wall Interaction
+ * Force in LBM Simulations of Hydrodynamic and MHD Flows").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code exists to check the CUDA library
+ * against the paper.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load it.  It shares no source, header,
+ * table or helper with the CUDA library under paper_2512_12213_gb300/.
+ *
+ * Everything is double precision, single threaded, node by node, in the order
+ * the paper states the algorithm (collide every node, then propagate).
+ *
+ * Data layout (an interchange format shared with the library's canonical
+ * export, written independently on each side):
+ *   populations f[a][z][y][x], index a*N + (z*ny + y)*nx + x, N = nx*ny*nz;
+ *   per-node scalars s[(z*ny + y)*nx + x]; per-node vectors v[k*N + node].
+ * Velocity ordering:
+ *   D2Q9 : 0 (0,0) 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1) 5 (1,1) 6 (-1,1) 7 (-1,-1) 8 (1,-1)
+ *   D3Q19: 0 rest, 1/2 +-x, 3/4 +-y, 5/6 +-z, 7/8 +-(1,1,0), 9/10 +-(1,-1,0),
+ *          11/12 +-(1,0,1), 13/14 +-(1,0,-1), 15/16 +-(0,1,1), 17/18 +-(0,1,-1)
+ * Geometry: wall_id[node] = 0 for fluid, k > 0 for a solid node of wall k.
+ * A non-periodic axis is closed by a halfway bounce-back wall outside the box
+ * on each of its two faces, whose wall id is face_wall[2*axis + (0 low|1 high)].
+ */
+#ifndef LBM_ORACLE_H
+#define LBM_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_MAX_WALLS 16
+
+/* force models of Sec. 2: [a] He, [b] Martys/Luo, [c] Shan-Chen (reformulated),
+ * [d] exact difference method (reformulated), [e] Guo */
+enum { ORC_FORCE_A = 0, ORC_FORCE_B = 1, ORC_FORCE_C = 2, ORC_FORCE_D = 3, ORC_FORCE_E = 4 };
+
+/* stress variants: 1 = from f^neq with the artefact term E_ij (Eq. 9),
+ * 2 = without it (the simplification after Eq. 23), 3 = from the half-step
+ * distribution (Eqs. 27-28), 4 = variant 3 plus Theta_ij/2 (Eq. 30) */
+enum { ORC_S1 = 1, ORC_S2 = 2, ORC_S3 = 3, ORC_S4 = 4 };
+
+/* wall-force corrections of Sec. 5 */
+enum { ORC_MOVING_CORR = 1, ORC_MAXWELL_REMOVE = 2 };
+
+typedef struct orc_cfg {
+    int q;                 /* 9 (D2Q9) or 19 (D3Q19) */
+    int nx, ny, nz;        /* nz = 1 for D2Q9 */
+    int periodic[3];
+    double dx, dt, tau, rho0;
+    int force_model;       /* ORC_FORCE_* */
+    double g[3];           /* uniform body acceleration */
+    int lorentz;           /* 1: a = g + (sigma_e/rho) (E + v x B) x B, imposed B, E */
+    double B[3], E[3], sigma_e, mu;
+    int maxwell;           /* 1: equilibrium of Eq. (10) with the imposed B */
+    int les;               /* 1: Smagorinsky relaxation time from f^neq */
+    double cs;             /* Smagorinsky constant */
+    int n_walls;           /* wall ids 1..n_walls */
+    double wall_u[ORC_MAX_WALLS][3];   /* velocity of wall k at index k-1 */
+    int face_wall[6];
+} orc_cfg;
+
+/* lattice tables: e (unit-speed integers, Q*3), w (Q), opposite index (Q) */
+int orc_lattice(int q, int* e, double* w, int* opp);
+
+/* equilibrium of Eq. (1), plus the Maxwell term of Eq. (10) if cfg->maxwell */
+void orc_feq(const orc_cfg* c, double rho, const double* u, double* out);
+
+/* per-node macroscopic quantities for pre-collision populations f[Q]:
+ * out[0] rho, out[1..3] u, out[4..6] v, out[7..9] a, out[10..12] u^eq,
+ * out[13..15] u^F, out[16] C, out[17] tau_eff */
+void orc_node_macro(const orc_cfg* c, const double* f, double* out);
+
+/* force term F_alpha of the configured model at a node (Sec. 2) */
+void orc_force_term(const orc_cfg* c, const double* f, double* F);
+
+/* relaxation of Eq. (2): frel = f + (f^eq - f)/tau + F at one node */
+void orc_collide_node(const orc_cfg* c, const double* f, double* frel);
+
+/* canonical initial state f = f^eq(rho(x), u(x)) * (1 + xi) at fluid nodes,
+ * 0 at solid nodes; u is [3][N]; xi may be NULL */
+void orc_init(const orc_cfg* c, const unsigned char* wall_id, const double* rho,
+              const double* u, const double* xi, double* f);
+
+/* one step of Eq. (2): f (in: f(t), out: f(t+dt)); frel (N*Q) receives
+ * f^rel(t) if not NULL */
+void orc_step(const orc_cfg* c, const unsigned char* wall_id, double* f, double* frel);
+
+/* run n steps in place */
+void orc_run(const orc_cfg* c, const unsigned char* wall_id, double* f, int n);
+
+/* momentum-exchange force of Eq. (25) on wall `wall` (or every wall if
+ * wall < 0) during the step t -> t+dt, from frel = f^rel(t) and
+ * fnext = f(t+dt); flags ORC_MOVING_CORR | ORC_MAXWELL_REMOVE; out[3] */
+void orc_wall_force(const orc_cfg* c, const unsigned char* wall_id, const double* frel,
+                    const double* fnext, int wall, int flags, double* out);
+
+/* number of boundary links of wall `wall` (or all walls if < 0) */
+long orc_count_links(const orc_cfg* c, const unsigned char* wall_id, int wall);
+
+/* stress tensor per node.  Variants 1, 2 use f = f(t); variants 3, 4 use
+ * frel = f^rel(t) and fnext = f(t+dt).  sigma, S: ncomp*N (ncomp 3 in 2-D:
+ * xx yy xy; 6 in 3-D: xx yy zz xy xz yz); rho: N; v: 3*N (for variants 1-2 the
+ * node's rho and flow velocity v, for 3-4 the half-step rho-bar and u-bar).
+ * Solid nodes get zeros. */
+void orc_stress(const orc_cfg* c, const unsigned char* wall_id, const double* f,
+                const double* frel, const double* fnext, int variant,
+                double* sigma, double* S, double* rho, double* v);
+
+/* global sums of the canonical state f(t) over fluid nodes, times dx^D:
+ * out[0] mass, out[1..3] momentum sum_x sum_a e f, out[4..6] sum rho a */
+void orc_balance(const orc_cfg* c, const unsigned char* wall_id, const double* f, double* out);
+
+/* time-averaged drag J = (1/T) sum_{t=0}^{T-1} d . F_wall(t) (uncorrected
+ * momentum exchange on wall `wall`) from the canonical initial state f0, and
+ * its gradient with respect to theta = (g[0..2], u_w[0..2] of `wall`), by the
+ * discrete adjoint with complex-step collision Jacobians.  grad[6]. */
+int orc_adjoint_drag(const orc_cfg* c, const unsigned char* wall_id, const double* f0, int T,
+                     int wall, const double* d, double* J, double* grad);
+
+/* J alone (forward only), for finite differences */
+double orc_drag_average(const orc_cfg* c, const unsigned char* wall_id, const double* f0, int T,
+                        int wall, const double* d);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

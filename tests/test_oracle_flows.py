@@ -1,0 +1,283 @@
+"""Pins of the oracle's whole-lattice behaviour against closed forms and exact
+identities (no GPU).
+
+* exact discrete momentum balance of every step (the discrete form of Eq. 32):
+  F_wall(t) = sum rho a - [M(t+dt) - M(t)]/dt;
+* Poiseuille channel at steady state: the flow velocity is the parabola of the
+  recovered Navier-Stokes equation (Eq. 7) plus the known halfway-bounce-back
+  slip of BGK, (g/2nu)(16 Lambda - 3)/12 with Lambda = (tau - 1/2)^2; each wall
+  carries half the body force (Eq. 33); the shear stress of Eqs. (8)-(9) is
+  rho g (H - 1 - 2y)/2;
+* Hartmann-Couette channel: second-order convergence to the cosh profile and
+  wall shear, exact global balance with the Lorentz force included;
+* moving-wall correction (Sec. 5): rho_w u_w (u_w . n) per flat wall node,
+  zero on a closed body;
+* Maxwell stress: with a uniform field f_B(t) = f_0(t) + Delta exactly, the
+  momentum exchange contains -L n per flat wall node (Sec. 5, Eq. 28), its
+  removal restores the field-free force, and it cancels on a closed body
+  (Eq. 36);
+* half-step consistency at steady state (Eqs. 29-30).
+"""
+import numpy as np
+import pytest
+
+from paper_2512_12213_gb300 import inputs
+
+
+def _channel_cfg(orc, H, tau, model, g, nx=2, **kw):
+    base = dict(q=9, nx=nx, ny=H, nz=1, periodic=(1, 0, 1), tau=tau, force_model=model,
+                g=(g, 0, 0), wall_u=((0, 0, 0), (0, 0, 0)), face_wall=(1, 1, 1, 2, 1, 1))
+    base.update(kw)
+    return orc.make_cfg(**base)
+
+
+def _rest(orc, cfg, mask):
+    nz, ny, nx = mask.shape
+    return orc.init(cfg, mask, np.full((nz, ny, nx), cfg.rho0), np.zeros((3, nz, ny, nx)))
+
+
+@pytest.mark.parametrize("q", [9, 19])
+@pytest.mark.parametrize("model", list("abcde"))
+def test_exact_momentum_balance_every_step(orc, q, model):
+    """Every step, the momentum lost to walls equals the body-force impulse
+    minus the change of fluid momentum, for moving walls, Lorentz force and the
+    Maxwell equilibrium together, at non-unit dx and dt."""
+    if q == 9:
+        nx, ny, nz, per = 12, 9, 1, (1, 0, 1)
+    else:
+        nx, ny, nz, per = 7, 6, 5, (1, 0, 0)
+    mask = inputs.random_solids(nx, ny, nz, 0.12, n_walls=2, seed=11 + q)
+    cfg = orc.make_cfg(q=q, nx=nx, ny=ny, nz=nz, periodic=per, dx=0.5, dt=0.2, tau=0.81,
+                       force_model=model, g=(3e-2, -1e-2, 5e-3), lorentz=1, B=(0.1, 0.25, -0.05),
+                       E=(1e-3, 0, 2e-3), sigma_e=0.8, maxwell=1, mu=1.3,
+                       wall_u=((0.01, 0.02, -0.01), (0.0, -0.015, 0.02), (0.03, 0, 0)),
+                       face_wall=(3, 3, 3, 2, 1, 3))
+    c = cfg.dx / cfg.dt
+    D = 2 if q == 9 else 3
+    rho, u = inputs.smooth_fields(nx, ny, nz, dims=D, seed=5)
+    f = orc.init(cfg, mask, rho, u * 0.5 * c, inputs.noise(q, nx, ny, nz, 1e-2, seed=6))
+    for _ in range(4):
+        _, M0, rhoa = orc.balance(cfg, mask, f)
+        fn, fr = orc.step(cfg, mask, f)
+        _, M1, _ = orc.balance(cfg, mask, fn)
+        F = orc.wall_force(cfg, mask, fr, fn, -1, 0)
+        ref = rhoa - (M1 - M0) / cfg.dt
+        scale = np.abs(M0).max() / cfg.dt + np.abs(F).max()
+        assert np.allclose(F, ref, rtol=0, atol=2e-14 * scale), (F, ref)
+        f = fn
+
+
+@pytest.mark.parametrize("model,tau", [("a", 0.8), ("b", 0.8), ("c", 0.8), ("d", 0.8),
+                                       ("e", 0.8), ("e", 0.6), ("d", 1.0)])
+def test_poiseuille_steady_state(orc, model, tau):
+    H, g, nx = 16, 1e-6, 2
+    cfg = _channel_cfg(orc, H, tau, model, g, nx=nx)
+    mask = inputs.empty_mask(nx, H)
+    nu = (tau - 0.5) / 3
+    steps = int(40 / (nu * np.pi ** 2 / H ** 2))      # slowest mode decayed by e^-40
+    f = orc.run(cfg, mask, _rest(orc, cfg, mask), steps)
+    fn, fr = orc.step(cfg, mask, f)
+    sig, S, rho, v = orc.stress(cfg, mask, f, fr, fn, 2)
+    y = np.arange(H)
+    lam = (tau - 0.5) ** 2
+    v_exact = g / (2 * nu) * ((y + 0.5) * (H - 0.5 - y) + (16 * lam - 3) / 12)
+    vx = v[0, 0, :, 0]
+    assert np.abs(vx - v_exact).max() < 1e-9 * v_exact.max()
+    assert np.abs(v[1]).max() < 1e-9 * v_exact.max()
+    # shear stress sigma_xy = rho nu du/dy, linear between the walls
+    sxy = sig[2, 0, :, 0]
+    s_exact = rho[0, :, 0] * g * (H - 1 - 2 * y) / 2
+    assert np.abs(sxy - s_exact).max() < 1e-9 * s_exact.max()
+    assert np.allclose(S[2], sig[2] / (2 * rho * nu), rtol=1e-13)
+    # each wall carries half of the body force (Eq. 33 and symmetry)
+    mass, M, rhoa = orc.balance(cfg, mask, f)
+    Fb = orc.wall_force(cfg, mask, fr, fn, 1)
+    Ft = orc.wall_force(cfg, mask, fr, fn, 2)
+    assert np.isclose(Fb[0], 0.5 * g * mass, rtol=1e-9)
+    assert np.isclose(Ft[0], 0.5 * g * mass, rtol=1e-9)
+    assert np.isclose(Fb[0] + Ft[0], rhoa[0], rtol=1e-9)
+
+
+def _hartmann(orc, H, tau, Ha=10.0, Uw=0.05, B0=0.05, model="e", maxwell=0):
+    nu = (tau - 0.5) / 3
+    K = nu * Ha ** 2 / H ** 2
+    g = 0.05 * K / (1 - 1 / np.cosh(Ha))
+    ny = 2 * H
+    cfg = orc.make_cfg(q=9, nx=1, ny=ny, nz=1, periodic=(1, 0, 1), tau=tau, force_model=model,
+                       g=(g, 0, 0), lorentz=1, B=(0, B0, 0), sigma_e=K / B0 ** 2, maxwell=maxwell,
+                       wall_u=((0, 0, 0), (Uw, 0, 0)), face_wall=(1, 1, 1, 2, 1, 1))
+    mask = inputs.empty_mask(1, ny)
+    f = orc.run(cfg, mask, _rest(orc, cfg, mask), int(36 / K))
+    fn, fr = orc.step(cfg, mask, f)
+    m = Ha / H
+    y = np.arange(ny) - H + 0.5
+    u_exact = (g / K) * (1 - np.cosh(m * y) / np.cosh(m * H)) + Uw * np.sinh(m * (y + H)) / np.sinh(2 * m * H)
+    dudy = lambda yy: (g / K) * (-m * np.sinh(m * yy) / np.cosh(m * H)) + Uw * m * np.cosh(m * (yy + H)) / np.sinh(2 * m * H)
+    return dict(cfg=cfg, mask=mask, f=f, fn=fn, fr=fr, u_exact=u_exact, y=y, nu=nu,
+                shear=(nu * dudy(-H), -nu * dudy(H)), dudy=dudy)
+
+
+def test_hartmann_couette_convergence(orc):
+    """Hartmann number 10, moving top wall: velocity and wall shear converge
+    at second order to nu u'' - K u + g = 0 with u(-H) = 0, u(H) = U_w; the
+    sum of wall forces equals sum rho a including the Lorentz force."""
+    errs, shear_b, shear_t = [], [], []
+    for H in (16, 32, 64):
+        r = _hartmann(orc, H, 0.8)
+        cfg, mask = r["cfg"], r["mask"]
+        _, _, _, v = orc.stress(cfg, mask, r["f"], r["fr"], r["fn"], 2)
+        errs.append(np.abs(v[0, 0, :, 0] - r["u_exact"]).max() / np.abs(r["u_exact"]).max())
+        Fb = orc.wall_force(cfg, mask, r["fr"], r["fn"], 1)
+        Ft = orc.wall_force(cfg, mask, r["fr"], r["fn"], 2)
+        _, _, rhoa = orc.balance(cfg, mask, r["f"])
+        assert np.isclose(Fb[0] + Ft[0], rhoa[0], rtol=1e-10)
+        shear_b.append(abs(Fb[0] / r["shear"][0] - 1))
+        shear_t.append(abs(Ft[0] / r["shear"][1] - 1))
+    assert errs[-1] < 2e-3 and errs[-2] / errs[-1] > 3.0
+    for s in (shear_b, shear_t):
+        assert s[-1] < 1e-3
+        assert 3.8 < s[0] / s[1] < 4.2 and 3.8 < s[1] / s[2] < 4.2
+
+
+@pytest.mark.parametrize("model", ["e", "d"])
+def test_half_step_consistency(orc, model):
+    """Eqs. (29)-(30) at steady state: the half-step stress about
+    f^eq(rho-bar, u-bar) plus Theta/2 equals the full-step stress (variant 2)
+    plus rho (v v - u^eq u^eq), which vanishes for Guo's model [e] where
+    u^eq = v."""
+    r = _hartmann(orc, 16, 0.7, model=model)
+    cfg, mask = r["cfg"], r["mask"]
+    s2, _, rho, v = orc.stress(cfg, mask, r["f"], r["fr"], r["fn"], 2)
+    s4, _, rb, ub = orc.stress(cfg, mask, r["f"], r["fr"], r["fn"], 4)
+    s3, _, _, _ = orc.stress(cfg, mask, r["f"], r["fr"], r["fn"], 3)
+    vx = v[0]
+    ueq = vx if model == "e" else None
+    if model == "d":
+        # u^eq = u = v - dt a/2 with a_x = g - K v_x (Lorentz), a_y = 0
+        g = cfg.g[0]
+        K = cfg.sigma_e * cfg.B[1] ** 2 / rho
+        ueq = vx - 0.5 * cfg.dt * (g - K * vx)
+    corr_xx = rho * (vx * vx - ueq * ueq)
+    scale = np.abs(s2).max()
+    assert np.allclose(rb, rho, rtol=1e-13)
+    assert np.allclose(ub[0], vx, rtol=0, atol=1e-13 * np.abs(vx).max())
+    assert np.allclose(s4[0], s2[0] + corr_xx, rtol=0, atol=1e-10 * scale)
+    assert np.allclose(s4[1:], s2[1:], rtol=0, atol=1e-10 * scale)
+    # and variant 3 differs from variant 4 by Theta/2, which is O(tau dt u a)
+    assert np.abs(s4 - s3).max() < 1e-2 * scale
+
+
+@pytest.mark.parametrize("q", [9, 19])
+def test_moving_wall_correction(orc, q):
+    """Wen's Galilean correction adds rho_w u_w (u_w . n) dx^(D-1) per flat
+    wall node (it offsets the momentum flux -rho u u n contained in Eq. 25);
+    tangential wall motion gets exactly zero."""
+    D = 2 if q == 9 else 3
+    nx, ny, nz = (6, 8, 1) if q == 9 else (4, 5, 6)
+    ax = 1 if q == 9 else 2            # closed axis
+    per = [1, 1, 1]
+    per[ax] = 0
+    fw = [3] * 6
+    fw[2 * ax], fw[2 * ax + 1] = 1, 2
+    ub = np.array([0.02, 0.01, 0.0])
+    ut = np.array([-0.01, 0.015, 0.0]) if q == 9 else np.array([0.01, -0.02, 0.015])
+    if q == 19:
+        ub = np.array([0.02, -0.01, 0.03])
+    cfg = orc.make_cfg(q=q, nx=nx, ny=ny, nz=nz, periodic=per, dx=0.5, dt=0.25, tau=0.9,
+                       force_model="e", g=(1e-3, 0, 0), wall_u=(ub, ut, (0, 0, 0)), face_wall=fw)
+    mask = inputs.empty_mask(nx, ny, nz)
+    f = orc.init(cfg, mask, np.ones((nz, ny, nx)), np.zeros((3, nz, ny, nx)),
+                 inputs.noise(q, nx, ny, nz, 1e-3))
+    fn, fr = orc.step(cfg, mask, f)
+    n_nodes = nx * ny * nz // [nx, ny, nz][ax]
+    area = cfg.dx ** (D - 1)
+    for wall, uw, nsign in ((1, ub, 1.0), (2, ut, -1.0)):
+        F0 = orc.wall_force(cfg, mask, fr, fn, wall, 0)
+        d = orc.wall_force(cfg, mask, fr, fn, wall, orc.MOVING_CORR) - F0
+        un = uw[ax] * nsign
+        # tolerance: rounding of the difference of two forces of size |F0|
+        assert np.allclose(d, n_nodes * area * cfg.rho0 * uw * un, rtol=0,
+                           atol=1e-14 * np.abs(F0).max())
+    # tangential motion only: exactly zero correction
+    ut2 = ut.copy()
+    ut2[ax] = 0
+    cfg2 = orc.make_cfg(q=q, nx=nx, ny=ny, nz=nz, periodic=per, dx=0.5, dt=0.25, tau=0.9,
+                        force_model="e", wall_u=(ut2, ut2, (0, 0, 0)), face_wall=fw)
+    fn, fr = orc.step(cfg2, mask, f)
+    for wall in (1, 2):
+        d = orc.wall_force(cfg2, mask, fr, fn, wall, orc.MOVING_CORR) - orc.wall_force(cfg2, mask, fr, fn, wall, 0)
+        assert np.abs(d).max() < 1e-15
+
+
+@pytest.mark.parametrize("q", [9, 19])
+def test_closed_body_corrections_cancel(orc, q):
+    """On a closed staircase body with uniform wall velocity the moving-wall
+    correction sums to zero, and the Maxwell part of the momentum exchange
+    cancels (the discrete form of Eq. 36)."""
+    if q == 9:
+        nx, ny, nz = 16, 12, 1
+        mask = inputs.cylinder_mask(nx, ny, (7.3, 5.6), 3.2)
+        B = (0.1, 0.2, 0.0)
+    else:
+        nx, ny, nz = 10, 9, 8
+        mask = inputs.sphere_mask(nx, ny, nz, (4.5, 4.2, 3.7), 2.6)
+        B = (0.1, 0.2, -0.15)
+    uw = (0.02, -0.01, 0.015 if q == 19 else 0.0)
+    cfg = orc.make_cfg(q=q, nx=nx, ny=ny, nz=nz, periodic=(1, 1, 1), tau=0.75, force_model="d",
+                       g=(1e-4, 0, 0), maxwell=1, B=B, wall_u=(uw,))
+    f = _rest(orc, cfg, mask)
+    f = orc.run(cfg, mask, f, 3)
+    fn, fr = orc.step(cfg, mask, f)
+    F0 = orc.wall_force(cfg, mask, fr, fn, 1, 0)
+    Fm = orc.wall_force(cfg, mask, fr, fn, 1, orc.MOVING_CORR)
+    Fx = orc.wall_force(cfg, mask, fr, fn, 1, orc.MAXWELL_REMOVE)
+    nl = orc.count_links(cfg, mask, 1)
+    assert nl > 0
+    # tolerance: rounding of a sum of nl link terms of size ~ rho0 c dx^D / dt
+    tol = 1e-15 * nl * cfg.rho0 * (cfg.dx / cfg.dt) * cfg.dx ** (2 if q == 9 else 3) / cfg.dt
+    assert np.abs(Fm - F0).max() < tol
+    assert np.abs(Fx - F0).max() < tol
+
+
+@pytest.mark.parametrize("q", [9, 19])
+def test_maxwell_equilibrium_shift_and_removal(orc, q):
+    """With a uniform B, the Maxwell term Delta of Eq. (10) has zero zeroth and
+    first moments and is even in e, so f_B(t) = f_0(t) + Delta exactly; the
+    momentum exchange then contains -L n per flat wall node, and the Maxwell
+    removal gives back the field-free force."""
+    D = 2 if q == 9 else 3
+    nx, ny, nz = (6, 8, 1) if q == 9 else (4, 5, 6)
+    ax = 1 if q == 9 else 2
+    per = [1, 1, 1]
+    per[ax] = 0
+    fw = [3] * 6
+    fw[2 * ax], fw[2 * ax + 1] = 1, 2
+    B = np.array([0.07, -0.12, 0.05 if q == 19 else 0.0])
+    kw = dict(q=q, nx=nx, ny=ny, nz=nz, periodic=per, dx=0.5, dt=0.25, tau=0.9, force_model="b",
+              g=(2e-3, 0, 0), B=B, mu=0.8, wall_u=((0.01, 0, 0), (0, 0, 0), (0, 0, 0)), face_wall=fw)
+    c0 = orc.make_cfg(maxwell=0, **kw)
+    cB = orc.make_cfg(maxwell=1, **kw)
+    mask = inputs.empty_mask(nx, ny, nz)
+    f0 = orc.init(c0, mask, np.ones((nz, ny, nx)), np.zeros((3, nz, ny, nx)),
+                  inputs.noise(q, nx, ny, nz, 1e-3))
+    delta = orc.feq(cB, 1.0, np.zeros(3)) - orc.feq(c0, 1.0, np.zeros(3))
+    fB = f0 + delta[:, None, None, None]
+    for _ in range(5):
+        f0n, f0r = orc.step(c0, mask, f0)
+        fBn, fBr = orc.step(cB, mask, fB)
+        assert np.allclose(fBn - f0n, delta[:, None, None, None], rtol=0, atol=1e-15)
+        d = np.diag([1.0] * D + [0.0] * (3 - D))
+        L = (B @ B * d / 2 - np.outer(B, B)) / cB.mu
+        n_nodes = nx * ny * nz // [nx, ny, nz][ax]
+        area = cB.dx ** (D - 1)
+        for wall, nsign in ((1, 1.0), (2, -1.0)):
+            n = np.zeros(3)
+            n[ax] = nsign
+            P0 = orc.wall_force(c0, mask, f0r, f0n, wall, 0)
+            PB = orc.wall_force(cB, mask, fBr, fBn, wall, 0)
+            PR = orc.wall_force(cB, mask, fBr, fBn, wall, orc.MAXWELL_REMOVE)
+            # tolerance: rounding relative to the wall's pressure force |P0|
+            tol = 1e-14 * np.abs(P0).max()
+            assert np.allclose(PB - P0, -n_nodes * area * (L @ n), rtol=0, atol=tol)
+            assert np.allclose(PR, P0, rtol=0, atol=tol)
+        f0, fB = f0n, fBn
