@@ -1,0 +1,247 @@
+/*
+ * lbm.h -- C ABI of the GB300 lattice Boltzmann hot path of arXiv 2512.12213
+ * ("Shear Stress and Fluid-Wall Interaction Force in LBM Simulations of
+ * Hydrodynamic and MHD Flows").
+ *
+ * What the library computes (all of it in CUDA kernels on the caller's stream):
+ *   - the BGK relaxation-propagation step of Eq. (2) on D2Q9 / D3Q19 with the
+ *     equilibrium of Eq. (1) (plus the Maxwell term of Eq. (10) on request),
+ *     one of the five force models of Sec. 2 ([a] He, [b] Martys/Luo,
+ *     [c] Shan-Chen reformulated, [d] exact difference reformulated, [e] Guo),
+ *     a uniform body force and/or an imposed-field low-Rm Lorentz force,
+ *     optional Smagorinsky relaxation time, halfway bounce-back with Ladd's
+ *     moving-wall term;
+ *   - the stress and strain-rate tensors of Eqs. (8)-(9) with or without the
+ *     artefact term E_ij, and from the half-step distribution of Eqs. (27)-(30);
+ *   - the momentum-exchange wall force of Eq. (25) with the moving-wall and
+ *     Maxwell-stress corrections discussed in Sec. 5, accumulated in FP64;
+ *   - global FP64 sums for the balance of Eq. (32);
+ *   - one reverse step of the discrete adjoint of the above, for gradients of
+ *     time-averaged wall drag.
+ *
+ * Conventions
+ *   Memory   : every large device buffer is allocated by the caller and bound
+ *              at lbm_create (sizes from lbm_buffer_sizes).  The library keeps
+ *              pointers to them and allocates no device memory itself.
+ *              Device pointers must be 256-byte aligned.
+ *   Streams  : `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *              default stream).  Device work is asynchronous on it; a call that
+ *              writes a host buffer synchronises that stream before returning.
+ *   Units    : physical (dx, dt, c = dx/dt); forces are per unit depth in 2-D.
+ *   Layout   : canonical arrays exchanged with the caller are dense C arrays,
+ *              node index n = (z*ny + y)*nx + x; populations f[a][n] (a the
+ *              velocity index), vectors v[k][n] (k = 0,1,2), tensors s[c][n]
+ *              with components xx yy xy (2-D) or xx yy zz xy xz yz (3-D).
+ *              Velocity order:
+ *                D2Q9 : 0 (0,0) 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1)
+ *                       5 (1,1) 6 (-1,1) 7 (-1,-1) 8 (1,-1)
+ *                D3Q19: 0 rest, 1/2 +-x, 3/4 +-y, 5/6 +-z, 7/8 +-(1,1,0),
+ *                       9/10 +-(1,-1,0), 11/12 +-(1,0,1), 13/14 +-(1,0,-1),
+ *                       15/16 +-(0,1,1), 17/18 +-(0,1,-1)
+ *   Geometry : wall_id[n] = 0 for a fluid node, k in 1..n_walls for a solid
+ *              node of wall k.  A non-periodic axis is closed on both faces by
+ *              halfway bounce-back walls with ids face_wall[2*axis + side].
+ *              A link leaving the box through several closed faces at once
+ *              takes the wall of the first such axis in the order x, y, z.
+ *   Time     : the context holds the state at time T (steps taken since the
+ *              last init/import).  Internally it stores the post-collision
+ *              populations f^rel(T-1); the canonical f(T) (post-propagation,
+ *              pre-collision) is what export returns.
+ *   Errors   : every call returns an lbm_status; nothing aborts or throws
+ *              across the ABI.  lbm_last_error() gives a message.  A context
+ *              is not thread safe.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum lbm_status {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,          /* invalid argument, configuration or buffer */
+    LBM_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+    LBM_ERR_OOM = 3,          /* a host allocation failed */
+    LBM_ERR_UNSUPPORTED = 4,  /* valid request that this build does not implement */
+    LBM_ERR_NAN = 5,          /* non-finite values found */
+    LBM_ERR_STATE = 6         /* call not valid in the context's current state */
+} lbm_status;
+
+enum { LBM_D2Q9 = 9, LBM_D3Q19 = 19 };
+
+/* force models of Sec. 2 (C, u^F, u^eq):
+ * [a] He 1997 (1, -, u)  [b] Martys/Luo (1, u, u)  [c] Shan-Chen (1, u + tau dt a/2, u)
+ * [d] exact difference (1, v, u)  [e] Guo 2002 (1 - 1/(2 tau), v, v), v = u + dt a/2 */
+enum { LBM_FORCE_A = 0, LBM_FORCE_B = 1, LBM_FORCE_C = 2, LBM_FORCE_D = 3, LBM_FORCE_E = 4 };
+
+/* population storage.  F64 computes in FP64; the others compute in FP32.
+ * All modes store the shifted deviation f_a - w_a rho0; F16S stores it scaled
+ * by 2^12 in IEEE binary16, BF16S unscaled in bfloat16. */
+enum { LBM_STORE_F64 = 0, LBM_STORE_F32 = 1, LBM_STORE_F16S = 2, LBM_STORE_BF16S = 3 };
+
+/* stress variants:
+ * S1 sigma = -(1 - 1/(2 tau)) [Pi^neq + E_ij]   (Eq. 9 with the artefact term)
+ * S2 sigma = -(1 - 1/(2 tau)) Pi^neq            (E_ij neglected, after Eq. 23)
+ * S3 sigma = -sum e e (fbar - f^eq(rhobar, ubar)), fbar of Eq. (27)
+ * S4 S3 + Theta/2                               (Eq. 30)
+ * with Pi^neq = sum e e f - (p delta + rho u^eq u^eq + L); S = sigma/(2 rho nu). */
+enum { LBM_S1 = 1, LBM_S2 = 2, LBM_S3 = 3, LBM_S4 = 4 };
+
+/* wall-force options (Sec. 5) */
+enum {
+    LBM_MOVING_CORR = 1,      /* add u_w (fbar_a - fbar_a') per link (Galilean correction) */
+    LBM_MAXWELL_REMOVE = 2,   /* subtract 2 e_a' Delta_a' per link (Maxwell stress) */
+    LBM_ACCUMULATE = 4        /* out += weight * F instead of out = weight * F */
+};
+
+/* caller-allocated device buffers, indexed by kind */
+enum {
+    LBM_BUF_POP_A = 0,        /* populations, ping       (required) */
+    LBM_BUF_POP_B = 1,        /* populations, pong       (required) */
+    LBM_BUF_NODE = 2,         /* node classes            (required) */
+    LBM_BUF_LINKS = 3,        /* boundary-link list      (required if any link exists) */
+    LBM_BUF_SCRATCH = 4,      /* FP64 reduction partials (required) */
+    LBM_BUF_STAGE = 5,        /* canonical staging for host import/export (optional) */
+    LBM_NUM_BUFFERS = 6
+};
+
+#define LBM_MAX_WALLS 16
+
+typedef struct lbm_config {
+    int32_t lattice;                 /* LBM_D2Q9 or LBM_D3Q19 */
+    int32_t nx, ny, nz;              /* nz = 1 for D2Q9; 1 <= n, nx*ny*nz < 2^31 */
+    int32_t periodic[3];             /* per axis; closed axes get face walls */
+    double dx, dt;                   /* lattice spacing and time step, c = dx/dt */
+    double tau;                      /* relaxation time, > 1/2; nu = dt c^2 (tau - 1/2)/3 */
+    double rho0;                     /* reference density (shift of the storage, wall density) */
+    int32_t force_model;             /* LBM_FORCE_* */
+    double g[3];                     /* uniform body acceleration */
+    int32_t lorentz;                 /* 1: add (sigma_e/rho)(E + v x B) x B at the flow velocity v */
+    double B[3], E[3];               /* imposed magnetic and electric field */
+    double sigma_e;                  /* electrical conductivity */
+    double mu;                       /* magnetic permeability (Maxwell equilibrium) */
+    int32_t maxwell;                 /* 1: Maxwell term of Eq. (10) with B in the equilibrium */
+    int32_t les;                     /* 1: Smagorinsky relaxation time */
+    double cs;                       /* Smagorinsky constant */
+    int32_t storage;                 /* LBM_STORE_* */
+    int32_t n_walls;                 /* wall ids 1..n_walls, n_walls <= LBM_MAX_WALLS */
+    double wall_u[LBM_MAX_WALLS][3]; /* velocity of wall k at index k-1 */
+    int32_t face_wall[6];            /* wall id of each closed face: -x +x -y +y -z +z */
+} lbm_config;
+
+/* Required bytes of each buffer kind for this configuration and geometry.
+ * host_wall_id: nx*ny*nz bytes (layout above), host memory.
+ * sizes[LBM_NUM_BUFFERS] receives the byte counts (0 where not needed).
+ * Errors: LBM_ERR_ARG for an invalid configuration (message via
+ * lbm_config_error). */
+lbm_status lbm_buffer_sizes(const lbm_config* cfg, const uint8_t* host_wall_id,
+                            size_t sizes[LBM_NUM_BUFFERS]);
+
+/* Message for the last lbm_buffer_sizes / lbm_create failure on this thread. */
+const char* lbm_config_error(void);
+
+/* Create a context on the current CUDA device.  buffers/sizes are indexed by
+ * LBM_BUF_*; each buffer must be 256-byte aligned and at least the size from
+ * lbm_buffer_sizes (STAGE may be NULL with size 0).  Uploads the node classes
+ * and the link list with copies on `stream` and waits for them.  Populations
+ * are left undefined until lbm_init_equilibrium or lbm_import_f. */
+lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id,
+                      void* const buffers[LBM_NUM_BUFFERS], const size_t sizes[LBM_NUM_BUFFERS],
+                      void* stream, lbm_ctx** out);
+
+/* Free the context (host memory only; the caller's buffers are untouched). */
+lbm_status lbm_destroy(lbm_ctx* ctx);
+
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Number of boundary links of wall `wall` (all walls if wall < 0). */
+lbm_status lbm_link_count(const lbm_ctx* ctx, int wall, int64_t* count);
+
+/* Change the uniform body force / one wall's velocity (takes effect at the
+ * next launch; used by the adjoint driver to set parameters). */
+lbm_status lbm_set_body_force(lbm_ctx* ctx, const double g[3]);
+lbm_status lbm_set_wall_velocity(lbm_ctx* ctx, int wall, const double u[3]);
+
+/* Initialise f(0) = f^eq(rho, u) (1 + xi) at fluid nodes (Eq. 1, or Eq. 10
+ * with the Maxwell term).  rho: N doubles; u: 3*N doubles (canonical layout);
+ * xi: Q*N doubles or NULL.  Arrays are on the host if on_host, else on the
+ * device.  Host arrays need the STAGE buffer.  Sets T = 0. */
+lbm_status lbm_init_equilibrium(lbm_ctx* ctx, const double* rho, const double* u,
+                                const double* xi, int on_host, void* stream);
+
+/* Import / export the canonical populations f(T) (dense, Q*N values).
+ * dtype: 0 = double, 1 = float.  Solid nodes export as 0 and are ignored on
+ * import.  Host arrays need the STAGE buffer; export to host synchronises.
+ * Import sets T = 0. */
+lbm_status lbm_import_f(lbm_ctx* ctx, const void* src, int dtype, int on_host, void* stream);
+lbm_status lbm_export_f(lbm_ctx* ctx, void* dst, int dtype, int on_host, void* stream);
+
+/* Advance nsteps steps of Eq. (2) (fused relaxation, force and propagation). */
+lbm_status lbm_step(lbm_ctx* ctx, int nsteps, void* stream);
+
+/* One step from a stored state `src` into `dst` (raw post-collision buffers
+ * laid out like LBM_BUF_POP_*, e.g. checkpoints); does not touch the
+ * context's own populations or time. */
+lbm_status lbm_step_from(lbm_ctx* ctx, const void* src, void* dst, void* stream);
+
+/* Copy the current raw stored state out / back in (checkpointing).  Loading
+ * sets T to `t` and marks the previous state as unavailable. */
+lbm_status lbm_save_state(lbm_ctx* ctx, void* dst, void* stream);
+lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, int64_t t, void* stream);
+
+/* Current time T. */
+lbm_status lbm_time(const lbm_ctx* ctx, int64_t* t);
+
+/* Stress tensor (Eqs. 8-9, 27-30).  Outputs are dense device arrays in the
+ * compute precision (double for F64 storage, else float); any may be NULL:
+ * sigma[ncomp][N], S[ncomp][N], rho[N], v[3][N].  S1/S2 use f(T) and report
+ * the node's rho and flow velocity v; S3/S4 use the half step between T-1
+ * and T (fbar of Eq. 27) and report rho-bar and u-bar; they need T >= 1
+ * (LBM_ERR_STATE otherwise).  Solid nodes get zeros. */
+lbm_status lbm_stress(lbm_ctx* ctx, int variant, void* sigma, void* S, void* rho, void* v,
+                      void* stream);
+
+/* Momentum-exchange force of Eq. (25) exerted during the last step (T-1 -> T)
+ * on wall `wall` (every wall if wall < 0), times `weight`; flags
+ * LBM_MOVING_CORR | LBM_MAXWELL_REMOVE | LBM_ACCUMULATE.  out: 3 doubles on
+ * the host (synchronises) or device.  Needs T >= 1.  Reduction: per-link FP64
+ * terms, warp shuffle, block, then a fixed-order pass (deterministic). */
+lbm_status lbm_wall_force(lbm_ctx* ctx, int wall, unsigned flags, double weight, double* out,
+                          int out_on_host, void* stream);
+
+/* FP64 sums over fluid nodes of the canonical state f(T), times dx^D:
+ * out[0] mass, out[1..3] momentum sum e f, out[4..6] body force sum rho a. */
+lbm_status lbm_balance(lbm_ctx* ctx, double* out, int out_on_host, void* stream);
+
+/* Discrete adjoint of J = (1/T) sum_{t<T} d . F_wall(t) (uncorrected momentum
+ * exchange on `wall`) for theta = (g, u_w of `wall`), one reverse step t:
+ *   phi_t = (dC/df)^T [ S^T phi_{t+1} + dF_t/dfrel seeds ],
+ * where C is the node collision at f(t) = propagation of state_prev (the
+ * stored post-collision state P_{t-1}, laid out like LBM_BUF_POP_*) and S the
+ * propagation with bounce-back.  phi_next (NULL for t = T-1) and phi_out are
+ * device arrays laid out like populations but in the compute precision
+ * (size from lbm_adjoint_buffer_bytes).  seed_weight = 1/T; dir = d (host, 3
+ * doubles).  The u_w gradient collects the Ladd terms of f(t+1) (through
+ * phi_next) and of F_t; f(0) is a fixed initial state.  Gradient
+ * contributions accumulate in FP64 per-block slots of the scratch buffer;
+ * read them with lbm_adjoint_gradient, clear them with lbm_adjoint_reset.
+ * Supported: uniform body force, every force model, Maxwell equilibrium;
+ * LBM_ERR_UNSUPPORTED with the Lorentz force or LES. */
+lbm_status lbm_adjoint_buffer_bytes(const lbm_ctx* ctx, size_t* bytes);
+lbm_status lbm_adjoint_reset(lbm_ctx* ctx, void* stream);
+lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* state_prev, const void* phi_next,
+                            void* phi_out, int wall, const double* dir, double seed_weight,
+                            void* stream);
+/* out[0..2] = dJ/dg, out[3..5] = dJ/du_w (host or device). */
+lbm_status lbm_adjoint_gradient(lbm_ctx* ctx, double* out, int out_on_host, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,704 @@
+// lbm_abi.cu -- host side of the C ABI declared in include/lbm.h: configuration
+// checks, node classes and the boundary-link list, buffer binding, and the
+// entry points that launch the kernels of lbm_kernels.cuh on the caller's
+// stream.  No device memory is allocated here; every buffer is the caller's.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_cfg_err;
+
+int dims_of(const lbm_config* c) { return c->lattice == LBM_D2Q9 ? 2 : 3; }
+
+long long nodes_of(const lbm_config* c) { return (long long)c->nx * c->ny * c->nz; }
+
+int pitch_of(int nx) { return (nx + 63) / 64 * 64; }
+
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+size_t elem_of(int storage)
+{
+    switch (storage) {
+    case LBM_STORE_F64: return 8;
+    case LBM_STORE_F32: return 4;
+    default: return 2;
+    }
+}
+
+bool validate(const lbm_config* c, const uint8_t* wid, std::string& err)
+{
+    char buf[256];
+    auto fail = [&](const char* m) { err = m; return false; };
+    if (!c) return fail("config is NULL");
+    if (c->lattice != LBM_D2Q9 && c->lattice != LBM_D3Q19) return fail("lattice must be 9 or 19");
+    if (c->nx < 1 || c->ny < 1 || c->nz < 1) return fail("nx, ny, nz must be >= 1");
+    if (c->lattice == LBM_D2Q9 && c->nz != 1) return fail("D2Q9 needs nz = 1");
+    const long long np = (long long)pitch_of(c->nx) * c->ny * c->nz;
+    if (np >= (1ll << 31)) return fail("domain too large (padded node count must be < 2^31)");
+    if (!(c->dx > 0) || !(c->dt > 0)) return fail("dx and dt must be > 0");
+    if (!(c->tau > 0.5)) return fail("tau must be > 1/2");
+    if (!(c->rho0 > 0)) return fail("rho0 must be > 0");
+    if (c->force_model < 0 || c->force_model > 4) return fail("force_model must be 0..4");
+    if (c->storage < 0 || c->storage > 3) return fail("storage must be 0..3");
+    if (c->n_walls < 0 || c->n_walls > LBM_MAX_WALLS) return fail("n_walls must be 0..16");
+    for (int k = 0; k < 3; ++k)
+        if (c->periodic[k] != 0 && c->periodic[k] != 1) return fail("periodic[] must be 0 or 1");
+    for (int k = 0; k < dims_of(c); ++k)
+        if (!c->periodic[k])
+            for (int s = 0; s < 2; ++s) {
+                const int w = c->face_wall[2 * k + s];
+                if (w < 1 || w > c->n_walls) {
+                    snprintf(buf, sizeof buf, "face_wall[%d] = %d is not a wall id in 1..n_walls", 2 * k + s, w);
+                    err = buf;
+                    return false;
+                }
+            }
+    if (c->lorentz && !(c->sigma_e >= 0)) return fail("sigma_e must be >= 0");
+    if (c->maxwell && !(c->mu > 0)) return fail("mu must be > 0");
+    if (c->les && !(c->cs >= 0)) return fail("cs must be >= 0");
+    if (!wid) return fail("wall_id is NULL");
+    const long long N = nodes_of(c);
+    for (long long n = 0; n < N; ++n)
+        if (wid[n] > c->n_walls) {
+            snprintf(buf, sizeof buf, "wall_id[%lld] = %d exceeds n_walls", n, (int)wid[n]);
+            err = buf;
+            return false;
+        }
+    return true;
+}
+
+// link leaving node (x,y,z) along E: fluid destination -> true; wall -> false + id.
+// Periodic axes wrap; the first closed axis crossed (x, y, z) names the wall.
+template <int Q>
+bool host_push_dest(const lbm_config* c, const uint8_t* wid, int x, int y, int z, int a, long long& dn, int& wall)
+{
+    int p[3] = {x + EX<Q>(a), y + EY<Q>(a), z + EZ<Q>(a)};
+    const int n[3] = {c->nx, c->ny, c->nz};
+    const int per[3] = {c->periodic[0], c->periodic[1], Q == 9 ? 1 : c->periodic[2]};
+    for (int k = 0; k < 3; ++k) {
+        if (p[k] >= 0 && p[k] < n[k]) continue;
+        if (per[k]) {
+            p[k] = (p[k] + n[k]) % n[k];
+        } else {
+            wall = c->face_wall[2 * k + (p[k] < 0 ? 0 : 1)];
+            return false;
+        }
+    }
+    dn = ((long long)p[2] * c->ny + p[1]) * c->nx + p[0];
+    if (wid[dn]) {
+        wall = wid[dn];
+        return false;
+    }
+    return true;
+}
+
+template <int Q>
+void build_geometry(const lbm_config* c, const uint8_t* wid, int nxp, std::vector<uint8_t>& cls,
+                    std::vector<Link>* links)
+{
+    cls.assign((size_t)nxp * c->ny * c->nz, NC_PAD);
+    std::vector<Link> raw;
+    for (int z = 0; z < c->nz; ++z)
+        for (int y = 0; y < c->ny; ++y)
+            for (int x = 0; x < c->nx; ++x) {
+                const long long n = ((long long)z * c->ny + y) * c->nx + x;
+                const long long np = ((long long)z * c->ny + y) * nxp + x;
+                if (wid[n]) {
+                    cls[np] = nc_make_solid(wid[n]);
+                    continue;
+                }
+                bool bound = false;
+                for (int a = 1; a < Q; ++a) {
+                    long long dn;
+                    int wall;
+                    if (!host_push_dest<Q>(c, wid, x, y, z, a, dn, wall)) {
+                        bound = true;
+                        if (links) raw.push_back(Link{(uint32_t)np, (uint16_t)a, (uint16_t)wall});
+                    }
+                }
+                cls[np] = bound ? NC_BOUND : NC_BULK;
+            }
+    if (links) {
+        links->clear();
+        links->reserve(raw.size());
+        for (int w = 0; w <= LBM_MAX_WALLS; ++w)
+            for (const Link& L : raw)
+                if (L.wall == w) links->push_back(L);
+    }
+}
+
+void count_links(const lbm_config* c, const uint8_t* wid, long long* per_wall /* MAX+1 */)
+{
+    std::fill(per_wall, per_wall + LBM_MAX_WALLS + 1, 0);
+    std::vector<uint8_t> cls;
+    std::vector<Link> links;
+    if (c->lattice == 9) build_geometry<9>(c, wid, pitch_of(c->nx), cls, &links);
+    else build_geometry<19>(c, wid, pitch_of(c->nx), cls, &links);
+    for (const Link& L : links) per_wall[L.wall]++;
+}
+
+void sizes_of(const lbm_config* c, long long n_links, size_t s[LBM_NUM_BUFFERS])
+{
+    const long long sq = (long long)pitch_of(c->nx) * c->ny * c->nz;
+    const long long N = nodes_of(c);
+    s[LBM_BUF_POP_A] = s[LBM_BUF_POP_B] = round256((size_t)c->lattice * sq * elem_of(c->storage));
+    s[LBM_BUF_NODE] = round256((size_t)sq);
+    s[LBM_BUF_LINKS] = n_links ? round256((size_t)n_links * sizeof(Link)) : 0;
+    s[LBM_BUF_SCRATCH] = round256(SCRATCH_DOUBLES * sizeof(double));
+    s[LBM_BUF_STAGE] = round256((size_t)(c->lattice + 4) * N * sizeof(double));
+}
+
+template <typename R> void cast_kp(const KP<double>& s, KP<R>& d)
+{
+    d.rho0 = (R)s.rho0; d.tau0 = (R)s.tau0; d.om0 = (R)s.om0;
+    for (int k = 0; k < 3; ++k) {
+        d.AG[k] = (R)s.AG[k]; d.AEB[k] = (R)s.AEB[k]; d.B[k] = (R)s.B[k];
+    }
+    d.model = s.model; d.lorentz = s.lorentz; d.kappa = (R)s.kappa; d.B2 = (R)s.B2; d.Bp2 = (R)s.Bp2;
+    d.maxwell = s.maxwell;
+    for (int a = 0; a < 19; ++a) d.mx[a] = (R)s.mx[a];
+    for (int k = 0; k < 6; ++k) d.Lh[k] = (R)s.Lh[k];
+    d.les = s.les; d.lesc = (R)s.lesc;
+    for (int w = 0; w <= MAXW; ++w)
+        for (int k = 0; k < 3; ++k) d.LW[w][k] = (R)s.LW[w][k];
+    d.c = (R)s.c; d.dt = (R)s.dt; d.svol = (R)s.svol;
+}
+
+template <int Q> void maxwell_table(const lbm_config* c, double* mx)
+{
+    const double cc = c->dx / c->dt;
+    const double B2 = c->B[0] * c->B[0] + c->B[1] * c->B[1] + c->B[2] * c->B[2];
+    for (int a = 0; a < 19; ++a) mx[a] = 0.0;
+    for (int a = 0; a < Q; ++a) {
+        const double E2 = SPEED2<Q>(a);
+        const double EB = EX<Q>(a) * c->B[0] + EY<Q>(a) * c->B[1] + EZ<Q>(a) * c->B[2];
+        double m = 0.5 * B2 * E2 - EB * EB;
+        if (Q == 19) m -= B2 / 6.0;
+        mx[a] = 9.0 * WD<Q>(a) / (2.0 * cc * cc * c->mu) * m;
+    }
+}
+
+void fill_params(Ctx& x)
+{
+    const lbm_config* c = &x.cfg;
+    KP<double>& p = x.kpd;
+    memset(&p, 0, sizeof p);
+    const double cc = c->dx / c->dt;
+    const int D = dims_of(c);
+    p.rho0 = c->rho0;
+    p.tau0 = c->tau;
+    p.om0 = 1.0 / c->tau;
+    for (int k = 0; k < 3; ++k) p.AG[k] = (k < D) ? c->dt * c->g[k] / cc : 0.0;
+    p.model = c->force_model;
+    p.lorentz = c->lorentz;
+    const double ExB[3] = {c->E[1] * c->B[2] - c->E[2] * c->B[1], c->E[2] * c->B[0] - c->E[0] * c->B[2],
+                           c->E[0] * c->B[1] - c->E[1] * c->B[0]};
+    for (int k = 0; k < 3; ++k) {
+        p.AEB[k] = c->lorentz ? c->dt * c->sigma_e * ExB[k] / cc : 0.0;
+        p.B[k] = c->B[k];
+    }
+    p.kappa = c->lorentz ? c->dt * c->sigma_e : 0.0;
+    p.B2 = c->B[0] * c->B[0] + c->B[1] * c->B[1] + c->B[2] * c->B[2];
+    p.Bp2 = c->B[0] * c->B[0] + c->B[1] * c->B[1] + (D == 3 ? c->B[2] * c->B[2] : 0.0);
+    p.maxwell = c->maxwell;
+    if (c->maxwell) {
+        if (c->lattice == 9) maxwell_table<9>(c, p.mx);
+        else maxwell_table<19>(c, p.mx);
+        const int ci[6] = {0, 1, 2, 0, 0, 1}, cj[6] = {0, 1, 2, 1, 2, 2};
+        for (int k = 0; k < 6; ++k)
+            p.Lh[k] = ((ci[k] == cj[k] ? 0.5 * p.B2 : 0.0) - c->B[ci[k]] * c->B[cj[k]]) / (c->mu * cc * cc);
+    }
+    p.les = c->les;
+    p.lesc = 18.0 * c->cs * c->cs;
+    for (int w = 1; w <= c->n_walls; ++w)
+        for (int k = 0; k < 3; ++k) p.LW[w][k] = (k < D) ? 6.0 * c->rho0 * c->wall_u[w - 1][k] / cc : 0.0;
+    p.c = cc;
+    p.dt = c->dt;
+    p.svol = (D == 3 ? c->dx * c->dx * c->dx : c->dx * c->dx) / c->dt;
+    cast_kp(p, x.kpf);
+}
+
+struct DeviceGuard {
+    int old = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&old) != cudaSuccess) { ok = false; return; }
+        if (old != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int now = -1;
+        if (old >= 0 && cudaGetDevice(&now) == cudaSuccess && now != old) cudaSetDevice(old);
+    }
+};
+
+lbm_status cuda_fail(Ctx& x, cudaError_t e, const char* what)
+{
+    x.err = std::string(what) + ": " + cudaGetErrorString(e);
+    return LBM_ERR_CUDA;
+}
+
+lbm_status arg_fail(Ctx& x, const char* what)
+{
+    x.err = what;
+    return LBM_ERR_ARG;
+}
+
+long long nodes(const Ctx& x) { return (long long)x.cfg.nx * x.cfg.ny * x.cfg.nz; }
+size_t pop_bytes(const Ctx& x) { return (size_t)x.cfg.lattice * x.geo.sq * x.elem; }
+
+#define CK(expr, what)                                        \
+    do {                                                      \
+        cudaError_t e_ = (expr);                              \
+        if (e_ != cudaSuccess) return cuda_fail(x, e_, what); \
+    } while (0)
+
+#define GUARD(x)                                                                 \
+    DeviceGuard guard_((x).device);                                              \
+    if (!guard_.ok) return cuda_fail((x), cudaErrorInvalidDevice, "set device");
+
+// reduce nb partial rows of width W into out (device or host)
+lbm_status finish_reduce(Ctx& x, const double* partials, int nb, int W, double* out, bool on_host, double weight,
+                         bool accumulate, cudaStream_t st)
+{
+    if (!on_host) {
+        CK(launch_reduce_rows(partials, nb, W, out, weight, accumulate ? 1 : 0, st), "reduce");
+        return LBM_OK;
+    }
+    double* slot = x.scratch + SCRATCH_OUT_OFF;
+    CK(launch_reduce_rows(partials, nb, W, slot, weight, 0, st), "reduce");
+    double tmp[8];
+    CK(cudaMemcpyAsync(tmp, slot, sizeof(double) * W, cudaMemcpyDeviceToHost, st), "copy result");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    for (int k = 0; k < W; ++k) out[k] = accumulate ? out[k] + tmp[k] : tmp[k];
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_config_error(void) { return g_cfg_err.c_str(); }
+
+lbm_status lbm_buffer_sizes(const lbm_config* cfg, const uint8_t* host_wall_id, size_t sizes[LBM_NUM_BUFFERS])
+{
+    if (!sizes) {
+        g_cfg_err = "sizes is NULL";
+        return LBM_ERR_ARG;
+    }
+    if (!validate(cfg, host_wall_id, g_cfg_err)) return LBM_ERR_ARG;
+    long long per_wall[LBM_MAX_WALLS + 1];
+    count_links(cfg, host_wall_id, per_wall);
+    long long nl = 0;
+    for (int w = 0; w <= LBM_MAX_WALLS; ++w) nl += per_wall[w];
+    sizes_of(cfg, nl, sizes);
+    return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* const buffers[LBM_NUM_BUFFERS],
+                      const size_t sizes[LBM_NUM_BUFFERS], void* stream, lbm_ctx** out)
+{
+    if (!out || !buffers || !sizes) {
+        g_cfg_err = "NULL argument";
+        return LBM_ERR_ARG;
+    }
+    *out = nullptr;
+    if (!validate(cfg, host_wall_id, g_cfg_err)) return LBM_ERR_ARG;
+    lbm_ctx* h = new (std::nothrow) lbm_ctx();
+    if (!h) return LBM_ERR_OOM;
+    Ctx& x = h->c;
+    x.cfg = *cfg;
+    if (x.cfg.lattice == LBM_D2Q9) x.cfg.periodic[2] = 1;
+    x.ext = (cfg->lorentz || cfg->maxwell || cfg->les) ? 1 : 0;
+    x.geo.nx = cfg->nx;
+    x.geo.ny = cfg->ny;
+    x.geo.nz = cfg->nz;
+    x.geo.nxp = pitch_of(cfg->nx);
+    x.geo.sq = (long long)x.geo.nxp * cfg->ny * cfg->nz;
+    for (int k = 0; k < 3; ++k) x.geo.periodic[k] = x.cfg.periodic[k];
+    for (int k = 0; k < 6; ++k) x.geo.face_wall[k] = cfg->face_wall[k];
+    x.elem = elem_of(cfg->storage);
+    x.relem = cfg->storage == LBM_STORE_F64 ? 8 : 4;
+    switch (cfg->storage) {
+    case LBM_STORE_F64: x.ops = &dispatch_f64(); break;
+    case LBM_STORE_F32: x.ops = &dispatch_f32(); break;
+    case LBM_STORE_F16S: x.ops = &dispatch_f16(); break;
+    default: x.ops = &dispatch_bf16(); break;
+    }
+    fill_params(x);
+
+    std::vector<uint8_t> cls;
+    std::vector<Link> links;
+    if (cfg->lattice == 9) build_geometry<9>(&x.cfg, host_wall_id, x.geo.nxp, cls, &links);
+    else build_geometry<19>(&x.cfg, host_wall_id, x.geo.nxp, cls, &links);
+    x.n_links = (long long)links.size();
+    for (int w = 0; w <= LBM_MAX_WALLS + 1; ++w) x.wall_begin[w] = 0;
+    {
+        long long pos = 0;
+        for (int w = 0; w <= LBM_MAX_WALLS; ++w) {
+            x.wall_begin[w] = pos;
+            while (pos < x.n_links && links[pos].wall == w) ++pos;
+        }
+        x.wall_begin[LBM_MAX_WALLS + 1] = pos;
+    }
+
+    size_t need[LBM_NUM_BUFFERS];
+    sizes_of(&x.cfg, x.n_links, need);
+    for (int b = 0; b < LBM_NUM_BUFFERS; ++b) {
+        const bool optional = (b == LBM_BUF_STAGE) || (b == LBM_BUF_LINKS && need[b] == 0);
+        if (!buffers[b]) {
+            if (optional) continue;
+            g_cfg_err = "required buffer " + std::to_string(b) + " is NULL";
+            delete h;
+            return LBM_ERR_ARG;
+        }
+        if (((uintptr_t)buffers[b]) % 256 != 0) {
+            g_cfg_err = "buffer " + std::to_string(b) + " is not 256-byte aligned";
+            delete h;
+            return LBM_ERR_ARG;
+        }
+        if (sizes[b] < need[b]) {
+            g_cfg_err = "buffer " + std::to_string(b) + " is smaller than required (" + std::to_string(sizes[b]) +
+                        " < " + std::to_string(need[b]) + ")";
+            delete h;
+            return LBM_ERR_ARG;
+        }
+    }
+    x.pop[0] = buffers[LBM_BUF_POP_A];
+    x.pop[1] = buffers[LBM_BUF_POP_B];
+    x.cur = 0;
+    x.cls = (uint8_t*)buffers[LBM_BUF_NODE];
+    x.links = (Link*)buffers[LBM_BUF_LINKS];
+    x.scratch = (double*)buffers[LBM_BUF_SCRATCH];
+    x.stage = buffers[LBM_BUF_STAGE];
+    x.stage_bytes = x.stage ? sizes[LBM_BUF_STAGE] : 0;
+    x.t = 0;
+    x.prev_valid = false;
+    if (cudaGetDevice(&x.device) != cudaSuccess) {
+        g_cfg_err = "cudaGetDevice failed";
+        delete h;
+        return LBM_ERR_CUDA;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(x.cls, cls.data(), cls.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && x.n_links)
+        e = cudaMemcpyAsync(x.links, links.data(), links.size() * sizeof(Link), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_zero(x.scratch, (long long)SCRATCH_DOUBLES, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        g_cfg_err = std::string("upload: ") + cudaGetErrorString(e);
+        delete h;
+        return LBM_ERR_CUDA;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_ctx* ctx)
+{
+    delete ctx;
+    return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->c.err.c_str() : "NULL context"; }
+
+lbm_status lbm_link_count(const lbm_ctx* ctx, int wall, int64_t* count)
+{
+    if (!ctx || !count) return LBM_ERR_ARG;
+    const Ctx& x = ctx->c;
+    if (wall < 0) *count = x.n_links;
+    else if (wall > LBM_MAX_WALLS) return LBM_ERR_ARG;
+    else *count = x.wall_begin[wall + 1] - x.wall_begin[wall];
+    return LBM_OK;
+}
+
+lbm_status lbm_set_body_force(lbm_ctx* ctx, const double g[3])
+{
+    if (!ctx || !g) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    for (int k = 0; k < 3; ++k) x.cfg.g[k] = g[k];
+    fill_params(x);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_wall_velocity(lbm_ctx* ctx, int wall, const double u[3])
+{
+    if (!ctx || !u) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (wall < 1 || wall > x.cfg.n_walls) return arg_fail(x, "wall id out of range");
+    for (int k = 0; k < 3; ++k) x.cfg.wall_u[wall - 1][k] = u[k];
+    fill_params(x);
+    return LBM_OK;
+}
+
+lbm_status lbm_init_equilibrium(lbm_ctx* ctx, const double* rho, const double* u, const double* xi, int on_host,
+                                void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (!rho || !u) return arg_fail(x, "rho and u are required");
+    GUARD(x);
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long N = nodes(x);
+    const double *dr = rho, *du = u, *dxi = xi;
+    if (on_host) {
+        const size_t need = (size_t)(4 + (xi ? x.cfg.lattice : 0)) * N * sizeof(double);
+        if (!x.stage || x.stage_bytes < need) return arg_fail(x, "host input needs the STAGE buffer");
+        double* s = (double*)x.stage;
+        CK(cudaMemcpyAsync(s, rho, N * sizeof(double), cudaMemcpyHostToDevice, st), "copy rho");
+        CK(cudaMemcpyAsync(s + N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, st), "copy u");
+        if (xi) CK(cudaMemcpyAsync(s + 4 * N, xi, (size_t)x.cfg.lattice * N * sizeof(double), cudaMemcpyHostToDevice, st),
+                   "copy xi");
+        dr = s;
+        du = s + N;
+        dxi = xi ? s + 4 * N : nullptr;
+    }
+    CK(x.ops->init_fields(x, dr, du, dxi, x.pop[x.cur], st), "init kernel");
+    if (on_host) CK(cudaStreamSynchronize(st), "synchronize");
+    x.t = 0;
+    x.prev_valid = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_import_f(lbm_ctx* ctx, const void* src, int dtype, int on_host, void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (!src || (dtype != 0 && dtype != 1)) return arg_fail(x, "src must be non-NULL and dtype 0 or 1");
+    GUARD(x);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)x.cfg.lattice * nodes(x) * (dtype == 0 ? 8 : 4);
+    const void* dsrc = src;
+    if (on_host) {
+        if (!x.stage || x.stage_bytes < bytes) return arg_fail(x, "host input needs the STAGE buffer");
+        CK(cudaMemcpyAsync(x.stage, src, bytes, cudaMemcpyHostToDevice, st), "copy f");
+        dsrc = x.stage;
+    }
+    CK(x.ops->import_f(x, dsrc, dtype, x.pop[x.cur], st), "import kernel");
+    if (on_host) CK(cudaStreamSynchronize(st), "synchronize");
+    x.t = 0;
+    x.prev_valid = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_export_f(lbm_ctx* ctx, void* dst, int dtype, int on_host, void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (!dst || (dtype != 0 && dtype != 1)) return arg_fail(x, "dst must be non-NULL and dtype 0 or 1");
+    GUARD(x);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)x.cfg.lattice * nodes(x) * (dtype == 0 ? 8 : 4);
+    void* ddst = dst;
+    if (on_host) {
+        if (!x.stage || x.stage_bytes < bytes) return arg_fail(x, "host output needs the STAGE buffer");
+        ddst = x.stage;
+    }
+    CK(x.ops->export_f(x, x.pop[x.cur], ddst, dtype, st), "export kernel");
+    if (on_host) {
+        CK(cudaMemcpyAsync(dst, x.stage, bytes, cudaMemcpyDeviceToHost, st), "copy f");
+        CK(cudaStreamSynchronize(st), "synchronize");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* ctx, int nsteps, void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (nsteps < 0) return arg_fail(x, "nsteps must be >= 0");
+    GUARD(x);
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int s = 0; s < nsteps; ++s) {
+        CK(x.ops->step(x, x.pop[x.cur], x.pop[1 - x.cur], st), "step kernel");
+        x.cur = 1 - x.cur;
+        x.t += 1;
+        x.prev_valid = true;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_step_from(lbm_ctx* ctx, const void* src, void* dst, void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (!src || !dst || src == dst) return arg_fail(x, "src and dst must be distinct non-NULL buffers");
+    if (((uintptr_t)src) % 256 || ((uintptr_t)dst) % 256) return arg_fail(x, "buffers must be 256-byte aligned");
+    GUARD(x);
+    CK(x.ops->step(x, src, dst, (cudaStream_t)stream), "step kernel");
+    return LBM_OK;
+}
+
+lbm_status lbm_save_state(lbm_ctx* ctx, void* dst, void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (!dst) return arg_fail(x, "dst is NULL");
+    GUARD(x);
+    CK(cudaMemcpyAsync(dst, x.pop[x.cur], pop_bytes(x), cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "save");
+    return LBM_OK;
+}
+
+lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, int64_t t, void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (!src || t < 0) return arg_fail(x, "src is NULL or t < 0");
+    GUARD(x);
+    CK(cudaMemcpyAsync(x.pop[x.cur], src, pop_bytes(x), cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "load");
+    x.t = t;
+    x.prev_valid = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_time(const lbm_ctx* ctx, int64_t* t)
+{
+    if (!ctx || !t) return LBM_ERR_ARG;
+    *t = ctx->c.t;
+    return LBM_OK;
+}
+
+lbm_status lbm_stress(lbm_ctx* ctx, int variant, void* sigma, void* S, void* rho, void* v, void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (variant < LBM_S1 || variant > LBM_S4) return arg_fail(x, "variant must be 1..4");
+    if (variant >= LBM_S3 && (x.t < 1 || !x.prev_valid)) {
+        x.err = "half-step stress needs at least one step since the last init/import/load";
+        return LBM_ERR_STATE;
+    }
+    GUARD(x);
+    CK(x.ops->stress(x, x.pop[x.cur], x.pop[1 - x.cur], variant, sigma, S, rho, v, (cudaStream_t)stream),
+       "stress kernel");
+    return LBM_OK;
+}
+
+lbm_status lbm_wall_force(lbm_ctx* ctx, int wall, unsigned flags, double weight, double* out, int out_on_host,
+                          void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (!out) return arg_fail(x, "out is NULL");
+    if (wall > LBM_MAX_WALLS) return arg_fail(x, "wall id out of range");
+    if (flags & ~7u) return arg_fail(x, "unknown flag");
+    if (x.t < 1) {
+        x.err = "the wall force needs at least one step";
+        return LBM_ERR_STATE;
+    }
+    GUARD(x);
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long b = wall < 0 ? 0 : x.wall_begin[wall];
+    const long long e = wall < 0 ? x.n_links : x.wall_begin[wall + 1];
+    double* part = x.scratch + SCRATCH_RED_OFF;
+    int nb = 0;
+    if (e > b) CK(x.ops->links(x, x.pop[x.cur], b, e, flags & 3u, part, &nb, st), "link kernel");
+    return finish_reduce(x, part, nb, 3, out, out_on_host != 0, weight, (flags & LBM_ACCUMULATE) != 0, st);
+}
+
+lbm_status lbm_balance(lbm_ctx* ctx, double* out, int out_on_host, void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (!out) return arg_fail(x, "out is NULL");
+    GUARD(x);
+    cudaStream_t st = (cudaStream_t)stream;
+    double* part = x.scratch + SCRATCH_RED_OFF;
+    int nb = 0;
+    CK(x.ops->balance(x, x.pop[x.cur], part, &nb, st), "balance kernel");
+    return finish_reduce(x, part, nb, 7, out, out_on_host != 0, 1.0, false, st);
+}
+
+lbm_status lbm_adjoint_buffer_bytes(const lbm_ctx* ctx, size_t* bytes)
+{
+    if (!ctx || !bytes) return LBM_ERR_ARG;
+    *bytes = round256((size_t)ctx->c.cfg.lattice * ctx->c.geo.sq * ctx->c.relem);
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_reset(lbm_ctx* ctx, void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    GUARD(x);
+    CK(launch_zero(x.scratch + SCRATCH_ADJ_OFF, (long long)ADJ_BLOCKS * 6, (cudaStream_t)stream), "zero");
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* state_prev, const void* phi_next, void* phi_out, int wall,
+                            const double* dir, double seed_weight, void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (x.cfg.lorentz || x.cfg.les) {
+        x.err = "the adjoint supports a uniform body force without LES";
+        return LBM_ERR_UNSUPPORTED;
+    }
+    if (!state_prev || !phi_out || !dir || phi_out == phi_next) return arg_fail(x, "bad adjoint buffers");
+    if (wall < 1 || wall > x.cfg.n_walls) return arg_fail(x, "wall id out of range");
+    GUARD(x);
+    CK(x.ops->adjoint(x, state_prev, phi_next, phi_out, wall, dir, seed_weight, x.scratch + SCRATCH_ADJ_OFF,
+                      (cudaStream_t)stream),
+       "adjoint kernel");
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_gradient(lbm_ctx* ctx, double* out, int out_on_host, void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (!out) return arg_fail(x, "out is NULL");
+    GUARD(x);
+    return finish_reduce(x, x.scratch + SCRATCH_ADJ_OFF, ADJ_BLOCKS, 6, out, out_on_host != 0, 1.0, false,
+                         (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------- small kernels
+namespace lbm {
+
+// warp k sums column k of the nb x W rows: lane l takes rows l, l+32, ...,
+// then a fixed shuffle tree; the order never depends on timing
+__global__ void k_reduce_rows(const double* __restrict__ partials, int nb, int W, double* __restrict__ out,
+                              double weight, int accumulate)
+{
+    const int col = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (col >= W) return;
+    double s = 0.0;
+    for (int r = lane; r < nb; r += 32) s += partials[(long long)r * W + col];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[col] = (accumulate ? out[col] : 0.0) + weight * s;
+}
+
+cudaError_t launch_reduce_rows(const double* partials, int nb, int W, double* out, double weight, int accumulate,
+                               cudaStream_t st)
+{
+    k_reduce_rows<<<1, 32 * W, 0, st>>>(partials, nb, W, out, weight, accumulate);
+    return cudaGetLastError();
+}
+
+__global__ void k_zero(double* p, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = 0.0;
+}
+
+cudaError_t launch_zero(double* p, long long n, cudaStream_t st)
+{
+    k_zero<<<64, 256, 0, st>>>(p, n);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,326 @@
+// lbm_device.cuh -- device-side lattice tables, population storage formats,
+// kernel parameters and the per-node arithmetic of the BGK relaxation with a
+// body-force term (arXiv 2512.12213, Sec. 2: Eqs. 1-5; Sec. 4: Eq. 10).
+//
+// Conventions inside the kernels
+//   * populations are held as shifted deviations d_a = f_a - w_a rho0, so the
+//     density is rho = rho0 + sum d and the momentum sum e f = c sum E d;
+//   * E_a are the integer lattice directions (e_a = c E_a); velocities are
+//     kept in units of c (W = u/c) and the body force as the velocity
+//     increment per step A = dt a / c, so c drops out of Eqs. (1)-(3):
+//       f^eq_a = rho w_a [1 + 3 E.W + 9/2 (E.W)^2 - 3/2 W.W]
+//       F_a    = C rho w_a [3 E.A - 3 W^F.A + 9 (E.W^F)(E.A)]
+//   * R is the compute type (double for FP64 storage, float otherwise).
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+// ---------------------------------------------------------------- lattices
+// D2Q9 : 0 (0,0) 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1) 5 (1,1) 6 (-1,1) 7 (-1,-1) 8 (1,-1)
+// D3Q19: 0 rest, 1/2 +-x, 3/4 +-y, 5/6 +-z, 7/8 +-(1,1,0), 9/10 +-(1,-1,0),
+//        11/12 +-(1,0,1), 13/14 +-(1,0,-1), 15/16 +-(0,1,1), 17/18 +-(0,1,-1)
+template <int Q> __host__ __device__ constexpr int EX(int a)
+{
+    constexpr int t9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    constexpr int t19[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return Q == 9 ? t9[a] : t19[a];
+}
+template <int Q> __host__ __device__ constexpr int EY(int a)
+{
+    constexpr int t9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    constexpr int t19[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return Q == 9 ? t9[a] : t19[a];
+}
+template <int Q> __host__ __device__ constexpr int EZ(int a)
+{
+    constexpr int t19[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return Q == 9 ? 0 : t19[a];
+}
+template <int Q> __host__ __device__ constexpr int OPP(int a)
+{
+    constexpr int t9[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    return Q == 9 ? t9[a] : (a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1));
+}
+// speed class: 0 rest, 1 axis, 2 diagonal
+template <int Q> __host__ __device__ constexpr int SPEED2(int a)
+{
+    return EX<Q>(a) * EX<Q>(a) + EY<Q>(a) * EY<Q>(a) + EZ<Q>(a) * EZ<Q>(a);
+}
+template <int Q> __host__ __device__ constexpr double WD(int a)
+{
+    return Q == 9 ? (SPEED2<Q>(a) == 0 ? 4.0 / 9.0 : (SPEED2<Q>(a) == 1 ? 1.0 / 9.0 : 1.0 / 36.0))
+                  : (SPEED2<Q>(a) == 0 ? 1.0 / 3.0 : (SPEED2<Q>(a) == 1 ? 1.0 / 18.0 : 1.0 / 36.0));
+}
+// the first direction of each opposite pair (the other is OPP of it)
+template <int Q> __host__ __device__ constexpr int PAIR(int k)
+{
+    constexpr int t9[4] = {1, 2, 5, 6};
+    return Q == 9 ? t9[k] : 2 * k + 1;
+}
+template <int Q> struct LatDim { static constexpr int D = (Q == 9) ? 2 : 3; static constexpr int NP = (Q - 1) / 2; };
+
+// ------------------------------------------------------- storage formats
+// Each format stores the shifted deviation d; V nodes fill one 16-byte vector.
+struct StoreF64 {
+    using T = double; using R = double; static constexpr int V = 2;
+    __device__ static R to_r(T x) { return x; }
+    __device__ static T from_r(R x) { return x; }
+};
+struct StoreF32 {
+    using T = float; using R = float; static constexpr int V = 4;
+    __device__ static R to_r(T x) { return x; }
+    __device__ static T from_r(R x) { return x; }
+};
+// binary16 holds 2^12 d: typical deviations 1e-5..1e-1 then sit in the normal
+// range of the format (min normal 6.1e-5, max 65504).
+struct StoreF16 {
+    using T = __half; using R = float; static constexpr int V = 8;
+    __device__ static R to_r(T x) { return __half2float(x) * (1.0f / 4096.0f); }
+    __device__ static T from_r(R x) { return __float2half_rn(x * 4096.0f); }
+};
+struct StoreBF16 {
+    using T = __nv_bfloat16; using R = float; static constexpr int V = 8;
+    __device__ static R to_r(T x) { return __bfloat162float(x); }
+    __device__ static T from_r(R x) { return __float2bfloat16_rn(x); }
+};
+
+template <class T, int V> union Vec16 {
+    uint4 raw;
+    T e[V];
+};
+
+// ------------------------------------------------------------- geometry
+// Populations (and node classes) use a padded pitch nxp (a multiple of 64
+// nodes, so every row starts on a 128-byte boundary for every format); the
+// planes of different directions are sq elements apart.
+struct Geo {
+    int nx, ny, nz, nxp;
+    long long sq;           // elements between direction planes (= nxp*ny*nz)
+    int periodic[3];
+    int face_wall[6];
+};
+
+// node classes (one byte per node, padded layout)
+enum : uint8_t { NC_BULK = 0, NC_BOUND = 1, NC_PAD = 0xFF };
+__host__ __device__ inline bool nc_solid(uint8_t c) { return (c & 0x80) && c != NC_PAD; }
+__host__ __device__ inline int nc_wall(uint8_t c) { return c & 0x7F; }
+__host__ __device__ inline uint8_t nc_make_solid(int wall) { return (uint8_t)(0x80 | wall); }
+
+// ----------------------------------------------------------- parameters
+enum { MODEL_A = 0, MODEL_B = 1, MODEL_C = 2, MODEL_D = 3, MODEL_E = 4 };
+constexpr int MAXW = 16;
+
+template <typename R> struct KP {
+    R rho0, tau0, om0;
+    R AG[3];          // dt g / c
+    int model;
+    int lorentz;
+    R AEB[3];         // dt sigma_e (E x B) / c   (divided by rho per node)
+    R kappa;          // dt sigma_e
+    R B[3], B2, Bp2;  // field, |B|^2, |B restricted to the simulated plane|^2
+    int maxwell;
+    R mx[19];         // Maxwell term of Eq. (10) per direction
+    R Lh[6];          // L / c^2: xx yy zz xy xz yz (zero without the Maxwell term)
+    int les;
+    R lesc;           // 18 Cs^2
+    R LW[MAXW + 1][3];  // 6 rho0 u_w / c per wall id (Ladd term = w_a E_a . LW)
+    // units for outputs
+    R c, dt, svol;    // c, dt, dx^D / dt
+};
+
+// ---------------------------------------------------- per-node quantities
+template <typename R> struct NodeM {
+    R rho, drho;
+    R u[3], A[3], v[3];   // in units of c (A: velocity increment per step)
+    R weq[3], wf[3];      // u^eq / c and u^F / c (wf = 0 for model [a])
+    R C, tau, om;
+};
+
+// moments and the per-model choices of Sec. 2; EXT enables Lorentz and LES
+template <typename R, int Q, bool EXT>
+__device__ __forceinline__ void node_macro(const R (&d)[Q], const KP<R>& p, NodeM<R>& m)
+{
+    constexpr int D = LatDim<Q>::D;
+    R drho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        drho += d[a];
+        if (EX<Q>(a) == 1) jx += d[a]; else if (EX<Q>(a) == -1) jx -= d[a];
+        if (EY<Q>(a) == 1) jy += d[a]; else if (EY<Q>(a) == -1) jy -= d[a];
+        if (D == 3) { if (EZ<Q>(a) == 1) jz += d[a]; else if (EZ<Q>(a) == -1) jz -= d[a]; }
+    }
+    const R rho = p.rho0 + drho, ir = R(1) / rho;
+    m.rho = rho;
+    m.drho = drho;
+    m.u[0] = jx * ir; m.u[1] = jy * ir; m.u[2] = (D == 3) ? jz * ir : R(0);
+    m.A[0] = p.AG[0]; m.A[1] = p.AG[1]; m.A[2] = (D == 3) ? p.AG[2] : R(0);
+    if (EXT && p.lorentz) {
+        // v = u + A/2 with A = A_g + (kappa/rho)[(v.B)B - B^2 v] in the D
+        // simulated components: (1 + k B^2) v - k B_p (B_p . v) = w, k = kappa/(2 rho),
+        // w = u + (A_g + A_EB/rho)/2, solved with the Sherman-Morrison formula.
+        R wv[3], Ag[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            Ag[k] = (k < D) ? p.AG[k] + p.AEB[k] * ir : R(0);
+            wv[k] = m.u[k] + R(0.5) * Ag[k];
+        }
+        const R kk = R(0.5) * p.kappa * ir;
+        const R Bw = p.B[0] * wv[0] + p.B[1] * wv[1] + ((D == 3) ? p.B[2] * wv[2] : R(0));
+        const R den = R(1) / (R(1) + kk * p.B2);
+        const R s = kk * Bw / (R(1) + kk * (p.B2 - p.Bp2));
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const R vk = (wv[k] + s * p.B[k]) * den;
+            m.A[k] = R(2) * (vk - m.u[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) m.v[k] = m.u[k] + R(0.5) * m.A[k];
+    const bool ueq_v = (p.model == MODEL_E);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) m.weq[k] = ueq_v ? m.v[k] : m.u[k];
+    R tau = p.tau0, om = p.om0;
+    if (EXT && p.les) {
+        // Smagorinsky: tau_eff = (tau0 + sqrt(tau0^2 + 18 Cs^2 |Pi|/(rho c^2)))/2,
+        // |Pi| = sqrt(2 Pi:Pi), Pi the non-equilibrium second moment
+        // sum e e f - (p delta + rho u^eq u^eq + L) (E_ij neglected)
+        R P[6] = {0, 0, 0, 0, 0, 0};   // xx yy zz xy xz yz, in units of c^2
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const int ex = EX<Q>(a), ey = EY<Q>(a), ez = EZ<Q>(a);
+            if (ex) P[0] += d[a];
+            if (ey) P[1] += d[a];
+            if (ez) P[2] += d[a];
+            if (ex * ey) P[3] += R(ex * ey) * d[a];
+            if (ex * ez) P[4] += R(ex * ez) * d[a];
+            if (ey * ez) P[5] += R(ey * ez) * d[a];
+        }
+        const R third = R(1) / R(3);
+        R PP = 0;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const int i = (c < 3) ? c : (c == 5 ? 1 : 0);
+            const int j = (c < 3) ? c : (c == 3 ? 1 : 2);
+            if (D == 2 && (i == 2 || j == 2)) continue;
+            R Pc = P[c] - rho * m.weq[i] * m.weq[j] - (p.maxwell ? p.Lh[c] : R(0));
+            if (i == j) Pc -= drho * third;
+            PP += (i == j ? R(1) : R(2)) * Pc * Pc;
+        }
+        tau = R(0.5) * (p.tau0 + sqrt(p.tau0 * p.tau0 + p.lesc * sqrt(R(2) * PP) * ir));
+        om = R(1) / tau;
+    }
+    m.tau = tau;
+    m.om = om;
+    m.C = (p.model == MODEL_E) ? R(1) - R(0.5) * om : R(1);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        R wf;
+        switch (p.model) {
+        case MODEL_A: wf = R(0); break;
+        case MODEL_B: wf = m.u[k]; break;
+        case MODEL_C: wf = m.u[k] + R(0.5) * tau * m.A[k]; break;
+        default: wf = m.v[k]; break;
+        }
+        m.wf[k] = wf;
+    }
+}
+
+// Eq. (2): d <- d + om (d^eq - d) + F, by opposite pairs
+template <typename R, int Q, bool EXT>
+__device__ __forceinline__ void node_relax(R (&d)[Q], const KP<R>& p, const NodeM<R>& m)
+{
+    constexpr int D = LatDim<Q>::D;
+    const R rho = m.rho, drho = m.drho, om = m.om;
+    const R usq = R(1.5) * (m.weq[0] * m.weq[0] + m.weq[1] * m.weq[1] + ((D == 3) ? m.weq[2] * m.weq[2] : R(0)));
+    const R fa = m.wf[0] * m.A[0] + m.wf[1] * m.A[1] + ((D == 3) ? m.wf[2] * m.A[2] : R(0));
+    const R Crho = m.C * rho;
+    const bool mxw = EXT && p.maxwell;
+    {   // rest population
+        constexpr R w0 = R(WD<Q>(0));
+        const R deq = w0 * (drho - rho * usq) + (mxw ? p.mx[0] : R(0));
+        const R F = -R(3) * w0 * Crho * fa;
+        d[0] = d[0] + om * (deq - d[0]) + F;
+    }
+#pragma unroll
+    for (int k = 0; k < LatDim<Q>::NP; ++k) {
+        const int a = PAIR<Q>(k), b = OPP<Q>(a);
+        const R w = R(WD<Q>(a));
+        const int ex = EX<Q>(a), ey = EY<Q>(a), ez = EZ<Q>(a);
+        const R eu = R(ex) * m.weq[0] + R(ey) * m.weq[1] + ((D == 3) ? R(ez) * m.weq[2] : R(0));
+        const R ea = R(ex) * m.A[0] + R(ey) * m.A[1] + ((D == 3) ? R(ez) * m.A[2] : R(0));
+        const R ef = R(ex) * m.wf[0] + R(ey) * m.wf[1] + ((D == 3) ? R(ez) * m.wf[2] : R(0));
+        const R sym_eq = w * (drho + rho * (R(4.5) * eu * eu - usq)) + (mxw ? p.mx[a] : R(0));
+        const R anti_eq = w * rho * R(3) * eu;
+        const R sym_f = w * Crho * (R(9) * ef * ea - R(3) * fa);
+        const R anti_f = w * Crho * R(3) * ea;
+        const R da = d[a], db = d[b];
+        d[a] = da + om * (sym_eq + anti_eq - da) + sym_f + anti_f;
+        d[b] = db + om * (sym_eq - anti_eq - db) + sym_f - anti_f;
+    }
+}
+
+// -------------------------------------------------------- addressing helpers
+__device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// one axis of a link: inside -> the coordinate; periodic -> wrapped; closed
+// face -> false and the face's wall id (constant indices only, so the
+// parameter struct never spills to local memory)
+__device__ __forceinline__ bool axis_step(int v, int n, int per, int wlo, int whi, int& out, int& wall)
+{
+    if (v >= 0 && v < n) { out = v; return true; }
+    if (per) { out = (v < 0) ? v + n : v - n; return true; }
+    wall = (v < 0) ? wlo : whi;
+    return false;
+}
+
+// Pull source of direction (ex,ey,ez) at node (x,y,z): returns true and the
+// source index (padded layout) if it is a fluid node; false and the wall id
+// if the link crosses a closed face (first axis x, y, z) or hits a solid.
+__device__ __forceinline__ bool pull_source(const Geo& g, const uint8_t* __restrict__ cls, int x, int y,
+                                            int z, int ex, int ey, int ez, long long& src, int& wall)
+{
+    int xs, ys, zs;
+    if (!axis_step(x - ex, g.nx, g.periodic[0], g.face_wall[0], g.face_wall[1], xs, wall)) return false;
+    if (!axis_step(y - ey, g.ny, g.periodic[1], g.face_wall[2], g.face_wall[3], ys, wall)) return false;
+    if (!axis_step(z - ez, g.nz, g.periodic[2], g.face_wall[4], g.face_wall[5], zs, wall)) return false;
+    src = ((long long)zs * g.ny + ys) * g.nxp + xs;
+    const uint8_t c = cls[src];
+    if (nc_solid(c)) {
+        wall = nc_wall(c);
+        return false;
+    }
+    return true;
+}
+
+// canonical post-propagation deviations at node (x,y,z) from a stored
+// post-collision state: d_b(x) = P_b(x - E_b), or P_opp(b)(x) + w_b E_b.LW
+// through a wall (halfway bounce-back with Ladd's moving-wall term)
+template <int Q, class S>
+__device__ __forceinline__ void gather_node(const typename S::T* __restrict__ P, const uint8_t* __restrict__ cls,
+                                            const Geo& g, const KP<typename S::R>& p, int x, int y, int z,
+                                            typename S::R (&d)[Q])
+{
+    using R = typename S::R;
+    const long long own = ((long long)z * g.ny + y) * g.nxp + x;
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+        long long src;
+        int wall;
+        if (b == 0) {
+            d[0] = S::to_r(P[own]);
+        } else if (pull_source(g, cls, x, y, z, EX<Q>(b), EY<Q>(b), EZ<Q>(b), src, wall)) {
+            d[b] = S::to_r(P[(long long)b * g.sq + src]);
+        } else {
+            const R w = R(WD<Q>(b));
+            const R el = R(EX<Q>(b)) * p.LW[wall][0] + R(EY<Q>(b)) * p.LW[wall][1] + R(EZ<Q>(b)) * p.LW[wall][2];
+            d[b] = S::to_r(P[(long long)OPP<Q>(b) * g.sq + own]) + w * el;
+        }
+    }
+}
+
+}  // namespace lbm

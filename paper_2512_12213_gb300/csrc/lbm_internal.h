@@ -1,0 +1,86 @@
+// lbm_internal.h -- host-side context of the C ABI and the per-storage-format
+// dispatch table of kernel launchers.
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lbm.h"
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// one boundary link (x_f, a'): node in the padded layout, direction a'
+// pointing into the wall, and the wall id (8 bytes)
+struct Link {
+    uint32_t node;
+    uint16_t dir;
+    uint16_t wall;
+};
+
+constexpr int MAX_PARTIAL_ROWS = 1024;   // block partials of one reduction
+constexpr int ADJ_BLOCKS = 2048;         // fixed grid of the adjoint kernel
+constexpr int PARTIAL_WIDTH = 8;         // doubles per partial row
+// scratch layout (doubles): [reduction rows | adjoint rows | 8 result slots]
+constexpr size_t SCRATCH_RED_OFF = 0;
+constexpr size_t SCRATCH_ADJ_OFF = (size_t)MAX_PARTIAL_ROWS * PARTIAL_WIDTH;
+constexpr size_t SCRATCH_OUT_OFF = SCRATCH_ADJ_OFF + (size_t)ADJ_BLOCKS * 6;
+constexpr size_t SCRATCH_DOUBLES = SCRATCH_OUT_OFF + 8;
+
+struct Ctx;
+
+struct Dispatch {
+    cudaError_t (*step)(const Ctx&, const void* src, void* dst, cudaStream_t);
+    cudaError_t (*import_f)(const Ctx&, const void* src, int dtype, void* dst, cudaStream_t);
+    cudaError_t (*init_fields)(const Ctx&, const double* rho, const double* u, const double* xi, void* dst,
+                               cudaStream_t);
+    cudaError_t (*export_f)(const Ctx&, const void* P, void* out, int dtype, cudaStream_t);
+    cudaError_t (*links)(const Ctx&, const void* P, long long begin, long long end, unsigned flags,
+                         double* partials, int* nblocks, cudaStream_t);
+    cudaError_t (*balance)(const Ctx&, const void* P, double* partials, int* nblocks, cudaStream_t);
+    cudaError_t (*stress)(const Ctx&, const void* cur, const void* prev, int variant, void* sig, void* S,
+                          void* rho, void* v, cudaStream_t);
+    cudaError_t (*adjoint)(const Ctx&, const void* Pprev, const void* phin, void* phio, int wall,
+                           const double* dir, double seedw, double* partials, cudaStream_t);
+};
+
+const Dispatch& dispatch_f64();
+const Dispatch& dispatch_f32();
+const Dispatch& dispatch_f16();
+const Dispatch& dispatch_bf16();
+
+cudaError_t launch_reduce_rows(const double* partials, int nb, int W, double* out, double weight, int accumulate,
+                               cudaStream_t st);
+cudaError_t launch_zero(double* p, long long n, cudaStream_t st);
+
+struct Ctx {
+    lbm_config cfg;
+    int device;
+    int ext;                 // Lorentz force, Maxwell equilibrium or LES present
+    Geo geo;
+    KP<double> kpd;
+    KP<float> kpf;
+    const Dispatch* ops;
+    size_t elem;             // bytes per stored population
+    size_t relem;            // bytes per compute value
+    void* pop[2];
+    int cur;                 // index of the buffer holding f^rel(T-1)
+    uint8_t* cls;
+    Link* links;
+    long long wall_begin[LBM_MAX_WALLS + 2];   // link ranges per wall id (sorted)
+    long long n_links;
+    double* scratch;
+    void* stage;
+    size_t stage_bytes;
+    int64_t t;
+    bool prev_valid;
+    std::string err;
+};
+
+}  // namespace lbm
+
+struct lbm_ctx {
+    lbm::Ctx c;
+};

@@ -1,0 +1,775 @@
+// lbm_kernels.cuh -- CUDA kernels of the lattice Boltzmann hot path
+// (arXiv 2512.12213) and their launchers, templated on the lattice (Q), the
+// population storage format (S) and EXT (Lorentz force, Maxwell equilibrium
+// or LES present).  Instantiated per storage format in inst_*.cu.
+#pragma once
+
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+constexpr int STEP_THREADS = 128;
+constexpr int NODE_THREADS = 256;
+constexpr int RED_THREADS = 256;
+
+// ------------------------------------------------------------ warp helpers
+template <class T> union Bits16 {
+    T t;
+    unsigned short s;
+};
+template <class T> __device__ __forceinline__ T shfl_up1(T v)
+{
+    if constexpr (sizeof(T) == 2) {
+        Bits16<T> b;
+        b.t = v;
+        b.s = (unsigned short)__shfl_up_sync(0xffffffffu, (unsigned)b.s, 1);
+        return b.t;
+    } else {
+        return __shfl_up_sync(0xffffffffu, v, 1);
+    }
+}
+template <class T> __device__ __forceinline__ T shfl_down1(T v)
+{
+    if constexpr (sizeof(T) == 2) {
+        Bits16<T> b;
+        b.t = v;
+        b.s = (unsigned short)__shfl_down_sync(0xffffffffu, (unsigned)b.s, 1);
+        return b.t;
+    } else {
+        return __shfl_down_sync(0xffffffffu, v, 1);
+    }
+}
+
+// sum W doubles over the block; thread 0 gets the totals in out[]
+template <int W>
+__device__ __forceinline__ void block_sum(double (&v)[W], double* smem /* >= W * 32 */)
+{
+#pragma unroll
+    for (int k = 0; k < W; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < W; ++k) smem[k * 32 + wid] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            double s = (lane < nw) ? smem[k * 32 + lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            v[k] = s;
+        }
+    }
+}
+
+// ------------------------------------------------- fused collide-stream step
+// One thread owns V consecutive nodes of a row (one 16-byte vector per
+// direction).  For every direction it loads the aligned vector of the pull
+// source row; the x-shifted directions take their edge element from the
+// neighbouring lane (warp shuffle), or from one scalar load at a row edge or
+// warp edge.  A chunk that holds a boundary, solid or padding node is
+// recomputed node by node with explicit bounce-back instead.
+template <int Q, class S, bool EXT>
+__global__ void __launch_bounds__(STEP_THREADS)
+k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
+       const uint8_t* __restrict__ cls, const Geo g, const KP<typename S::R> p)
+{
+    using T = typename S::T;
+    using R = typename S::R;
+    constexpr int V = S::V;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int ncx = g.nxp / V;
+    const long long nch = (long long)ncx * g.ny * g.nz;
+    const bool active = tid < nch;
+    const long long ch = active ? tid : nch - 1;
+    const int cx = (int)(ch % ncx);
+    const long long row = ch / ncx;
+    const int y = (int)(row % g.ny);
+    const int z = (int)(row / g.ny);
+    const int x0 = cx * V;
+
+    bool special;
+    {
+        const uint8_t* cp = cls + row * g.nxp + x0;
+        if constexpr (V == 8) {
+            const uint2 cv = *reinterpret_cast<const uint2*>(cp);
+            special = (cv.x | cv.y) != 0u;
+        }
+        else if constexpr (V == 4) special = *reinterpret_cast<const uint32_t*>(cp) != 0u;
+        else special = *reinterpret_cast<const uint16_t*>(cp) != 0;
+    }
+
+    T f[Q][V];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int ys = wrapi(y - EY<Q>(a), g.ny);
+        const int zs = (Q == 19) ? wrapi(z - EZ<Q>(a), g.nz) : 0;
+        const T* rp = src + (long long)a * g.sq + ((long long)zs * g.ny + ys) * g.nxp;
+        Vec16<T, V> raw;
+        raw.raw = __ldg(reinterpret_cast<const uint4*>(rp + x0));
+        if (EX<Q>(a) == 0) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) f[a][k] = raw.e[k];
+        } else if (EX<Q>(a) == 1) {
+            T left = shfl_up1(raw.e[V - 1]);
+            if (lane == 0 || cx == 0) left = rp[cx == 0 ? g.nx - 1 : x0 - 1];
+            f[a][0] = left;
+#pragma unroll
+            for (int k = 1; k < V; ++k) f[a][k] = raw.e[k - 1];
+        } else {
+            T right = shfl_down1(raw.e[0]);
+            if (lane == 31 || x0 + V >= g.nx) right = rp[x0 + V >= g.nx ? 0 : x0 + V];
+            f[a][V - 1] = right;
+#pragma unroll
+            for (int k = 0; k < V - 1; ++k) f[a][k] = raw.e[k + 1];
+        }
+    }
+    if (!active) return;
+
+    const long long base = row * g.nxp + x0;
+    if (!special) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            R d[Q];
+#pragma unroll
+            for (int a = 0; a < Q; ++a) d[a] = S::to_r(f[a][k]);
+            NodeM<R> m;
+            node_macro<R, Q, EXT>(d, p, m);
+            node_relax<R, Q, EXT>(d, p, m);
+#pragma unroll
+            for (int a = 0; a < Q; ++a) f[a][k] = S::from_r(d[a]);
+        }
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            Vec16<T, V> o;
+#pragma unroll
+            for (int k = 0; k < V; ++k) o.e[k] = f[a][k];
+            *reinterpret_cast<uint4*>(dst + (long long)a * g.sq + base) = o.raw;
+        }
+        return;
+    }
+    // chunk with a boundary, solid or padding node: node by node
+    for (int k = 0; k < V; ++k) {
+        const int x = x0 + k;
+        const uint8_t c = cls[base + k];
+        if (x >= g.nx || nc_solid(c) || c == NC_PAD) {
+#pragma unroll
+            for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + base + k] = S::from_r(R(0));
+            continue;
+        }
+        R d[Q];
+        gather_node<Q, S>(src, cls, g, p, x, y, z, d);
+        NodeM<R> m;
+        node_macro<R, Q, EXT>(d, p, m);
+        node_relax<R, Q, EXT>(d, p, m);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + base + k] = S::from_r(d[a]);
+    }
+}
+
+// ------------------------------------------ inverse propagation (import/init)
+// Stored state P with gather(P) = the given canonical f: P_a(y) = f_a(y + E_a)
+// if y + E_a is fluid, else f_opp(a)(y) - (Ladd term of opp(a)).
+struct SrcCanonD { const double* f; long long N; };
+struct SrcCanonF { const float* f; long long N; };
+struct SrcFields { const double* rho; const double* u; const double* xi; long long N; };
+
+template <int Q, typename R>
+__device__ __forceinline__ R src_value(const SrcCanonD& s, const KP<R>& p, int a, long long n)
+{
+    return R(s.f[(long long)a * s.N + n] - WD<Q>(a) * (double)p.rho0);
+}
+template <int Q, typename R>
+__device__ __forceinline__ R src_value(const SrcCanonF& s, const KP<R>& p, int a, long long n)
+{
+    return R((double)s.f[(long long)a * s.N + n] - WD<Q>(a) * (double)p.rho0);
+}
+// Eq. (1) (+ Eq. 10) evaluated in double from the fields, times (1 + xi)
+template <int Q, typename R>
+__device__ __forceinline__ R src_value(const SrcFields& s, const KP<R>& p, int a, long long n)
+{
+    const double c = (double)p.c;
+    const double rho = s.rho[n];
+    const double W[3] = {s.u[n] / c, s.u[s.N + n] / c, (Q == 19) ? s.u[2 * s.N + n] / c : 0.0};
+    const double eu = EX<Q>(a) * W[0] + EY<Q>(a) * W[1] + EZ<Q>(a) * W[2];
+    const double ww = W[0] * W[0] + W[1] * W[1] + W[2] * W[2];
+    double fe = rho * WD<Q>(a) * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * ww);
+    if (p.maxwell) fe += (double)p.mx[a];
+    if (s.xi) fe *= 1.0 + s.xi[(long long)a * s.N + n];
+    return R(fe - WD<Q>(a) * (double)p.rho0);
+}
+
+template <int Q, class S, class Src>
+__global__ void __launch_bounds__(NODE_THREADS)
+k_inverse_stream(typename S::T* __restrict__ P, const uint8_t* __restrict__ cls, const Geo g,
+                 const KP<typename S::R> p, const Src s)
+{
+    using R = typename S::R;
+    const long long N = (long long)g.nx * g.ny * g.nz;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < (long long)g.nxp * g.ny * g.nz;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % g.nxp);
+        const long long r = n / g.nxp;
+        const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+        const uint8_t c = cls[n];
+        if (x >= g.nx || nc_solid(c) || c == NC_PAD) {
+#pragma unroll
+            for (int a = 0; a < Q; ++a) P[(long long)a * g.sq + n] = S::from_r(R(0));
+            continue;
+        }
+        const long long nd = ((long long)z * g.ny + y) * g.nx + x;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            // the link from y along a is the pull source of direction opp(a) at y
+            long long srcp;
+            int wall;
+            R val;
+            if (a == 0) {
+                val = src_value<Q, R>(s, p, 0, nd);
+            } else if (pull_source(g, cls, x, y, z, EX<Q>(OPP<Q>(a)), EY<Q>(OPP<Q>(a)), EZ<Q>(OPP<Q>(a)), srcp, wall)) {
+                const int xs = (int)(srcp % g.nxp);
+                const long long rs = srcp / g.nxp;
+                const long long ns = rs * g.nx + xs;
+                val = src_value<Q, R>(s, p, a, ns);
+            } else {
+                const R el = R(EX<Q>(a)) * p.LW[wall][0] + R(EY<Q>(a)) * p.LW[wall][1] + R(EZ<Q>(a)) * p.LW[wall][2];
+                val = src_value<Q, R>(s, p, OPP<Q>(a), nd) + R(WD<Q>(a)) * el;
+            }
+            P[(long long)a * g.sq + n] = S::from_r(val);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- export
+template <int Q, class S, typename OutT>
+__global__ void __launch_bounds__(NODE_THREADS)
+k_export(const typename S::T* __restrict__ P, const uint8_t* __restrict__ cls, const Geo g,
+         const KP<typename S::R> p, OutT* __restrict__ out)
+{
+    using R = typename S::R;
+    const long long N = (long long)g.nx * g.ny * g.nz;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % g.nx);
+        const long long r = n / g.nx;
+        const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+        const uint8_t c = cls[r * g.nxp + x];
+        if (nc_solid(c)) {
+#pragma unroll
+            for (int a = 0; a < Q; ++a) out[(long long)a * N + n] = OutT(0);
+            continue;
+        }
+        R d[Q];
+        gather_node<Q, S>(P, cls, g, p, x, y, z, d);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) out[(long long)a * N + n] = OutT((double)d[a] + WD<Q>(a) * (double)p.rho0);
+    }
+}
+
+// ------------------------------------------------------------- wall force
+// One thread per boundary link (x_f, a') of one wall: fbar_a' = P_a'(x_f)
+// = f^rel(x_f, T-1), fbar_a = f_opp(a')(x_f, T) = fbar_a' - w E_a'.LW.
+// Per link (dx^D/dt) [e_a' (fbar_a' + fbar_a) + corrections], in FP64.
+template <int Q, class S>
+__global__ void __launch_bounds__(RED_THREADS)
+k_links(const typename S::T* __restrict__ P, const Link* __restrict__ links, long long begin, long long end,
+        const Geo g, const KP<typename S::R> p, unsigned flags, double* __restrict__ partials)
+{
+    __shared__ double sm[3 * 32];
+    double acc[3] = {0.0, 0.0, 0.0};
+    const double c = (double)p.c, rho0 = (double)p.rho0, svol = (double)p.svol;
+    for (long long i = begin + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < end;
+         i += (long long)gridDim.x * blockDim.x) {
+        const Link L = links[i];
+        const int a = L.dir;
+        double e[3], w = 0.0;
+        double fo = 0.0;
+        // direction tables by a small switch (a is data here)
+#pragma unroll
+        for (int b = 1; b < Q; ++b)
+            if (b == a) {
+                e[0] = EX<Q>(b); e[1] = EY<Q>(b); e[2] = EZ<Q>(b);
+                w = WD<Q>(b);
+            }
+        fo = (double)S::to_r(P[(long long)a * g.sq + L.node]) + w * rho0;
+        const double el = e[0] * (double)p.LW[L.wall][0] + e[1] * (double)p.LW[L.wall][1] + e[2] * (double)p.LW[L.wall][2];
+        const double fi = fo - w * el;        // bounced population f_opp(a')(x_f, T)
+        double mxa = 0.0;
+        if ((flags & 2u) && p.maxwell)
+#pragma unroll
+            for (int b = 1; b < Q; ++b)
+                if (b == a) mxa = (double)p.mx[b];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double ek = c * e[k];
+            double t = ek * (fo + fi);
+            if (flags & 1u) t += (double)p.LW[L.wall][k] * c / (6.0 * rho0) * (fi - fo);
+            if (flags & 2u) t -= 2.0 * ek * mxa;
+            acc[k] += svol * t;
+        }
+    }
+    block_sum<3>(acc, sm);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) partials[(long long)blockIdx.x * 3 + k] = acc[k];
+}
+
+// ---------------------------------------------------------------- balance
+template <int Q, class S, bool EXT>
+__global__ void __launch_bounds__(RED_THREADS)
+k_balance(const typename S::T* __restrict__ P, const uint8_t* __restrict__ cls, const Geo g,
+          const KP<typename S::R> p, double vol, double* __restrict__ partials)
+{
+    using R = typename S::R;
+    __shared__ double sm[7 * 32];
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    const long long N = (long long)g.nx * g.ny * g.nz;
+    const double c = (double)p.c;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % g.nx);
+        const long long r = n / g.nx;
+        const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+        if (nc_solid(cls[r * g.nxp + x])) continue;
+        R d[Q];
+        gather_node<Q, S>(P, cls, g, p, x, y, z, d);
+        double dr = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const double da = (double)d[a];
+            dr += da;
+            jx += EX<Q>(a) * da;
+            jy += EY<Q>(a) * da;
+            jz += EZ<Q>(a) * da;
+        }
+        NodeM<R> m;
+        node_macro<R, Q, EXT>(d, p, m);
+        const double rho = (double)p.rho0 + dr;
+        acc[0] += vol * rho;
+        acc[1] += vol * c * jx;
+        acc[2] += vol * c * jy;
+        acc[3] += vol * c * jz;
+        // rho a = rho (c/dt) A
+        for (int k = 0; k < 3; ++k) acc[4 + k] += vol * rho * (c / (double)p.dt) * (double)m.A[k];
+    }
+    block_sum<7>(acc, sm);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 7; ++k) partials[(long long)blockIdx.x * 7 + k] = acc[k];
+}
+
+// ----------------------------------------------------------------- stress
+// Variants 1, 2 at f(T) = gather(cur); 3, 4 at the half step between T-1 and
+// T: fbar = (cur + gather(cur))/2 with the node's state at T-1 = gather(prev).
+template <int Q, class S, bool EXT>
+__global__ void __launch_bounds__(NODE_THREADS)
+k_stress(const typename S::T* __restrict__ cur, const typename S::T* __restrict__ prev,
+         const uint8_t* __restrict__ cls, const Geo g, const KP<typename S::R> p, int variant,
+         typename S::R* __restrict__ sig, typename S::R* __restrict__ Sout, typename S::R* __restrict__ rho_out,
+         typename S::R* __restrict__ v_out)
+{
+    using R = typename S::R;
+    constexpr int D = LatDim<Q>::D;
+    constexpr int NC = (D == 3) ? 6 : 3;
+    const long long N = (long long)g.nx * g.ny * g.nz;
+    const R c = p.c, c2 = p.c * p.c;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % g.nx);
+        const long long r = n / g.nx;
+        const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+        const long long own = r * g.nxp + x;
+        R out[6] = {0, 0, 0, 0, 0, 0}, Sv[6] = {0, 0, 0, 0, 0, 0}, rr = 0, vv[3] = {0, 0, 0};
+        if (!nc_solid(cls[own])) {
+            R d[Q];
+            NodeM<R> m;
+            // component index -> (i, j)
+            constexpr int ci3[6] = {0, 1, 2, 0, 0, 1}, cj3[6] = {0, 1, 2, 1, 2, 2};
+            constexpr int ci2[3] = {0, 1, 0}, cj2[3] = {0, 1, 1};
+            if (variant <= 2) {
+                gather_node<Q, S>(cur, cls, g, p, x, y, z, d);
+                node_macro<R, Q, EXT>(d, p, m);
+                const R fac = -(R(1) - R(0.5) * m.om) * c2;
+                const bool model_a = (p.model == MODEL_A);
+#pragma unroll
+                for (int cc = 0; cc < NC; ++cc) {
+                    const int i = (D == 3) ? ci3[cc] : ci2[cc], j = (D == 3) ? cj3[cc] : cj2[cc];
+                    const int lc = (D == 3) ? cc : (cc == 2 ? 3 : cc);   // index into Lh
+                    R P2 = 0;
+#pragma unroll
+                    for (int a = 0; a < Q; ++a) {
+                        const int ea[3] = {EX<Q>(a), EY<Q>(a), EZ<Q>(a)};
+                        const int ee = ea[i] * ea[j];
+                        if (ee) P2 += R(ee) * d[a];
+                    }
+                    // cheap form of Sec. 3: sum e e f - (p delta + rho u^eq u^eq + L)
+                    R Pi = P2 - m.rho * m.weq[i] * m.weq[j] - (p.maxwell ? p.Lh[lc] : R(0));
+                    if (i == j) Pi -= m.drho / R(3);
+                    if (variant == 1) {
+                        // E_ij = tau dt rho (u^eq a + a u^eq) - tau Theta_ij, in units of c^2
+                        R E = m.tau * m.rho * (m.weq[i] * m.A[j] + m.weq[j] * m.A[i]);
+                        if (!model_a) E -= m.tau * m.C * m.rho * (m.wf[i] * m.A[j] + m.wf[j] * m.A[i]);
+                        Pi += E;
+                    }
+                    out[cc] = fac * Pi;
+                }
+                rr = m.rho;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) vv[k] = c * m.v[k];
+            } else {
+                R dn[Q];
+                gather_node<Q, S>(cur, cls, g, p, x, y, z, dn);
+                R db[Q];
+                R drb = 0, jb[3] = {0, 0, 0};
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    db[a] = R(0.5) * (S::to_r(cur[(long long)a * g.sq + own]) + dn[a]);
+                    drb += db[a];
+                    jb[0] += R(EX<Q>(a)) * db[a];
+                    jb[1] += R(EY<Q>(a)) * db[a];
+                    jb[2] += R(EZ<Q>(a)) * db[a];
+                }
+                const R rb = p.rho0 + drb;
+                const R ub[3] = {jb[0] / rb, jb[1] / rb, jb[2] / rb};
+                gather_node<Q, S>(prev, cls, g, p, x, y, z, d);
+                node_macro<R, Q, EXT>(d, p, m);
+#pragma unroll
+                for (int cc = 0; cc < NC; ++cc) {
+                    const int i = (D == 3) ? ci3[cc] : ci2[cc], j = (D == 3) ? cj3[cc] : cj2[cc];
+                    const int lc = (D == 3) ? cc : (cc == 2 ? 3 : cc);
+                    R P2 = 0;
+#pragma unroll
+                    for (int a = 0; a < Q; ++a) {
+                        const int ea[3] = {EX<Q>(a), EY<Q>(a), EZ<Q>(a)};
+                        const int ee = ea[i] * ea[j];
+                        if (ee) P2 += R(ee) * db[a];
+                    }
+                    // sum e e (fbar - f^eq(rhobar, ubar)), in units of c^2
+                    R Pi = P2 - rb * ub[i] * ub[j] - (p.maxwell ? p.Lh[lc] : R(0));
+                    if (i == j) Pi -= drb / R(3);
+                    R s = -c2 * Pi;
+                    if (variant == 4 && p.model != MODEL_A)
+                        s += R(0.5) * c2 * m.C * m.rho * (m.wf[i] * m.A[j] + m.wf[j] * m.A[i]);
+                    out[cc] = s;
+                }
+                rr = rb;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) vv[k] = c * ub[k];
+            }
+            const R nu = p.dt * c2 * (m.tau - R(0.5)) / R(3);
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc) Sv[cc] = out[cc] / (R(2) * rr * nu);
+        }
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) {
+            if (sig) sig[(long long)cc * N + n] = out[cc];
+            if (Sout) Sout[(long long)cc * N + n] = Sv[cc];
+        }
+        if (rho_out) rho_out[n] = rr;
+        if (v_out)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) v_out[(long long)k * N + n] = vv[k];
+    }
+}
+
+// ---------------------------------------------------------------- adjoint
+// One reverse step of the drag adjoint (uniform body force, any model).
+// psi_a(x) = phi_next_a(x + E_a) through a fluid link, or phi_next_opp(a)(x)
+// plus the drag seed through a link into the target wall; then
+// phi_b = (1 - om) psi_b + A_rho + E_b . B_j from the omega-weighted moments
+// of psi (see the transpose of node_macro/node_relax in the comments below).
+template <int Q, class S>
+__global__ void __launch_bounds__(RED_THREADS)
+k_adjoint(const typename S::T* __restrict__ Pprev, const typename S::R* __restrict__ phin,
+          typename S::R* __restrict__ phio, const uint8_t* __restrict__ cls, const Geo g,
+          const KP<typename S::R> p, int target, double d0, double d1, double d2, double seedw,
+          double* __restrict__ partials)
+{
+    using R = typename S::R;
+    constexpr int D = LatDim<Q>::D;
+    __shared__ double sm[6 * 32];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const long long NP = (long long)g.nxp * g.ny * g.nz;
+    const double c = (double)p.c, svol = (double)p.svol, rho0 = (double)p.rho0;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < NP; n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % g.nxp);
+        const long long r = n / g.nxp;
+        const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+        const uint8_t cl = cls[n];
+        if (x >= g.nx || nc_solid(cl) || cl == NC_PAD) {
+#pragma unroll
+            for (int a = 0; a < Q; ++a) phio[(long long)a * g.sq + n] = R(0);
+            continue;
+        }
+        // transpose of propagation and drag seeds
+        R psi[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            long long dn;
+            int wall;
+            if (a == 0) {
+                psi[0] = phin ? phin[n] : R(0);
+            } else if (pull_source(g, cls, x, y, z, EX<Q>(OPP<Q>(a)), EY<Q>(OPP<Q>(a)), EZ<Q>(OPP<Q>(a)), dn, wall)) {
+                psi[a] = phin ? phin[(long long)a * g.sq + dn] : R(0);
+            } else {
+                const double back = phin ? (double)phin[(long long)OPP<Q>(a) * g.sq + n] : 0.0;
+                double ps = back;
+                if (wall == target) {
+                    const double de = c * (d0 * EX<Q>(a) + d1 * EY<Q>(a) + d2 * EZ<Q>(a));
+                    ps += seedw * 2.0 * svol * de;
+                    // u_w enters f(t+1) and F_t through the Ladd term -6 w rho0 E.u_w / c
+                    const double gl = -6.0 * WD<Q>(a) * rho0 / c * (back + seedw * svol * de);
+                    acc[3] += gl * EX<Q>(a);
+                    acc[4] += gl * EY<Q>(a);
+                    acc[5] += gl * EZ<Q>(a);
+                }
+                psi[a] = R(ps);
+            }
+        }
+        // forward node state at f(t)
+        R d[Q];
+        gather_node<Q, S>(Pprev, cls, g, p, x, y, z, d);
+        NodeM<R> m;
+        node_macro<R, Q, false>(d, p, m);
+        // omega-weighted moments of psi
+        R s0 = 0, s1[3] = {0, 0, 0}, s2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const R wp = R(WD<Q>(a)) * psi[a];
+            const int e[3] = {EX<Q>(a), EY<Q>(a), EZ<Q>(a)};
+            s0 += wp;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                if (e[i]) s1[i] += R(e[i]) * wp;
+#pragma unroll
+                for (int j = 0; j < D; ++j)
+                    if (e[i] * e[j]) s2[i][j] += R(e[i] * e[j]) * wp;
+            }
+        }
+        // sum psi f^eq(rho, W) = rho Psi_e(W); grad_W = rho (3 s1 + 9 s2 W - 3 s0 W)
+        // sum psi F = C rho Psi_f; grad_Wf = C rho (9 s2 A - 3 s0 A); grad_A = C rho (3 s1 - 3 s0 Wf + 9 s2 Wf)
+        const R* W = m.weq;
+        const R* Wf = m.wf;
+        const R* A = m.A;
+        R s2W[3] = {0, 0, 0}, s2A[3] = {0, 0, 0}, s2F[3] = {0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                s2W[i] += s2[i][j] * W[j];
+                s2A[i] += s2[i][j] * A[j];
+                s2F[i] += s2[i][j] * Wf[j];
+            }
+        R WW = 0, s1W = 0, WsW = 0, s1A = 0, FA = 0, FsA = 0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            WW += W[i] * W[i];
+            s1W += s1[i] * W[i];
+            WsW += W[i] * s2W[i];
+            s1A += s1[i] * A[i];
+            FA += Wf[i] * A[i];
+            FsA += Wf[i] * s2A[i];
+        }
+        const bool ma = (p.model == MODEL_A);
+        const R Psi_e = s0 + R(3) * s1W + R(4.5) * WsW - R(1.5) * WW * s0;
+        const R Psi_f = ma ? R(3) * s1A : (R(3) * s1A - R(3) * FA * s0 + R(9) * FsA);
+        R Ge[3], Gf[3], GA[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            Ge[i] = (i < D) ? m.om * m.rho * (R(3) * s1[i] + R(9) * s2W[i] - R(3) * s0 * W[i]) : R(0);
+            Gf[i] = (i < D && !ma) ? m.C * m.rho * (R(9) * s2A[i] - R(3) * s0 * A[i]) : R(0);
+            GA[i] = (i < D) ? (ma ? m.C * m.rho * R(3) * s1[i]
+                                  : m.C * m.rho * (R(3) * s1[i] - R(3) * s0 * Wf[i] + R(9) * s2F[i]))
+                            : R(0);
+        }
+        // W and Wf move with u = j/rho: d/dj = I/rho, d/drho = -u/rho
+        const R ir = R(1) / m.rho;
+        R Arho = m.om * Psi_e + m.C * Psi_f;
+        R Bj[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            Arho -= (Ge[i] + Gf[i]) * m.u[i] * ir;
+            Bj[i] = (Ge[i] + Gf[i]) * ir;
+        }
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+            const R phib = (R(1) - m.om) * psi[b] + Arho + R(EX<Q>(b)) * Bj[0] + R(EY<Q>(b)) * Bj[1] +
+                           R(EZ<Q>(b)) * Bj[2];
+            phio[(long long)b * g.sq + n] = phib;
+        }
+        // dJ/dg: A = dt g / c; W^eq moves with A/2 for [e]; W^F with tau/2 ([c]) or 1/2 ([d], [e])
+        const R keq = (p.model == MODEL_E) ? R(0.5) : R(0);
+        const R kf = (p.model == MODEL_C) ? R(0.5) * m.tau : ((p.model == MODEL_D || p.model == MODEL_E) ? R(0.5) : R(0));
+        const double sc = (double)p.dt / c;
+#pragma unroll
+        for (int i = 0; i < D; ++i) acc[i] += sc * (double)(GA[i] + keq * Ge[i] + kf * Gf[i]);
+    }
+    block_sum<6>(acc, sm);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 6; ++k) partials[(long long)blockIdx.x * 6 + k] += acc[k];
+}
+
+// ================================================================ launchers
+inline int grid_for(long long n, int threads, long long cap)
+{
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+template <class S> inline const KP<typename S::R>& kp_of(const Ctx& c)
+{
+    if constexpr (sizeof(typename S::R) == 8) return c.kpd;
+    else return c.kpf;
+}
+
+template <int Q, class S, bool EXT>
+cudaError_t launch_step_q(const Ctx& c, const void* src, void* dst, cudaStream_t st)
+{
+    using T = typename S::T;
+    const long long nch = (long long)(c.geo.nxp / S::V) * c.geo.ny * c.geo.nz;
+    const int blocks = grid_for(nch, STEP_THREADS, 1ll << 31);
+    k_step<Q, S, EXT><<<blocks, STEP_THREADS, 0, st>>>((const T*)src, (T*)dst, c.cls, c.geo, kp_of<S>(c));
+    return cudaGetLastError();
+}
+
+template <int Q, class S>
+cudaError_t launch_step(const Ctx& c, const void* src, void* dst, cudaStream_t st)
+{
+    return c.ext ? launch_step_q<Q, S, true>(c, src, dst, st) : launch_step_q<Q, S, false>(c, src, dst, st);
+}
+
+template <int Q, class S>
+cudaError_t launch_import(const Ctx& c, const void* srcf, int dtype, void* dst, cudaStream_t st)
+{
+    using T = typename S::T;
+    const long long NP = (long long)c.geo.nxp * c.geo.ny * c.geo.nz;
+    const int blocks = grid_for(NP, NODE_THREADS, 65535ll * 16);
+    const long long N = (long long)c.geo.nx * c.geo.ny * c.geo.nz;
+    if (dtype == 0)
+        k_inverse_stream<Q, S, SrcCanonD><<<blocks, NODE_THREADS, 0, st>>>((T*)dst, c.cls, c.geo, kp_of<S>(c),
+                                                                          SrcCanonD{(const double*)srcf, N});
+    else
+        k_inverse_stream<Q, S, SrcCanonF><<<blocks, NODE_THREADS, 0, st>>>((T*)dst, c.cls, c.geo, kp_of<S>(c),
+                                                                          SrcCanonF{(const float*)srcf, N});
+    return cudaGetLastError();
+}
+
+template <int Q, class S>
+cudaError_t launch_init(const Ctx& c, const double* rho, const double* u, const double* xi, void* dst,
+                        cudaStream_t st)
+{
+    using T = typename S::T;
+    const long long NP = (long long)c.geo.nxp * c.geo.ny * c.geo.nz;
+    const int blocks = grid_for(NP, NODE_THREADS, 65535ll * 16);
+    const long long N = (long long)c.geo.nx * c.geo.ny * c.geo.nz;
+    k_inverse_stream<Q, S, SrcFields><<<blocks, NODE_THREADS, 0, st>>>((T*)dst, c.cls, c.geo, kp_of<S>(c),
+                                                                      SrcFields{rho, u, xi, N});
+    return cudaGetLastError();
+}
+
+template <int Q, class S>
+cudaError_t launch_export(const Ctx& c, const void* P, void* out, int dtype, cudaStream_t st)
+{
+    using T = typename S::T;
+    const long long N = (long long)c.geo.nx * c.geo.ny * c.geo.nz;
+    const int blocks = grid_for(N, NODE_THREADS, 65535ll * 16);
+    if (dtype == 0)
+        k_export<Q, S, double><<<blocks, NODE_THREADS, 0, st>>>((const T*)P, c.cls, c.geo, kp_of<S>(c), (double*)out);
+    else
+        k_export<Q, S, float><<<blocks, NODE_THREADS, 0, st>>>((const T*)P, c.cls, c.geo, kp_of<S>(c), (float*)out);
+    return cudaGetLastError();
+}
+
+template <int Q, class S>
+cudaError_t launch_links(const Ctx& c, const void* P, long long begin, long long end, unsigned flags,
+                         double* partials, int* nblocks, cudaStream_t st)
+{
+    using T = typename S::T;
+    const int blocks = grid_for(end - begin, RED_THREADS, MAX_PARTIAL_ROWS);
+    *nblocks = blocks;
+    k_links<Q, S><<<blocks, RED_THREADS, 0, st>>>((const T*)P, c.links, begin, end, c.geo, kp_of<S>(c), flags,
+                                                  partials);
+    return cudaGetLastError();
+}
+
+template <int Q, class S>
+cudaError_t launch_balance(const Ctx& c, const void* P, double* partials, int* nblocks, cudaStream_t st)
+{
+    using T = typename S::T;
+    const long long N = (long long)c.geo.nx * c.geo.ny * c.geo.nz;
+    const int blocks = grid_for(N, RED_THREADS, MAX_PARTIAL_ROWS);
+    *nblocks = blocks;
+    const double vol = (Q == 9) ? c.cfg.dx * c.cfg.dx : c.cfg.dx * c.cfg.dx * c.cfg.dx;
+    if (c.ext)
+        k_balance<Q, S, true><<<blocks, RED_THREADS, 0, st>>>((const T*)P, c.cls, c.geo, kp_of<S>(c), vol, partials);
+    else
+        k_balance<Q, S, false><<<blocks, RED_THREADS, 0, st>>>((const T*)P, c.cls, c.geo, kp_of<S>(c), vol, partials);
+    return cudaGetLastError();
+}
+
+template <int Q, class S>
+cudaError_t launch_stress(const Ctx& c, const void* cur, const void* prev, int variant, void* sig, void* Sv,
+                          void* rho, void* v, cudaStream_t st)
+{
+    using T = typename S::T;
+    using R = typename S::R;
+    const long long N = (long long)c.geo.nx * c.geo.ny * c.geo.nz;
+    const int blocks = grid_for(N, NODE_THREADS, 65535ll * 16);
+    if (c.ext)
+        k_stress<Q, S, true><<<blocks, NODE_THREADS, 0, st>>>((const T*)cur, (const T*)prev, c.cls, c.geo, kp_of<S>(c),
+                                                              variant, (R*)sig, (R*)Sv, (R*)rho, (R*)v);
+    else
+        k_stress<Q, S, false><<<blocks, NODE_THREADS, 0, st>>>((const T*)cur, (const T*)prev, c.cls, c.geo, kp_of<S>(c),
+                                                               variant, (R*)sig, (R*)Sv, (R*)rho, (R*)v);
+    return cudaGetLastError();
+}
+
+template <int Q, class S>
+cudaError_t launch_adjoint(const Ctx& c, const void* Pprev, const void* phin, void* phio, int wall,
+                           const double* dir, double seedw, double* partials, cudaStream_t st)
+{
+    using T = typename S::T;
+    using R = typename S::R;
+    k_adjoint<Q, S><<<ADJ_BLOCKS, RED_THREADS, 0, st>>>((const T*)Pprev, (const R*)phin, (R*)phio, c.cls, c.geo,
+                                                        kp_of<S>(c), wall, dir[0], dir[1], dir[2], seedw, partials);
+    return cudaGetLastError();
+}
+
+template <class S> Dispatch make_dispatch()
+{
+    Dispatch d;
+    d.step = [](const Ctx& c, const void* s, void* t, cudaStream_t st) {
+        return c.cfg.lattice == 9 ? launch_step<9, S>(c, s, t, st) : launch_step<19, S>(c, s, t, st);
+    };
+    d.import_f = [](const Ctx& c, const void* s, int dt, void* t, cudaStream_t st) {
+        return c.cfg.lattice == 9 ? launch_import<9, S>(c, s, dt, t, st) : launch_import<19, S>(c, s, dt, t, st);
+    };
+    d.init_fields = [](const Ctx& c, const double* r, const double* u, const double* xi, void* t, cudaStream_t st) {
+        return c.cfg.lattice == 9 ? launch_init<9, S>(c, r, u, xi, t, st) : launch_init<19, S>(c, r, u, xi, t, st);
+    };
+    d.export_f = [](const Ctx& c, const void* P, void* o, int dt, cudaStream_t st) {
+        return c.cfg.lattice == 9 ? launch_export<9, S>(c, P, o, dt, st) : launch_export<19, S>(c, P, o, dt, st);
+    };
+    d.links = [](const Ctx& c, const void* P, long long b, long long e, unsigned fl, double* pa, int* nb,
+                 cudaStream_t st) {
+        return c.cfg.lattice == 9 ? launch_links<9, S>(c, P, b, e, fl, pa, nb, st)
+                                  : launch_links<19, S>(c, P, b, e, fl, pa, nb, st);
+    };
+    d.balance = [](const Ctx& c, const void* P, double* pa, int* nb, cudaStream_t st) {
+        return c.cfg.lattice == 9 ? launch_balance<9, S>(c, P, pa, nb, st) : launch_balance<19, S>(c, P, pa, nb, st);
+    };
+    d.stress = [](const Ctx& c, const void* cu, const void* pr, int var, void* sg, void* Sv, void* rh, void* v,
+                  cudaStream_t st) {
+        return c.cfg.lattice == 9 ? launch_stress<9, S>(c, cu, pr, var, sg, Sv, rh, v, st)
+                                  : launch_stress<19, S>(c, cu, pr, var, sg, Sv, rh, v, st);
+    };
+    d.adjoint = [](const Ctx& c, const void* Pp, const void* pn, void* po, int w, const double* dir, double sw,
+                   double* pa, cudaStream_t st) {
+        return c.cfg.lattice == 9 ? launch_adjoint<9, S>(c, Pp, pn, po, w, dir, sw, pa, st)
+                                  : launch_adjoint<19, S>(c, Pp, pn, po, w, dir, sw, pa, st);
+    };
+    return d;
+}
+
+}  // namespace lbm

@@ -1,0 +1,82 @@
+"""Synthetic workloads shaped like the flows the paper (arXiv 2512.12213)
+analyses: a body-force-driven channel, a Hartmann-Couette channel with an
+imposed field, flow past a sphere in a periodic box, a lid-driven cavity with
+Smagorinsky LES, and cylinder/sphere drag for the adjoint.  Each returns a
+configuration dict (keys of ``lbm.make_config``; the oracle accepts the same
+keys with ``q`` for ``lattice``) and a uint8 wall-id mask (nz, ny, nx).
+
+No dataset is involved: geometry and parameters are generated here.
+"""
+from __future__ import annotations
+
+import math
+
+from . import inputs
+
+
+def poiseuille(nx=64, ny=32, tau=0.8, g=1e-6, model="d", storage="f64"):
+    """D2Q9 channel, periodic in x, halfway walls below y = 0 (id 1) and above
+    y = ny - 1 (id 2), uniform body force along x."""
+    cfg = dict(lattice=9, nx=nx, ny=ny, nz=1, periodic=(1, 0, 1), tau=tau, force_model=model,
+               g=(g, 0.0, 0.0), storage=storage, wall_u=((0, 0, 0), (0, 0, 0)), face_wall=(1, 1, 1, 2, 1, 1))
+    return cfg, inputs.empty_mask(nx, ny)
+
+
+def hartmann(nx=256, ny=128, tau=0.8, Ha=10.0, Uw=0.05, B0=0.05, model="e", maxwell=0, storage="f64"):
+    """D2Q9 channel of half-width H = ny/2 in a transverse imposed field
+    B = (0, B0, 0) at Hartmann number Ha = B0 H sqrt(sigma_e/(rho nu)), low-Rm
+    Lorentz force, top wall moving at Uw; the body force makes the
+    pressure-driven part peak at 0.05."""
+    H = ny / 2
+    nu = (tau - 0.5) / 3
+    K = nu * Ha ** 2 / H ** 2
+    g = 0.05 * K / (1 - 1 / math.cosh(Ha))
+    cfg = dict(lattice=9, nx=nx, ny=ny, nz=1, periodic=(1, 0, 1), tau=tau, force_model=model, g=(g, 0.0, 0.0),
+               lorentz=1, B=(0.0, B0, 0.0), sigma_e=K / B0 ** 2, maxwell=maxwell, mu=1.0, storage=storage,
+               wall_u=((0, 0, 0), (Uw, 0, 0)), face_wall=(1, 1, 1, 2, 1, 1))
+    return cfg, inputs.empty_mask(nx, ny)
+
+
+# body forces for the sphere case, from a Stokes estimate with a finite-Re
+# drag factor (the measured Reynolds number is reported by the benchmark)
+SPHERE_RE = {20: dict(tau=0.68, g=4.5e-7), 100: dict(tau=0.536, g=1.9e-7)}
+
+
+def sphere(nx=256, ny=128, nz=128, radius=12, Re=20, model="e", storage="f16s", center=(64, 64, 64)):
+    """D3Q19 periodic box with a staircase sphere (wall id 1), body force
+    along x."""
+    p = SPHERE_RE[Re]
+    cfg = dict(lattice=19, nx=nx, ny=ny, nz=nz, periodic=(1, 1, 1), tau=p["tau"], force_model=model,
+               g=(p["g"], 0.0, 0.0), storage=storage, wall_u=((0, 0, 0),))
+    return cfg, inputs.sphere_mask(nx, ny, nz, center, radius)
+
+
+def cavity(n=128, lid=0.1, tau=0.55, cs=0.1, storage="f32", model="e"):
+    """D3Q19 lid-driven cube: five stationary walls (id 1) and a lid at +z
+    (id 2) moving along x; Smagorinsky LES."""
+    cfg = dict(lattice=19, nx=n, ny=n, nz=n, periodic=(0, 0, 0), tau=tau, force_model=model, les=1, cs=cs,
+               storage=storage, wall_u=((0, 0, 0), (lid, 0, 0)), face_wall=(1, 1, 1, 1, 1, 2))
+    return cfg, inputs.empty_mask(n, n, n)
+
+
+def cylinder(nx=512, ny=256, radius=20, tau=0.65, g=1.5e-6, model="e", storage="f32"):
+    """D2Q9 periodic box with a staircase circular cylinder (wall id 1),
+    body force along x."""
+    cfg = dict(lattice=9, nx=nx, ny=ny, nz=1, periodic=(1, 1, 1), tau=tau, force_model=model, g=(g, 0.0, 0.0),
+               storage=storage, wall_u=((0, 0, 0),))
+    return cfg, inputs.cylinder_mask(nx, ny, (nx / 4, ny / 2), radius)
+
+
+def sphere_small(n=128, radius=10, tau=0.65, g=2e-6, model="e", storage="f32"):
+    """D3Q19 periodic cube with a sphere, for the adjoint."""
+    cfg = dict(lattice=19, nx=n, ny=n, nz=n, periodic=(1, 1, 1), tau=tau, force_model=model, g=(g, 0.0, 0.0),
+               storage=storage, wall_u=((0, 0, 0),))
+    return cfg, inputs.sphere_mask(n, n, n, (n / 4, n / 2, n / 2), radius)
+
+
+def oracle_kwargs(cfg: dict) -> dict:
+    """The same configuration in the oracle's keyword form."""
+    out = dict(cfg)
+    out["q"] = out.pop("lattice")
+    out.pop("storage", None)
+    return out

@@ -1,0 +1,97 @@
+"""The C ABI library on a machine without a GPU: it loads, exports every
+symbol declared in include/lbm.h, and validates configurations (lbm_buffer_sizes
+touches no CUDA state)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2512_12213_gb300 import inputs, lbm, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2512_12213_gb300 import build
+    build.build()
+    return lbm.load()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(lbm.EXPORTED)
+
+
+def test_buffer_sizes(lib):
+    cfg, mask = workloads.sphere(nx=32, ny=16, nz=16, radius=4, center=(8, 8, 8), storage="f16s")
+    c = lbm.make_config(**cfg)
+    s = lbm.lbm_buffer_sizes(c, mask)
+    nxp = 64
+    assert s[lbm.BUF_POP_A] == s[lbm.BUF_POP_B] >= 19 * nxp * 16 * 16 * 2
+    assert s[lbm.BUF_NODE] >= nxp * 16 * 16
+    assert s[lbm.BUF_LINKS] > 0 and s[lbm.BUF_LINKS] % 256 == 0
+    assert all(v % 256 == 0 for v in s)
+    # the same geometry with FP64 storage needs four times the population bytes
+    c64 = lbm.make_config(**dict(cfg, storage="f64"))
+    s64 = lbm.lbm_buffer_sizes(c64, mask)
+    assert s64[lbm.BUF_POP_A] >= 4 * 19 * nxp * 16 * 16 * 2
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("lattice", 7, "lattice"), ("nx", 0, "nx"), ("tau", 0.5, "tau"), ("force_model", 5, "force_model"),
+    ("storage", 4, "storage"), ("dx", 0.0, "dx"), ("nz", 2, "D2Q9"),
+])
+def test_invalid_configs_rejected(lib, field, value, msg):
+    cfg, mask = workloads.poiseuille(nx=8, ny=6)
+    c = lbm.make_config(**cfg)
+    setattr(c, field, value)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_buffer_sizes(c, mask if field != "nz" else np.zeros((2, 6, 8), np.uint8))
+    assert e.value.status == 1 and msg in str(e.value)
+
+
+def test_face_wall_and_mask_ids_checked(lib):
+    cfg, mask = workloads.poiseuille(nx=8, ny=6)
+    c = lbm.make_config(**dict(cfg, face_wall=(1, 1, 1, 3, 1, 1)))
+    with pytest.raises(lbm.LbmError, match="face_wall"):
+        lbm.lbm_buffer_sizes(c, mask)
+    c = lbm.make_config(**cfg)
+    bad = mask.copy()
+    bad[0, 2, 3] = 5
+    with pytest.raises(lbm.LbmError, match="exceeds n_walls"):
+        lbm.lbm_buffer_sizes(c, bad)
+
+
+def test_maximum_size_rejected(lib):
+    # padded node count must stay below 2^31
+    c = lbm.make_config(lattice=19, nx=1300, ny=1300, nz=1300, periodic=(1, 1, 1))
+    with pytest.raises(lbm.LbmError, match="too large"):
+        lbm.lbm_buffer_sizes(c, np.zeros(1, np.uint8))
+
+
+def test_link_count_matches_oracle(lib, orc):
+    """The library's link list has exactly the oracle's boundary links."""
+    for q in (9, 19):
+        if q == 9:
+            mask = inputs.random_solids(23, 11, 1, 0.15, n_walls=3, seed=3)
+            cfg = dict(lattice=9, nx=23, ny=11, nz=1, periodic=(1, 0, 1), wall_u=((0, 0, 0),) * 3,
+                       face_wall=(1, 1, 2, 3, 1, 1))
+        else:
+            mask = inputs.random_solids(9, 8, 7, 0.1, n_walls=2, seed=4)
+            cfg = dict(lattice=19, nx=9, ny=8, nz=7, periodic=(0, 1, 0), wall_u=((0, 0, 0),) * 2,
+                       face_wall=(1, 2, 1, 1, 2, 1))
+        c = lbm.make_config(**cfg)
+        s = lbm.lbm_buffer_sizes(c, mask)
+        n_links = orc.count_links(orc.make_cfg(**workloads.oracle_kwargs(cfg)), mask)
+        assert s[lbm.BUF_LINKS] == (n_links * 8 + 255) // 256 * 256

@@ -1,0 +1,221 @@
+"""CUDA path against the FP64 CPU oracle, element by element, through the C ABI.
+
+Sizes span several 64-node rows and vector chunks with a ragged tail; every
+force model, moving walls, scattered solids, the Lorentz force, the Maxwell
+equilibrium and LES are covered; non-unit dx and dt.
+
+Tolerances: FP64 populations within 1e-12 of max|f| (the FP64 requirement);
+the FP32 compute paths within bounds derived from the storage rounding
+(relative half-ulp u of the stored deviation d ~ 1e-2 f, accumulated over
+the steps): FP32 u = 6e-8, binary16 (scaled) u = 4.9e-4, bfloat16 u = 3.9e-3.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2512_12213_gb300 import inputs, lbm, workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 2e-6, "f16s": 1e-4, "bf16s": 1e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2512_12213_gb300 import build
+    build.build()
+    lbm.load()
+    assert torch.cuda.is_available()
+
+
+def _case(name, model="e", storage="f64"):
+    if name == "d2q9":
+        nx, ny, nz = 70, 37, 1
+        mask = inputs.random_solids(nx, ny, nz, 0.06, n_walls=1, seed=21)
+        mask[mask > 0] = 3
+        cfg = dict(lattice=9, nx=nx, ny=ny, nz=nz, periodic=(1, 0, 1), dx=0.5, dt=0.2, tau=0.74,
+                   force_model=model, g=(2e-3, -1e-3, 0), storage=storage,
+                   wall_u=((0.01, 0, 0), (-0.02, 0.0, 0), (0.0, 0.0, 0)), face_wall=(1, 1, 1, 2, 1, 1))
+    elif name == "d2q9_mhd":
+        nx, ny, nz = 66, 29, 1
+        mask = inputs.cylinder_mask(nx, ny, (20.5, 14.2), 5.3, wall=3)
+        cfg = dict(lattice=9, nx=nx, ny=ny, nz=nz, periodic=(1, 0, 1), dx=1.0, dt=1.0, tau=0.81,
+                   force_model=model, g=(1e-4, 0, 0), lorentz=1, B=(0.05, 0.2, 0.03), E=(0, 0, 1e-3),
+                   sigma_e=0.3, maxwell=1, mu=0.9, storage=storage,
+                   wall_u=((0, 0, 0), (0.03, 0, 0), (0, 0, 0)), face_wall=(1, 1, 1, 2, 1, 1))
+    elif name == "d3q19":
+        nx, ny, nz = 21, 13, 11
+        mask = inputs.sphere_mask(nx, ny, nz, (9.3, 6.1, 5.2), 3.1, wall=3)
+        cfg = dict(lattice=19, nx=nx, ny=ny, nz=nz, periodic=(1, 0, 0), dx=0.5, dt=0.25, tau=0.7,
+                   force_model=model, g=(1e-2, 2e-3, -1e-3), storage=storage,
+                   wall_u=((0.0, 0.01, 0.0), (0.02, 0.0, -0.01), (0, 0, 0)), face_wall=(1, 1, 1, 2, 2, 1))
+    elif name == "d3q19_ext":
+        nx, ny, nz = 67, 9, 8
+        mask = inputs.random_solids(nx, ny, nz, 0.05, n_walls=1, seed=5)
+        mask[mask > 0] = 2
+        cfg = dict(lattice=19, nx=nx, ny=ny, nz=nz, periodic=(1, 1, 0), dx=1.0, dt=1.0, tau=0.6,
+                   force_model=model, g=(5e-5, 0, 1e-5), lorentz=1, B=(0.1, -0.05, 0.2), E=(1e-3, 0, 0),
+                   sigma_e=0.4, maxwell=1, mu=1.2, les=1, cs=0.16, storage=storage,
+                   wall_u=((0.02, 0, 0), (0, 0, 0)), face_wall=(1, 1, 1, 1, 1, 1))
+    elif name == "cavity":
+        n = 19
+        mask = inputs.empty_mask(n, n, n)
+        cfg = dict(lattice=19, nx=n, ny=n, nz=n, periodic=(0, 0, 0), tau=0.55, force_model=model, les=1, cs=0.1,
+                   storage=storage, wall_u=((0, 0, 0), (0.1, 0, 0)), face_wall=(1, 1, 1, 1, 1, 2))
+    elif name == "column":     # nx = 1: every chunk is mostly padding
+        mask = inputs.empty_mask(1, 24)
+        cfg = dict(lattice=9, nx=1, ny=24, nz=1, periodic=(1, 0, 1), tau=0.9, force_model=model, g=(1e-4, 0, 0),
+                   storage=storage, wall_u=((0, 0, 0), (0.05, 0, 0)), face_wall=(1, 1, 1, 2, 1, 1))
+    elif name == "single":     # one periodic node
+        mask = inputs.empty_mask(1, 1, 1)
+        cfg = dict(lattice=19, nx=1, ny=1, nz=1, periodic=(1, 1, 1), tau=0.9, force_model=model,
+                   g=(1e-3, 2e-3, 3e-3), storage=storage)
+    elif name == "wide":       # several warps per row, exact multiple of 64
+        mask = inputs.empty_mask(256, 6)
+        cfg = dict(lattice=9, nx=256, ny=6, nz=1, periodic=(1, 1, 1), tau=0.6, force_model=model,
+                   g=(1e-4, 3e-5, 0), storage=storage)
+    else:
+        raise KeyError(name)
+    return cfg, mask
+
+
+def _initial(orc, cfg, mask, amp=1e-3):
+    ocfg = orc.make_cfg(**workloads.oracle_kwargs(cfg))
+    nz, ny, nx = mask.shape
+    D = 2 if cfg["lattice"] == 9 else 3
+    rho, u = inputs.smooth_fields(nx, ny, nz, dims=D, u_amplitude=0.04, seed=8)
+    c = cfg.get("dx", 1.0) / cfg.get("dt", 1.0)
+    f0 = orc.init(ocfg, mask, rho, u * c, inputs.noise(cfg["lattice"], nx, ny, nz, amp, seed=9))
+    return ocfg, f0, rho, u * c
+
+
+def _rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300))
+
+
+CASES = [("d2q9", m) for m in "abcde"] + [("d3q19", m) for m in "abcde"] + [
+    ("d2q9_mhd", "d"), ("d2q9_mhd", "e"), ("d3q19_ext", "c"), ("d3q19_ext", "e"), ("cavity", "e"),
+    ("column", "b"), ("single", "c"), ("wide", "a")]
+
+
+@pytest.mark.parametrize("name,model", CASES)
+def test_populations_fp64(orc, name, model):
+    cfg, mask = _case(name, model)
+    ocfg, f0, _, _ = _initial(orc, cfg, mask)
+    sim = lbm.Sim(cfg, mask)
+    sim.import_f(f0)
+    # the round trip import -> export is exact up to the Ladd term's rounding
+    assert _rel(sim.export_f().cpu().numpy(), f0) < 1e-15
+    steps = 25
+    sim.step(steps)
+    f_ref = orc.run(ocfg, mask, f0, steps)
+    assert sim.time == steps
+    assert _rel(sim.export_f().cpu().numpy(), f_ref) < TOL["f64"]
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s", "bf16s"])
+@pytest.mark.parametrize("name,model", [("d2q9", "d"), ("d3q19", "e"), ("d3q19_ext", "c"), ("cavity", "e")])
+def test_populations_reduced_precision(orc, name, model, storage):
+    cfg, mask = _case(name, model, storage)
+    ocfg, f0, _, _ = _initial(orc, cfg, mask)
+    sim = lbm.Sim(cfg, mask)
+    sim.import_f(f0)
+    steps = 10
+    sim.step(steps)
+    f_ref = orc.run(ocfg, mask, f0, steps)
+    err = _rel(sim.export_f().cpu().numpy(), f_ref)
+    assert err < TOL[storage], err
+
+
+@pytest.mark.parametrize("name,model", [("d2q9", "e"), ("d2q9_mhd", "d"), ("d3q19", "c"), ("d3q19_ext", "e")])
+def test_init_equilibrium_matches_oracle(orc, name, model):
+    cfg, mask = _case(name, model)
+    ocfg, f0, rho, u = _initial(orc, cfg, mask)
+    nz, ny, nx = mask.shape
+    xi = inputs.noise(cfg["lattice"], nx, ny, nz, 1e-3, seed=9)
+    sim = lbm.Sim(cfg, mask)
+    sim.init_equilibrium(rho, u, xi)                       # host arrays
+    assert _rel(sim.export_f().cpu().numpy(), f0) < 1e-14
+    sim.init_equilibrium(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda(),
+                         torch.from_numpy(xi).cuda())      # device arrays
+    assert _rel(sim.export_f().cpu().numpy(), f0) < 1e-14
+
+
+@pytest.mark.parametrize("name,model", [("d2q9", "b"), ("d2q9_mhd", "e"), ("d3q19", "d"), ("d3q19_ext", "c"),
+                                        ("cavity", "e")])
+def test_wall_force_stress_balance_fp64(orc, name, model):
+    cfg, mask = _case(name, model)
+    ocfg, f0, _, _ = _initial(orc, cfg, mask)
+    sim = lbm.Sim(cfg, mask)
+    sim.import_f(f0)
+    K = 7
+    sim.step(K)
+    f_prev = orc.run(ocfg, mask, f0, K - 1)                # f(K-1)
+    f_K, frel = orc.step(ocfg, mask, f_prev)               # f(K), f^rel(K-1)
+    walls = sorted(set(range(1, len(cfg.get("wall_u", ())) + 1)))
+    for wall in walls + [-1]:
+        for flags in (0, 1, 2, 3):
+            Fg = sim.wall_force(wall, flags)
+            Fo = orc.wall_force(ocfg, mask, frel, f_K, wall, flags)
+            scale = max(np.abs(orc.wall_force(ocfg, mask, frel, f_K, -1, 0)).max(), 1e-30)
+            assert np.abs(Fg - Fo).max() < 1e-12 * scale, (wall, flags, Fg, Fo)
+    for variant in (1, 2, 3, 4):
+        sg, Sg, rg, vg = [x.cpu().numpy() for x in sim.stress(variant)]
+        so, So, ro, vo = orc.stress(ocfg, mask, f_K if variant <= 2 else f_prev, frel, f_K, variant)
+        assert _rel(sg, so) < 1e-10, variant
+        assert _rel(Sg, So) < 1e-10, variant
+        assert _rel(rg, ro) < 1e-14, variant
+        assert _rel(vg, vo) < 1e-11, variant
+    mg, Mg, bg = sim.balance()
+    mo, Mo, bo = orc.balance(ocfg, mask, f_K)
+    assert abs(mg - mo) < 1e-13 * mo
+    assert np.abs(Mg - Mo).max() < 1e-12 * mo * ocfg.dx / ocfg.dt
+    assert np.abs(bg - bo).max() < 1e-12 * max(np.abs(bo).max(), 1e-30)
+
+
+@pytest.mark.parametrize("name,model", [("d2q9", "a"), ("d3q19", "e"), ("d3q19_ext", "d")])
+def test_exact_momentum_balance_on_gpu(orc, name, model):
+    """Every step: F_wall = sum rho a - [M(t+dt) - M(t)]/dt (FP64 path)."""
+    cfg, mask = _case(name, model)
+    _, f0, _, _ = _initial(orc, cfg, mask)
+    sim = lbm.Sim(cfg, mask)
+    sim.import_f(f0)
+    dt = cfg.get("dt", 1.0)
+    for _ in range(5):
+        _, M0, ba = sim.balance()
+        sim.step(1)
+        _, M1, _ = sim.balance()
+        F = sim.wall_force(-1, 0)
+        ref = ba - (M1 - M0) / dt
+        scale = np.abs(M0).max() / dt + np.abs(F).max()
+        assert np.abs(F - ref).max() < 1e-13 * scale
+
+
+def test_state_errors(orc):
+    cfg, mask = _case("d2q9", "e")
+    sim = lbm.Sim(cfg, mask)
+    sim.rest()
+    with pytest.raises(lbm.LbmError) as e:
+        sim.wall_force(1)
+    assert e.value.status == 6
+    with pytest.raises(lbm.LbmError) as e:
+        sim.stress(3)
+    assert e.value.status == 6
+    sim.step(1)
+    sim.stress(3)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_step(sim.ctx, -1, sim.stream)
+    assert e.value.status == 1
+
+
+def test_all_solid_domain():
+    mask = np.ones((1, 8, 70), np.uint8)
+    cfg = dict(lattice=9, nx=70, ny=8, nz=1, periodic=(1, 1, 1), tau=0.8, force_model="e", g=(1e-3, 0, 0),
+               wall_u=((0, 0, 0),))
+    sim = lbm.Sim(cfg, mask)
+    sim.rest()
+    sim.step(3)
+    assert np.all(sim.export_f().cpu().numpy() == 0)
+    assert np.all(sim.wall_force(-1) == 0)
+    m, M, b = sim.balance()
+    assert m == 0 and np.all(M == 0) and np.all(b == 0)
