@@ -1,0 +1,448 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 lattice Boltzmann hot path (arXiv 2512.12213).
+
+Headline (value): D3Q19 flow past a sphere, 256 x 128 x 128 nodes, periodic
+box, body force, populations stored as shifted binary16 (FP32 arithmetic);
+one step = the fused collide-stream kernel plus the FP64 momentum-exchange
+drag on the sphere (link kernel + fixed-order reduction), every step.
+Reported beside it on the same workload: FP64, FP32 and bfloat16 storage
+with their drag error against FP64; the FP32 D3Q19 lid-driven LES cavity;
+adjoint throughput on the 2-D cylinder; an end-to-end run through host
+buffers; the roofline of the fused step kernel; the CPU oracle.
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per rank, launched by torchrun) and
+reports their summed throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D3Q19 MLUPS & % HBM roofline, mixed vs FP64 at stated drag error; adjoint MLUPS"
+WORKLOAD = "D3Q19 sphere r=12 in 256x128x128 periodic box, Re~20, body force, model [e], halfway bounce-back"
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--drag-steps", type=int, default=2000)
+    p.add_argument("--no-extras", action="store_true", help="headline only")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2512_12213_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(key):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+        e = d.get(key)
+        if e and e.get("source_sha") == source_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """Samples SM clock and throttle reasons with nvidia-smi while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.samples, self.proc, self.active = index, [], None, False
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            if self.active:
+                self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 3 + i and s[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# --------------------------------------------------------------- our arm
+def bytes_per_node(Q, storage):
+    s = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}[storage]
+    return 2 * Q * s + 1      # read + write every population, plus the node-class byte
+
+
+def timed_run(torch, lbm, sim, steps, warmup, wall=1, events=True):
+    """Warm up, then time `steps` steps (fused step + drag) with CUDA events on
+    the launching stream.  Returns (total_ms, mean step-kernel ms)."""
+    st = sim.stream
+    cs = torch.cuda.current_stream()
+    hist = torch.zeros((max(steps, warmup), 3), dtype=torch.float64, device=sim.device)
+    for i in range(warmup):
+        lbm.lbm_step(sim.ctx, 1, st)
+        lbm.lbm_wall_force(sim.ctx, wall, 0, 1.0, hist[i], 0, st)
+    torch.cuda.synchronize()
+    a = [torch.cuda.Event(enable_timing=True) for _ in range(steps)] if events else []
+    b = [torch.cuda.Event(enable_timing=True) for _ in range(steps)] if events else []
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(cs)
+    for i in range(steps):
+        if events:
+            a[i].record(cs)
+        lbm.lbm_step(sim.ctx, 1, st)
+        if events:
+            b[i].record(cs)
+        lbm.lbm_wall_force(sim.ctx, wall, 0, 1.0, hist[i], 0, st)
+    t1.record(cs)
+    torch.cuda.synchronize()
+    total = t0.elapsed_time(t1)
+    kern = sum(x.elapsed_time(y) for x, y in zip(a, b)) / steps if events else None
+    return total, kern
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2512_12213_gb300 import build, lbm, workloads
+    build.build()
+    lbm.load()
+
+    clocks = Clocks(local)
+    clocks.start()
+    hbm, peak_kind = peaks()
+    out = {}
+
+    # ---- headline: sphere, shifted binary16 storage
+    cfg, mask = workloads.sphere(storage="f16s")
+    sim = lbm.Sim(cfg, mask)
+    sim.rest()
+    N = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    fluid = int((mask == 0).sum())
+    bpn = bytes_per_node(19, "f16s")
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.active = True
+    total_ms, kern_ms = timed_run(torch, lbm, sim, args.steps, args.warmup)
+    clocks.active = False
+    tmax = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.barrier()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    total_ms = float(tmax.item())
+    ms_step = total_ms / args.steps
+    value = ws * N * args.steps / (total_ms * 1e-3) / 1e6
+    achieved = N * bpn / (kern_ms * 1e-3) / 1e9
+    roof = {"kernel": "k_step<19,StoreF16,false>", "bound": "hbm", "achieved": round(achieved, 1),
+            "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "peak_source": peak_kind,
+            "bytes_per_node": bpn, "step_kernel_ms": round(kern_ms, 5),
+            "kernel_mlups": round(N / (kern_ms * 1e-3) / 1e6, 1),
+            "traffic": traffic_for("sphere256_f16s")}
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    if rank == 0 and not args.no_extras:
+        # ---- the same workload in the other storage formats, and drag error vs FP64
+        variants = {}
+        for storage, steps in (("f32", args.steps), ("bf16s", args.steps), ("f64", max(args.steps // 4, 50))):
+            c, m = workloads.sphere(storage=storage)
+            s = lbm.Sim(c, m)
+            s.rest()
+            clocks.active = True
+            t, k = timed_run(torch, lbm, s, steps, args.warmup)
+            clocks.active = False
+            bp = bytes_per_node(19, storage)
+            ach = N * bp / (k * 1e-3) / 1e9
+            variants[storage] = {"mlups": round(N * steps / (t * 1e-3) / 1e6, 1),
+                                 "kernel_mlups": round(N / (k * 1e-3) / 1e6, 1),
+                                 "achieved_gbs": round(ach, 1), "frac": round(ach / hbm, 4)}
+            s.close()
+            del s
+            torch.cuda.empty_cache()
+        variants["f16s"] = {"mlups": round(value / ws, 1), "kernel_mlups": roof["kernel_mlups"],
+                            "achieved_gbs": roof["achieved"], "frac": roof["frac"]}
+        out["storage_variants"] = variants
+        out["drag_error_vs_f64"] = drag_errors(torch, lbm, workloads, args.drag_steps)
+        out["cavity_les_f32"] = cavity_bench(torch, lbm, workloads, hbm, args)
+        out["adjoint"] = adjoint_bench(torch, lbm, workloads)
+        e2e = e2e_bench(torch, lbm, workloads, args)
+        cpu = cpu_baseline()
+    else:
+        e2e, cpu = None, None
+
+    clocks.stop()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes": N, "fluid_nodes": fluid, "storage": "f16s (shifted, x2^12)",
+                       "compute": "f32", "step": "fused collide-stream + FP64 drag reduction",
+                       "l2": "inputs larger than L2: 159 MB of populations read and 159 MB written per step",
+                       "parallelism": f"{ws} independent replica(s)"},
+            "roofline": roof, "gpu_launches": 3 * args.steps, "clocks": clocks.summary(),
+        }
+        if e2e:
+            line["e2e"] = e2e
+        if cpu:
+            line["cpu_baseline"] = cpu
+        line.update(out)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def drag_errors(torch, lbm, workloads, steps):
+    """Drag on the sphere after `steps` steps from rest (and its average over
+    the window) in each storage format, relative to FP64."""
+    res = {}
+    for storage in ("f64", "f32", "f16s", "bf16s"):
+        c, m = workloads.sphere(storage=storage)
+        s = lbm.Sim(c, m)
+        s.rest()
+        st = s.stream
+        acc = torch.zeros(3, dtype=torch.float64, device=s.device)
+        last = torch.zeros(3, dtype=torch.float64, device=s.device)
+        for i in range(steps):
+            lbm.lbm_step(s.ctx, 1, st)
+            lbm.lbm_wall_force(s.ctx, 1, lbm.ACCUMULATE, 1.0 / steps, acc, 0, st)
+        lbm.lbm_wall_force(s.ctx, 1, 0, 1.0, last, 0, st)
+        res[storage] = (float(last[0].item()), float(acc[0].item()))
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    ref_last, ref_avg = res["f64"]
+    out = {"steps": steps, "f64_drag_last": ref_last, "f64_drag_mean": ref_avg}
+    for k in ("f32", "f16s", "bf16s"):
+        out[k] = {"rel_err_last": abs(res[k][0] / ref_last - 1), "rel_err_mean": abs(res[k][1] / ref_avg - 1)}
+    return out
+
+
+def cavity_bench(torch, lbm, workloads, hbm, args):
+    n = 256
+    c, m = workloads.cavity(n=n, storage="f32")
+    s = lbm.Sim(c, m)
+    s.rest()
+    N = n ** 3
+    steps = max(args.steps // 4, 50)
+    t, k = timed_run(torch, lbm, s, steps, args.warmup, wall=2)
+    bp = bytes_per_node(19, "f32")
+    ach = N * bp / (k * 1e-3) / 1e9
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    return {"workload": "D3Q19 lid-driven cavity 256^3, lid u=0.1, tau=0.55, Smagorinsky Cs=0.1, FP32",
+            "mlups": round(N * steps / (t * 1e-3) / 1e6, 1), "kernel_mlups": round(N / (k * 1e-3) / 1e6, 1),
+            "achieved_gbs": round(ach, 1), "frac": round(ach / hbm, 4), "steps": steps}
+
+
+def adjoint_bench(torch, lbm, workloads, T=400):
+    from paper_2512_12213_gb300 import adjoint
+    c, m = workloads.cylinder(storage="f32")
+    s = lbm.Sim(c, m)
+    prob = adjoint.DragProblem(s, T, 1)
+    theta = list(c["g"]) + [0.0, 0.0, 0.0]
+    prob.forward(theta)
+    prob.backward()                      # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    prob.forward(theta)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    g = prob.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    N = c["nx"] * c["ny"]
+    # adjoint kernel alone
+    st = s.stream
+    cs = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cs)
+    phi_n, cur = None, 0
+    for i in range(T):
+        lbm.lbm_adjoint_step(s.ctx, prob.ckpt[0], phi_n, prob.phi[cur], 1, prob.d, 1.0 / T, st)
+        phi_n, cur = prob.phi[cur], 1 - cur
+    e1.record(cs)
+    torch.cuda.synchronize()
+    ka = e0.elapsed_time(e1) / T
+    s.close()
+    return {"workload": f"D2Q9 cylinder r=20 in 512x256, T={T} (sqrt(T) checkpoints), FP32 forward/adjoint",
+            "adjoint_kernel_mlups": round(N / (ka * 1e-3) / 1e6, 1),
+            "backward_mlups_with_recompute": round(N * T / (t2 - t1) / 1e6, 1),
+            "forward_mlups": round(N * T / (t1 - t0) / 1e6, 1), "grad": [float(x) for x in g]}
+
+
+def e2e_bench(torch, lbm, workloads, args):
+    """Through the C ABI with host buffers: the initial canonical state is
+    copied from pinned host memory, every step reads its drag back to the host,
+    and the final state is copied back to the host."""
+    c, m = workloads.sphere(storage="f16s")
+    s = lbm.Sim(c, m)
+    N = c["nx"] * c["ny"] * c["nz"]
+    s.rest()
+    f_host = torch.empty((19, N), dtype=torch.float32, pin_memory=True)
+    lbm.lbm_export_f(s.ctx, f_host, 1, 1, s.stream)
+    drag = torch.zeros(3, dtype=torch.float64, pin_memory=True)
+    steps = args.steps
+    st = s.stream
+    for i in range(args.warmup):
+        lbm.lbm_step(s.ctx, 1, st)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbm.lbm_import_f(s.ctx, f_host, 1, 1, st)
+    for i in range(steps):
+        lbm.lbm_step(s.ctx, 1, st)
+        lbm.lbm_wall_force(s.ctx, 1, 0, 1.0, drag, 1, st)
+    lbm.lbm_export_f(s.ctx, f_host, 1, 1, st)
+    t1 = time.perf_counter()
+    s.close()
+    state_bytes = 19 * N * 4
+    return {"value": round(N * steps / (t1 - t0) / 1e6, 1), "unit": "MLUPS",
+            "h2d_bytes_per_step": round(state_bytes / steps, 1),
+            "d2h_bytes_per_step": round((state_bytes + 24 * steps) / steps, 1)}
+
+
+def cpu_baseline(budget_s=20.0):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample of
+    the headline workload: steps of the full 256x128x128 sphere box."""
+    from oracle import oracle as orc
+    from paper_2512_12213_gb300 import workloads
+    orc.build()
+    cfg, mask = workloads.sphere(storage="f64")
+    ocfg = orc.make_cfg(**workloads.oracle_kwargs(cfg))
+    nz, ny, nx = mask.shape
+    f = orc.init(ocfg, mask, np.ones((nz, ny, nx)), np.zeros((3, nz, ny, nx)))
+    steps, t = 0, 0.0
+    t0 = time.perf_counter()
+    while t < budget_s and steps < 10:
+        f = orc.run(ocfg, mask, f, 1)
+        steps += 1
+        t = time.perf_counter() - t0
+    N = nx * ny * nz
+    return {"value": round(N * steps / t / 1e6, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} FP64 step(s) of the full 256x128x128 sphere box, single thread"}
+
+
+# --------------------------------------------------------- reference arm
+def run_reference(args):
+    """The FP64 CPU oracle as it stands on the headline workload's metric:
+    each step is one oracle step on a z-slab of the sphere box (periodic),
+    sized so the whole run stays within a few minutes."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    from paper_2512_12213_gb300 import workloads
+    orc.build()
+    cfg, mask = workloads.sphere(storage="f64")
+    total_steps = args.steps + args.warmup
+    # pick the slab thickness from a one-layer probe: ~120 s for the whole run
+    def slab(nzs):
+        m = mask[64 - nzs // 2: 64 - nzs // 2 + nzs].copy()
+        c = dict(cfg, nz=nzs)
+        oc = orc.make_cfg(**workloads.oracle_kwargs(c))
+        f = orc.init(oc, m, np.ones(m.shape), np.zeros((3,) + m.shape))
+        return oc, m, f
+    oc, m, f = slab(1)
+    t0 = time.perf_counter()
+    f = orc.run(oc, m, f, 2)
+    per_layer = (time.perf_counter() - t0) / 2
+    nzs = int(max(1, min(128, 120.0 / max(total_steps * per_layer, 1e-9))))
+    oc, m, f = slab(nzs)
+    f = orc.run(oc, m, f, args.warmup)
+    t0 = time.perf_counter()
+    f = orc.run(oc, m, f, args.steps)
+    t = time.perf_counter() - t0
+    N = m.size
+    value = N * args.steps / t / 1e6
+    sample = f"each step: one FP64 oracle step on a 256x128x{nzs} z-slab through the sphere (periodic)"
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_nodes": N},
+            "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -53,7 +53,9 @@ typedef struct orc_cfg {
     double g[3];           /* uniform body acceleration */
     int lorentz;           /* 1: a = g + (sigma_e/rho) (E + v x B) x B, imposed B, E */
     double B[3], E[3], sigma_e, mu;
-    int maxwell;           /* 1: equilibrium of Eq. (10) with the imposed B */
+    int maxwell;           /* 1: equilibrium of Eq. (10) with the imposed B (in 2-D
+                              the field must lie in the plane, B[2] = 0, for the
+                              term to carry no mass and the Maxwell stress) */
     int les;               /* 1: Smagorinsky relaxation time from f^neq */
     double cs;             /* Smagorinsky constant */
     int n_walls;           /* wall ids 1..n_walls */

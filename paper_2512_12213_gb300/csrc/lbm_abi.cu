@@ -65,6 +65,10 @@ bool validate(const lbm_config* c, const uint8_t* wid, std::string& err)
             }
     if (c->lorentz && !(c->sigma_e >= 0)) return fail("sigma_e must be >= 0");
     if (c->maxwell && !(c->mu > 0)) return fail("mu must be > 0");
+    // Eq. (10) without -c^2 B^2/6 has zero mass and the Maxwell stress as its
+    // second moment in 2-D only for a field in the simulated plane
+    if (c->maxwell && c->lattice == LBM_D2Q9 && c->B[2] != 0.0)
+        return fail("the 2-D Maxwell equilibrium needs an in-plane field (B[2] = 0)");
     if (c->les && !(c->cs >= 0)) return fail("cs must be >= 0");
     if (!wid) return fail("wall_id is NULL");
     const long long N = nodes_of(c);

@@ -95,3 +95,10 @@ def test_link_count_matches_oracle(lib, orc):
         s = lbm.lbm_buffer_sizes(c, mask)
         n_links = orc.count_links(orc.make_cfg(**workloads.oracle_kwargs(cfg)), mask)
         assert s[lbm.BUF_LINKS] == (n_links * 8 + 255) // 256 * 256
+
+
+def test_2d_maxwell_needs_in_plane_field(lib):
+    cfg, mask = workloads.hartmann(nx=8, ny=6, maxwell=1)
+    c = lbm.make_config(**dict(cfg, B=(0.0, 0.05, 0.01)))
+    with pytest.raises(lbm.LbmError, match="in-plane"):
+        lbm.lbm_buffer_sizes(c, mask)

@@ -40,7 +40,7 @@ def _case(name, model="e", storage="f64"):
         nx, ny, nz = 66, 29, 1
         mask = inputs.cylinder_mask(nx, ny, (20.5, 14.2), 5.3, wall=3)
         cfg = dict(lattice=9, nx=nx, ny=ny, nz=nz, periodic=(1, 0, 1), dx=1.0, dt=1.0, tau=0.81,
-                   force_model=model, g=(1e-4, 0, 0), lorentz=1, B=(0.05, 0.2, 0.03), E=(0, 0, 1e-3),
+                   force_model=model, g=(1e-4, 0, 0), lorentz=1, B=(0.05, 0.2, 0.0), E=(0, 0, 1e-3),
                    sigma_e=0.3, maxwell=1, mu=0.9, storage=storage,
                    wall_u=((0, 0, 0), (0.03, 0, 0), (0, 0, 0)), face_wall=(1, 1, 1, 2, 1, 1))
     elif name == "d3q19":
