@@ -46,6 +46,10 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--drag-steps", type=int, default=2000)
     p.add_argument("--no-extras", action="store_true", help="headline only")
+    p.add_argument("--storage", default="f16s", choices=["f64", "f32", "f16s", "bf16s"],
+                   help="storage of the headline run (profiling)")
+    p.add_argument("--workload", default="sphere", choices=["sphere", "cavity"],
+                   help="headline workload (profiling): sphere 256x128x128 or cavity 256^3 LES")
     return p.parse_args()
 
 
@@ -185,17 +189,22 @@ def run_ours(args):
     out = {}
 
     # ---- headline: sphere, shifted binary16 storage
-    cfg, mask = workloads.sphere(storage="f16s")
+    if args.workload == "sphere":
+        cfg, mask = workloads.sphere(storage=args.storage)
+        hwall = 1
+    else:
+        cfg, mask = workloads.cavity(n=256, storage=args.storage)
+        hwall = 2
     sim = lbm.Sim(cfg, mask)
     sim.rest()
     N = cfg["nx"] * cfg["ny"] * cfg["nz"]
     fluid = int((mask == 0).sum())
-    bpn = bytes_per_node(19, "f16s")
+    bpn = bytes_per_node(19, args.storage)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.active = True
-    total_ms, kern_ms = timed_run(torch, lbm, sim, args.steps, args.warmup)
+    total_ms, kern_ms = timed_run(torch, lbm, sim, args.steps, args.warmup, wall=hwall)
     clocks.active = False
     tmax = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
     if ws > 1:
@@ -205,16 +214,17 @@ def run_ours(args):
     ms_step = total_ms / args.steps
     value = ws * N * args.steps / (total_ms * 1e-3) / 1e6
     achieved = N * bpn / (kern_ms * 1e-3) / 1e9
-    roof = {"kernel": "k_step<19,StoreF16,false>", "bound": "hbm", "achieved": round(achieved, 1),
+    kname = {"f64": "StoreF64", "f32": "StoreF32", "f16s": "StoreF16", "bf16s": "StoreBF16"}[args.storage]
+    roof = {"kernel": f"k_step<19,{kname},{'true' if cfg.get('les') else 'false'}>", "bound": "hbm", "achieved": round(achieved, 1),
             "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "peak_source": peak_kind,
             "bytes_per_node": bpn, "step_kernel_ms": round(kern_ms, 5),
             "kernel_mlups": round(N / (kern_ms * 1e-3) / 1e6, 1),
-            "traffic": traffic_for("sphere256_f16s")}
+            "traffic": traffic_for(f"{args.workload}256_{args.storage}")}
     sim.close()
     del sim
     torch.cuda.empty_cache()
 
-    if rank == 0 and not args.no_extras:
+    if rank == 0 and not args.no_extras and args.workload == "sphere" and args.storage == "f16s":
         # ---- the same workload in the other storage formats, and drag error vs FP64
         variants = {}
         for storage, steps in (("f32", args.steps), ("bf16s", args.steps), ("f64", max(args.steps // 4, 50))):
@@ -249,9 +259,11 @@ def run_ours(args):
             "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nodes": N, "fluid_nodes": fluid, "storage": "f16s (shifted, x2^12)",
+            "config": {"workload": WORKLOAD if args.workload == "sphere" else "D3Q19 LES cavity 256^3",
+                       "nodes": N, "fluid_nodes": fluid, "storage": args.storage,
                        "compute": "f32", "step": "fused collide-stream + FP64 drag reduction",
-                       "l2": "inputs larger than L2: 159 MB of populations read and 159 MB written per step",
+                       "l2": f"inputs larger than L2: {N * (bpn - 1) / 2 / 1e6:.0f} MB of populations read and the same "
+                  "written per step",
                        "parallelism": f"{ws} independent replica(s)"},
             "roofline": roof, "gpu_launches": 3 * args.steps, "clocks": clocks.summary(),
         }

@@ -198,6 +198,12 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, int64_t t, void* stream
 /* Current time T. */
 lbm_status lbm_time(const lbm_ctx* ctx, int64_t* t);
 
+/* Error flags raised by kernels since the last clear (synchronises the
+ * stream): bit 0 = a bounded wait for staged input expired (the step was not
+ * completed; the state is invalid).  clear != 0 resets them. */
+#define LBM_DEVICE_WAIT_TIMEOUT 1u
+lbm_status lbm_device_status(lbm_ctx* ctx, uint32_t* flags, int clear, void* stream);
+
 /* Stress tensor (Eqs. 8-9, 27-30).  Outputs are dense device arrays in the
  * compute precision (double for F64 storage, else float); any may be NULL:
  * sigma[ncomp][N], S[ncomp][N], rho[N], v[3][N].  S1/S2 use f(T) and report

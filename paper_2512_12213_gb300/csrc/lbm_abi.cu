@@ -232,6 +232,23 @@ void fill_params(Ctx& x)
     cast_kp(p, x.kpf);
 }
 
+// rows per tile of the shared-memory staged step: a stage of about 40 KB so
+// that two stages of two blocks fit one SM; 0 when even one row per stage
+// does not fit (the register-tiled kernel is used then)
+void choose_tile(Ctx& x)
+{
+    const size_t Q = x.cfg.lattice, nxp = x.geo.nxp;
+    const size_t per_row = Q * nxp * x.elem + nxp;
+    int R = (int)std::max<size_t>(1, std::min<size_t>(16, 40960 / per_row));
+    R = std::min(R, x.cfg.ny);
+    auto smem_for = [&](int r) { return 2 * ((per_row * r + 127) / 128 * 128) + 2 * sizeof(uint64_t); };
+    while (R > 1 && smem_for(R) > (size_t)x.smem_optin) --R;
+    x.tile_R = smem_for(R) <= (size_t)x.smem_optin ? R : 0;
+    x.tile_smem = x.tile_R ? smem_for(R) : 0;
+    x.tile_ntiles = x.tile_R ? ((x.cfg.ny + R - 1) / R) * x.cfg.nz : 0;
+    x.tile_blocks = 0;
+}
+
 struct DeviceGuard {
     int old = -1;
     bool ok = true;
@@ -394,11 +411,22 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
         delete h;
         return LBM_ERR_CUDA;
     }
+    x.errflag = reinterpret_cast<unsigned*>(x.scratch + SCRATCH_FLAG_OFF);
+    if (cudaDeviceGetAttribute(&x.sm_count, cudaDevAttrMultiProcessorCount, x.device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&x.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, x.device) != cudaSuccess) {
+        g_cfg_err = "cudaDeviceGetAttribute failed";
+        delete h;
+        return LBM_ERR_CUDA;
+    }
+    choose_tile(x);
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(x.cls, cls.data(), cls.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && x.n_links)
         e = cudaMemcpyAsync(x.links, links.data(), links.size() * sizeof(Link), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = launch_zero(x.scratch, (long long)SCRATCH_DOUBLES, st);
+    // solid and padding entries of both population buffers start defined
+    if (e == cudaSuccess) e = cudaMemsetAsync(x.pop[0], 0, need[LBM_BUF_POP_A], st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x.pop[1], 0, need[LBM_BUF_POP_B], st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         g_cfg_err = std::string("upload: ") + cudaGetErrorString(e);
@@ -563,6 +591,18 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, int64_t t, void* stream
     CK(cudaMemcpyAsync(x.pop[x.cur], src, pop_bytes(x), cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "load");
     x.t = t;
     x.prev_valid = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_device_status(lbm_ctx* ctx, uint32_t* flags, int clear, void* stream)
+{
+    if (!ctx || !flags) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    GUARD(x);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(flags, x.errflag, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "copy flags");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    if (clear) CK(cudaMemsetAsync(x.errflag, 0, sizeof(uint32_t), st), "clear flags");
     return LBM_OK;
 }
 

@@ -27,7 +27,8 @@ constexpr int PARTIAL_WIDTH = 8;         // doubles per partial row
 constexpr size_t SCRATCH_RED_OFF = 0;
 constexpr size_t SCRATCH_ADJ_OFF = (size_t)MAX_PARTIAL_ROWS * PARTIAL_WIDTH;
 constexpr size_t SCRATCH_OUT_OFF = SCRATCH_ADJ_OFF + (size_t)ADJ_BLOCKS * 6;
-constexpr size_t SCRATCH_DOUBLES = SCRATCH_OUT_OFF + 8;
+constexpr size_t SCRATCH_FLAG_OFF = SCRATCH_OUT_OFF + 8;   // device error flags (unsigned)
+constexpr size_t SCRATCH_DOUBLES = SCRATCH_FLAG_OFF + 8;
 
 struct Ctx;
 
@@ -77,6 +78,14 @@ struct Ctx {
     int64_t t;
     bool prev_valid;
     std::string err;
+    // shared-memory tiled step (tile_R = 0: rows too long, register kernel)
+    int sm_count;
+    int smem_optin;
+    int tile_R;
+    int tile_ntiles;
+    size_t tile_smem;
+    mutable int tile_blocks;
+    unsigned* errflag;
 };
 
 }  // namespace lbm

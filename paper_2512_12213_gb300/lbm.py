@@ -76,6 +76,7 @@ _SIGS = {
     "lbm_save_state": [_vp, _vp, _vp],
     "lbm_load_state": [_vp, _vp, ctypes.c_int64, _vp],
     "lbm_time": [_vp, _P(ctypes.c_int64)],
+    "lbm_device_status": [_vp, _P(ctypes.c_uint32), _i, _vp],
     "lbm_stress": [_vp, _i, _vp, _vp, _vp, _vp, _vp],
     "lbm_wall_force": [_vp, _i, ctypes.c_uint, _d, _vp, _i, _vp],
     "lbm_balance": [_vp, _vp, _i, _vp],
@@ -217,6 +218,12 @@ def lbm_time(ctx):
     return t.value
 
 
+def lbm_device_status(ctx, clear, stream):
+    f = ctypes.c_uint32()
+    _check(load().lbm_device_status(ctx, ctypes.byref(f), int(clear), stream), ctx)
+    return f.value
+
+
 def lbm_stress(ctx, variant, sigma, S, rho, v, stream):
     _check(load().lbm_stress(ctx, int(variant), _ptr(sigma), _ptr(S), _ptr(rho), _ptr(v), stream), ctx)
 
@@ -331,6 +338,9 @@ class Sim:
     @property
     def time(self):
         return lbm_time(self.ctx)
+
+    def device_status(self, clear=True):
+        return lbm_device_status(self.ctx, clear, self.stream)
 
     # diagnostics
     def stress(self, variant):

@@ -74,6 +74,11 @@ def _case(name, model="e", storage="f64"):
         mask = inputs.empty_mask(256, 6)
         cfg = dict(lattice=9, nx=256, ny=6, nz=1, periodic=(1, 1, 1), tau=0.6, force_model=model,
                    g=(1e-4, 3e-5, 0), storage=storage)
+    elif name == "ultrawide":  # rows too long for shared-memory staging: register-tiled kernel
+        nx, ny, nz = 4100, 3, 2
+        mask = inputs.random_solids(nx, ny, nz, 0.02, n_walls=1, seed=13)
+        cfg = dict(lattice=19, nx=nx, ny=ny, nz=nz, periodic=(1, 1, 0), tau=0.8, force_model=model,
+                   g=(1e-4, 0, 0), storage=storage, wall_u=((0.01, 0, 0),), face_wall=(1, 1, 1, 1, 1, 1))
     else:
         raise KeyError(name)
     return cfg, mask
@@ -95,7 +100,7 @@ def _rel(a, b):
 
 CASES = [("d2q9", m) for m in "abcde"] + [("d3q19", m) for m in "abcde"] + [
     ("d2q9_mhd", "d"), ("d2q9_mhd", "e"), ("d3q19_ext", "c"), ("d3q19_ext", "e"), ("cavity", "e"),
-    ("column", "b"), ("single", "c"), ("wide", "a")]
+    ("column", "b"), ("single", "c"), ("wide", "a"), ("ultrawide", "d")]
 
 
 @pytest.mark.parametrize("name,model", CASES)
@@ -111,10 +116,12 @@ def test_populations_fp64(orc, name, model):
     f_ref = orc.run(ocfg, mask, f0, steps)
     assert sim.time == steps
     assert _rel(sim.export_f().cpu().numpy(), f_ref) < TOL["f64"]
+    assert sim.device_status() == 0
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16s", "bf16s"])
-@pytest.mark.parametrize("name,model", [("d2q9", "d"), ("d3q19", "e"), ("d3q19_ext", "c"), ("cavity", "e")])
+@pytest.mark.parametrize("name,model", [("d2q9", "d"), ("d3q19", "e"), ("d3q19_ext", "c"), ("cavity", "e"),
+                                        ("ultrawide", "b")])
 def test_populations_reduced_precision(orc, name, model, storage):
     cfg, mask = _case(name, model, storage)
     ocfg, f0, _, _ = _initial(orc, cfg, mask)
