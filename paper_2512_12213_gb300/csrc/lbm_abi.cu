@@ -5,12 +5,14 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "lbm_internal.h"
+#include "lbm_tile.cuh"
 
 using namespace lbm;
 
@@ -230,22 +232,47 @@ void fill_params(Ctx& x)
     p.dt = c->dt;
     p.svol = (D == 3 ? c->dx * c->dx * c->dx : c->dx * c->dx) / c->dt;
     cast_kp(p, x.kpf);
+    // storage units: every term that adds to or is compared with a stored
+    // deviation scales with it (rho0 enters rho = rho0 + sum d); velocities,
+    // relaxation times and the body-force increment do not
+    const double s = (c->storage == LBM_STORE_F16S) ? 4096.0 : 1.0;
+    KP<double> q = p;
+    q.rho0 *= s;
+    q.kappa *= s;
+    for (int k = 0; k < 3; ++k) q.AEB[k] *= s;
+    for (int a = 0; a < 19; ++a) q.mx[a] *= s;
+    for (int k = 0; k < 6; ++k) q.Lh[k] *= s;
+    for (int w = 0; w <= MAXW; ++w)
+        for (int k = 0; k < 3; ++k) q.LW[w][k] *= s;
+    cast_kp(q, x.kps);
 }
 
-// rows per tile of the shared-memory staged step: a stage of about 40 KB so
-// that two stages of two blocks fit one SM; 0 when even one row per stage
-// does not fit (the register-tiled kernel is used then)
+// shape of the shared-memory staged step: R rows per tile so that each of
+// the consumer warps gets one row segment (64 nodes for FP64, 128 otherwise),
+// 2..4 stages within about 100 KB; tile_R = 0 when two one-row stages do not
+// fit in shared memory (the register-tiled kernel is used then)
 void choose_tile(Ctx& x)
 {
     const size_t Q = x.cfg.lattice, nxp = x.geo.nxp;
     const size_t per_row = Q * nxp * x.elem + nxp;
-    int R = (int)std::max<size_t>(1, std::min<size_t>(16, 40960 / per_row));
+    const size_t seg = (x.elem == 8) ? 64 : 128;
+    const size_t nseg = (nxp + seg - 1) / seg;
+    int R = (int)std::max<size_t>(1, (TILE_CWARPS + nseg - 1) / nseg);
     R = std::min(R, x.cfg.ny);
-    auto smem_for = [&](int r) { return 2 * ((per_row * r + 127) / 128 * 128) + 2 * sizeof(uint64_t); };
-    while (R > 1 && smem_for(R) > (size_t)x.smem_optin) --R;
-    x.tile_R = smem_for(R) <= (size_t)x.smem_optin ? R : 0;
-    x.tile_smem = x.tile_R ? smem_for(R) : 0;
-    x.tile_ntiles = x.tile_R ? ((x.cfg.ny + R - 1) / R) * x.cfg.nz : 0;
+    auto stage_of = [&](int r) { return (per_row * r + 127) / 128 * 128; };
+    auto smem_for = [&](int r, int n) { return n * stage_of(r) + 2 * n * sizeof(uint64_t); };
+    while (R > 1 && smem_for(R, 2) > (size_t)x.smem_optin) --R;
+    int ns = (int)std::min<size_t>(4, std::max<size_t>(2, 102400 / stage_of(R)));
+    while (ns > 2 && smem_for(R, ns) > (size_t)x.smem_optin) --ns;
+    // LBM_STEP_KERNEL=tile selects the shared-memory staged step where it fits;
+    // the register-tiled step is the default
+    const char* sel = getenv("LBM_STEP_KERNEL");
+    const bool want_tile = sel && strcmp(sel, "tile") == 0;
+    const bool fits = want_tile && smem_for(R, ns) <= (size_t)x.smem_optin;
+    x.tile_R = fits ? R : 0;
+    x.tile_stages = fits ? ns : 0;
+    x.tile_smem = fits ? smem_for(R, ns) : 0;
+    x.tile_ntiles = fits ? ((x.cfg.ny + R - 1) / R) * x.cfg.nz : 0;
     x.tile_blocks = 0;
 }
 

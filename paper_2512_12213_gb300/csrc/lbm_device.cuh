@@ -14,6 +14,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cstring>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -66,27 +67,69 @@ template <int Q> struct LatDim { static constexpr int D = (Q == 9) ? 2 : 3; stat
 
 // ------------------------------------------------------- storage formats
 // Each format stores the shifted deviation d; V nodes fill one 16-byte vector.
+// to_r/from_r convert to and from the physical deviation d; to_raw/from_raw
+// keep the storage units (d times SCALE), in which the step kernels work
+// with parameters scaled to match (see scale_params on the host).
 struct StoreF64 {
     using T = double; using R = double; static constexpr int V = 2;
+    static constexpr double SCALE = 1.0;
     __device__ static R to_r(T x) { return x; }
     __device__ static T from_r(R x) { return x; }
+    __device__ static R to_raw(T x) { return x; }
+    __device__ static T from_raw(R x) { return x; }
 };
 struct StoreF32 {
     using T = float; using R = float; static constexpr int V = 4;
+    static constexpr double SCALE = 1.0;
     __device__ static R to_r(T x) { return x; }
     __device__ static T from_r(R x) { return x; }
+    __device__ static R to_raw(T x) { return x; }
+    __device__ static T from_raw(R x) { return x; }
 };
 // binary16 holds 2^12 d: typical deviations 1e-5..1e-1 then sit in the normal
 // range of the format (min normal 6.1e-5, max 65504).
 struct StoreF16 {
     using T = __half; using R = float; static constexpr int V = 8;
+    static constexpr double SCALE = 4096.0;
     __device__ static R to_r(T x) { return __half2float(x) * (1.0f / 4096.0f); }
     __device__ static T from_r(R x) { return __float2half_rn(x * 4096.0f); }
+    __device__ static R to_raw(T x) { return __half2float(x); }
+    __device__ static T from_raw(R x) { return __float2half_rn(x); }
+    // two packed values <-> two floats
+    __device__ static float2 unpack2(uint32_t w)
+    {
+        __half2 h;
+        memcpy(&h, &w, 4);
+        return __half22float2(h);
+    }
+    __device__ static uint32_t pack2(float a, float b)
+    {
+        __half2 h = __floats2half2_rn(a, b);
+        uint32_t w;
+        memcpy(&w, &h, 4);
+        return w;
+    }
 };
 struct StoreBF16 {
     using T = __nv_bfloat16; using R = float; static constexpr int V = 8;
+    static constexpr double SCALE = 1.0;
     __device__ static R to_r(T x) { return __bfloat162float(x); }
     __device__ static T from_r(R x) { return __float2bfloat16_rn(x); }
+    __device__ static R to_raw(T x) { return __bfloat162float(x); }
+    __device__ static T from_raw(R x) { return __float2bfloat16_rn(x); }
+    __device__ static float2 unpack2(uint32_t w)
+    {
+        __nv_bfloat162 h;
+        memcpy(&h, &w, 4);
+        return __bfloat1622float2(h);
+    }
+    __device__ static uint32_t pack2(float a, float b)
+    {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        uint32_t w;
+        memcpy(&w, &h, 4);
+        return w;
+    }
 };
 
 template <class T, int V> union Vec16 {
@@ -141,23 +184,51 @@ template <typename R> struct NodeM {
     R C, tau, om;
 };
 
-// moments and the per-model choices of Sec. 2; EXT enables Lorentz and LES
+// raw moments of the shifted populations: sum d, sum E d, and (LES) sum E_i E_j d
+template <typename R> struct Mom {
+    R drho, j[3];
+    R P[6];   // xx yy zz xy xz yz, only accumulated when LES is on
+};
+
+template <typename R, int Q, bool PI>
+__device__ __forceinline__ void mom_add(Mom<R>& mo, int a, R v)
+{
+    mo.drho += v;
+    const int ex = EX<Q>(a), ey = EY<Q>(a), ez = EZ<Q>(a);
+    if (ex == 1) mo.j[0] += v; else if (ex == -1) mo.j[0] -= v;
+    if (ey == 1) mo.j[1] += v; else if (ey == -1) mo.j[1] -= v;
+    if (ez == 1) mo.j[2] += v; else if (ez == -1) mo.j[2] -= v;
+    if (PI) {
+        if (ex) mo.P[0] += v;
+        if (ey) mo.P[1] += v;
+        if (ez) mo.P[2] += v;
+        if (ex * ey) mo.P[3] += R(ex * ey) * v;
+        if (ex * ez) mo.P[4] += R(ex * ez) * v;
+        if (ey * ez) mo.P[5] += R(ey * ez) * v;
+    }
+}
+
+template <typename R> __device__ __forceinline__ void mom_zero(Mom<R>& mo)
+{
+    mo.drho = R(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) mo.j[k] = R(0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) mo.P[k] = R(0);
+}
+
+// the per-node quantities of the text after Eq. (1) and the per-model
+// choices of C, u^F and u^eq of Sec. 2, from the raw moments; EXT enables
+// the Lorentz force and LES
 template <typename R, int Q, bool EXT>
-__device__ __forceinline__ void node_macro(const R (&d)[Q], const KP<R>& p, NodeM<R>& m)
+__device__ __forceinline__ void macro_from_moments(const Mom<R>& mo, const KP<R>& p, NodeM<R>& m)
 {
     constexpr int D = LatDim<Q>::D;
-    R drho = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-    for (int a = 0; a < Q; ++a) {
-        drho += d[a];
-        if (EX<Q>(a) == 1) jx += d[a]; else if (EX<Q>(a) == -1) jx -= d[a];
-        if (EY<Q>(a) == 1) jy += d[a]; else if (EY<Q>(a) == -1) jy -= d[a];
-        if (D == 3) { if (EZ<Q>(a) == 1) jz += d[a]; else if (EZ<Q>(a) == -1) jz -= d[a]; }
-    }
+    const R drho = mo.drho;
     const R rho = p.rho0 + drho, ir = R(1) / rho;
     m.rho = rho;
     m.drho = drho;
-    m.u[0] = jx * ir; m.u[1] = jy * ir; m.u[2] = (D == 3) ? jz * ir : R(0);
+    m.u[0] = mo.j[0] * ir; m.u[1] = mo.j[1] * ir; m.u[2] = (D == 3) ? mo.j[2] * ir : R(0);
     m.A[0] = p.AG[0]; m.A[1] = p.AG[1]; m.A[2] = (D == 3) ? p.AG[2] : R(0);
     if (EXT && p.lorentz) {
         // v = u + A/2 with A = A_g + (kappa/rho)[(v.B)B - B^2 v] in the D
@@ -189,17 +260,6 @@ __device__ __forceinline__ void node_macro(const R (&d)[Q], const KP<R>& p, Node
         // Smagorinsky: tau_eff = (tau0 + sqrt(tau0^2 + 18 Cs^2 |Pi|/(rho c^2)))/2,
         // |Pi| = sqrt(2 Pi:Pi), Pi the non-equilibrium second moment
         // sum e e f - (p delta + rho u^eq u^eq + L) (E_ij neglected)
-        R P[6] = {0, 0, 0, 0, 0, 0};   // xx yy zz xy xz yz, in units of c^2
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const int ex = EX<Q>(a), ey = EY<Q>(a), ez = EZ<Q>(a);
-            if (ex) P[0] += d[a];
-            if (ey) P[1] += d[a];
-            if (ez) P[2] += d[a];
-            if (ex * ey) P[3] += R(ex * ey) * d[a];
-            if (ex * ez) P[4] += R(ex * ez) * d[a];
-            if (ey * ez) P[5] += R(ey * ez) * d[a];
-        }
         const R third = R(1) / R(3);
         R PP = 0;
 #pragma unroll
@@ -207,7 +267,7 @@ __device__ __forceinline__ void node_macro(const R (&d)[Q], const KP<R>& p, Node
             const int i = (c < 3) ? c : (c == 5 ? 1 : 0);
             const int j = (c < 3) ? c : (c == 3 ? 1 : 2);
             if (D == 2 && (i == 2 || j == 2)) continue;
-            R Pc = P[c] - rho * m.weq[i] * m.weq[j] - (p.maxwell ? p.Lh[c] : R(0));
+            R Pc = mo.P[c] - rho * m.weq[i] * m.weq[j] - (p.maxwell ? p.Lh[c] : R(0));
             if (i == j) Pc -= drho * third;
             PP += (i == j ? R(1) : R(2)) * Pc * Pc;
         }
@@ -230,37 +290,111 @@ __device__ __forceinline__ void node_macro(const R (&d)[Q], const KP<R>& p, Node
     }
 }
 
-// Eq. (2): d <- d + om (d^eq - d) + F, by opposite pairs
+// moments and per-node quantities of the populations d[Q]
+template <typename R, int Q, bool EXT>
+__device__ __forceinline__ void node_macro(const R (&d)[Q], const KP<R>& p, NodeM<R>& m)
+{
+    Mom<R> mo;
+    mom_zero(mo);
+    if (EXT && p.les) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) mom_add<R, Q, true>(mo, a, d[a]);
+    } else {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) mom_add<R, Q, false>(mo, a, d[a]);
+    }
+    macro_from_moments<R, Q, EXT>(mo, p, m);
+}
+
+// what the relaxation of one node needs, compactly
+template <typename R> struct Coef {
+    R drho, rho, om, usq, fa, Crho;
+    R weq[3], wf[3], A[3];
+};
+
+template <typename R, int Q>
+__device__ __forceinline__ void coef_of(const NodeM<R>& m, Coef<R>& c)
+{
+    constexpr int D = LatDim<Q>::D;
+    c.drho = m.drho;
+    c.rho = m.rho;
+    c.om = m.om;
+    c.usq = R(1.5) * (m.weq[0] * m.weq[0] + m.weq[1] * m.weq[1] + ((D == 3) ? m.weq[2] * m.weq[2] : R(0)));
+    c.fa = m.wf[0] * m.A[0] + m.wf[1] * m.A[1] + ((D == 3) ? m.wf[2] * m.A[2] : R(0));
+    c.Crho = m.C * m.rho;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        c.weq[k] = m.weq[k];
+        c.wf[k] = m.wf[k];
+        c.A[k] = m.A[k];
+    }
+}
+
+// Eq. (2) for the rest population
+template <typename R, int Q, bool EXT>
+__device__ __forceinline__ R relax_rest(R d0, const Coef<R>& c, const KP<R>& p)
+{
+    constexpr R w0 = R(WD<Q>(0));
+    const R deq = w0 * (c.drho - c.rho * c.usq) + ((EXT && p.maxwell) ? p.mx[0] : R(0));
+    return d0 + c.om * (deq - d0) - R(3) * w0 * c.Crho * c.fa;
+}
+
+// Eq. (2) for the opposite pair (a, opp(a)): equilibrium of Eq. (1) (+ Eq. 10)
+// split into its even and odd parts, force term of Eq. (3)
+template <typename R, int Q, bool EXT>
+__device__ __forceinline__ void relax_pair(int a, R& da, R& db, const Coef<R>& c, const KP<R>& p)
+{
+    constexpr int D = LatDim<Q>::D;
+    const R w = R(WD<Q>(a));
+    const int ex = EX<Q>(a), ey = EY<Q>(a), ez = EZ<Q>(a);
+    const R eu = R(ex) * c.weq[0] + R(ey) * c.weq[1] + ((D == 3) ? R(ez) * c.weq[2] : R(0));
+    const R ea = R(ex) * c.A[0] + R(ey) * c.A[1] + ((D == 3) ? R(ez) * c.A[2] : R(0));
+    const R ef = R(ex) * c.wf[0] + R(ey) * c.wf[1] + ((D == 3) ? R(ez) * c.wf[2] : R(0));
+    const R sym_eq = w * (c.drho + c.rho * (R(4.5) * eu * eu - c.usq)) + ((EXT && p.maxwell) ? p.mx[a] : R(0));
+    const R anti_eq = w * c.rho * R(3) * eu;
+    const R sym_f = w * c.Crho * (R(9) * ef * ea - R(3) * c.fa);
+    const R anti_f = w * c.Crho * R(3) * ea;
+    const R a0 = da, b0 = db;
+    da = a0 + c.om * (sym_eq + anti_eq - a0) + sym_f + anti_f;
+    db = b0 + c.om * (sym_eq - anti_eq - b0) + sym_f - anti_f;
+}
+
+// Eq. (2): d <- d + om (d^eq - d) + F for all populations of a node, in the
+// form d_a' = (1 - om) d_a + Ps + Pa, d_opp' = (1 - om) d_opp + Ps - Pa per
+// opposite pair, with t = E_a.W^eq, the even part
+//   Ps = om w (drho - rho 3/2 W.W) - 3 w C rho W^F.A + om 9/2 w rho t^2
+//        + 9 w C rho (E_a.W^F)(E_a.A)   (+ om Maxwell term)
+// and the odd part Pa = om 3 w rho t + 3 w C rho (E_a.A), the coefficients
+// taken once per speed class (Eqs. 1-3).
 template <typename R, int Q, bool EXT>
 __device__ __forceinline__ void node_relax(R (&d)[Q], const KP<R>& p, const NodeM<R>& m)
 {
     constexpr int D = LatDim<Q>::D;
-    const R rho = m.rho, drho = m.drho, om = m.om;
+    const R om = m.om, om1 = R(1) - om;
+    const R rho = m.rho, Crho = m.C * m.rho;
     const R usq = R(1.5) * (m.weq[0] * m.weq[0] + m.weq[1] * m.weq[1] + ((D == 3) ? m.weq[2] * m.weq[2] : R(0)));
     const R fa = m.wf[0] * m.A[0] + m.wf[1] * m.A[1] + ((D == 3) ? m.wf[2] * m.A[2] : R(0));
-    const R Crho = m.C * rho;
+    const R base = om * (m.drho - rho * usq) - R(3) * Crho * fa;   // times w
     const bool mxw = EXT && p.maxwell;
-    {   // rest population
+    {
         constexpr R w0 = R(WD<Q>(0));
-        const R deq = w0 * (drho - rho * usq) + (mxw ? p.mx[0] : R(0));
-        const R F = -R(3) * w0 * Crho * fa;
-        d[0] = d[0] + om * (deq - d[0]) + F;
+        d[0] = om1 * d[0] + w0 * base + (mxw ? om * p.mx[0] : R(0));
     }
+    const R k1 = R(4.5) * om * rho, k2 = R(9) * Crho, kl = R(3) * om * rho, kf = R(3) * Crho;
 #pragma unroll
     for (int k = 0; k < LatDim<Q>::NP; ++k) {
         const int a = PAIR<Q>(k), b = OPP<Q>(a);
         const R w = R(WD<Q>(a));
         const int ex = EX<Q>(a), ey = EY<Q>(a), ez = EZ<Q>(a);
-        const R eu = R(ex) * m.weq[0] + R(ey) * m.weq[1] + ((D == 3) ? R(ez) * m.weq[2] : R(0));
+        const R t = R(ex) * m.weq[0] + R(ey) * m.weq[1] + ((D == 3) ? R(ez) * m.weq[2] : R(0));
         const R ea = R(ex) * m.A[0] + R(ey) * m.A[1] + ((D == 3) ? R(ez) * m.A[2] : R(0));
         const R ef = R(ex) * m.wf[0] + R(ey) * m.wf[1] + ((D == 3) ? R(ez) * m.wf[2] : R(0));
-        const R sym_eq = w * (drho + rho * (R(4.5) * eu * eu - usq)) + (mxw ? p.mx[a] : R(0));
-        const R anti_eq = w * rho * R(3) * eu;
-        const R sym_f = w * Crho * (R(9) * ef * ea - R(3) * fa);
-        const R anti_f = w * Crho * R(3) * ea;
+        R ps = w * (base + k1 * t * t + k2 * ef * ea);
+        if (mxw) ps += om * p.mx[a];
+        const R pa = w * (kl * t + kf * ea);
         const R da = d[a], db = d[b];
-        d[a] = da + om * (sym_eq + anti_eq - da) + sym_f + anti_f;
-        d[b] = db + om * (sym_eq - anti_eq - db) + sym_f - anti_f;
+        d[a] = om1 * da + (ps + pa);
+        d[b] = om1 * db + (ps - pa);
     }
 }
 
@@ -300,25 +434,26 @@ __device__ __forceinline__ bool pull_source(const Geo& g, const uint8_t* __restr
 // canonical post-propagation deviations at node (x,y,z) from a stored
 // post-collision state: d_b(x) = P_b(x - E_b), or P_opp(b)(x) + w_b E_b.LW
 // through a wall (halfway bounce-back with Ladd's moving-wall term)
-template <int Q, class S>
+template <int Q, class S, bool RAW = false>
 __device__ __forceinline__ void gather_node(const typename S::T* __restrict__ P, const uint8_t* __restrict__ cls,
                                             const Geo& g, const KP<typename S::R>& p, int x, int y, int z,
                                             typename S::R (&d)[Q])
 {
     using R = typename S::R;
+    auto cv = [](typename S::T v) { return RAW ? S::to_raw(v) : S::to_r(v); };
     const long long own = ((long long)z * g.ny + y) * g.nxp + x;
 #pragma unroll
     for (int b = 0; b < Q; ++b) {
         long long src;
         int wall;
         if (b == 0) {
-            d[0] = S::to_r(P[own]);
+            d[0] = cv(P[own]);
         } else if (pull_source(g, cls, x, y, z, EX<Q>(b), EY<Q>(b), EZ<Q>(b), src, wall)) {
-            d[b] = S::to_r(P[(long long)b * g.sq + src]);
+            d[b] = cv(P[(long long)b * g.sq + src]);
         } else {
             const R w = R(WD<Q>(b));
             const R el = R(EX<Q>(b)) * p.LW[wall][0] + R(EY<Q>(b)) * p.LW[wall][1] + R(EZ<Q>(b)) * p.LW[wall][2];
-            d[b] = S::to_r(P[(long long)OPP<Q>(b) * g.sq + own]) + w * el;
+            d[b] = cv(P[(long long)OPP<Q>(b) * g.sq + own]) + w * el;
         }
     }
 }

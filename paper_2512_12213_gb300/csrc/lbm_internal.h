@@ -61,8 +61,9 @@ struct Ctx {
     int device;
     int ext;                 // Lorentz force, Maxwell equilibrium or LES present
     Geo geo;
-    KP<double> kpd;
-    KP<float> kpf;
+    KP<double> kpd;          // physical units
+    KP<float> kpf;           // physical units, float
+    KP<float> kps;           // storage units (d times the format's scale), float
     const Dispatch* ops;
     size_t elem;             // bytes per stored population
     size_t relem;            // bytes per compute value
@@ -82,6 +83,7 @@ struct Ctx {
     int sm_count;
     int smem_optin;
     int tile_R;
+    int tile_stages;
     int tile_ntiles;
     size_t tile_smem;
     mutable int tile_blocks;

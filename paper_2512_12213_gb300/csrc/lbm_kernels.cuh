@@ -73,8 +73,11 @@ __device__ __forceinline__ void block_sum(double (&v)[W], double* smem /* >= W *
 // direction).  For every direction it loads the aligned vector of the pull
 // source row; the x-shifted directions take their edge element from the
 // neighbouring lane (warp shuffle), or from one scalar load at a row edge or
-// warp edge.  A chunk that holds a boundary, solid or padding node is
-// recomputed node by node with explicit bounce-back instead.
+// warp edge.  16-bit formats stay packed two to a register (the x shift is a
+// byte permute) and are relaxed two nodes at a time.  A chunk that holds a
+// boundary, solid or padding node is recomputed node by node with explicit
+// bounce-back.  Populations are in storage units (kernel parameters scaled
+// to match).
 template <int Q, class S, bool EXT>
 __global__ void __launch_bounds__(STEP_THREADS)
 k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
@@ -83,6 +86,7 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
     using T = typename S::T;
     using R = typename S::R;
     constexpr int V = S::V;
+    constexpr bool PACKED = sizeof(T) == 2;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const int ncx = g.nxp / V;
@@ -101,57 +105,115 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
         if constexpr (V == 8) {
             const uint2 cv = *reinterpret_cast<const uint2*>(cp);
             special = (cv.x | cv.y) != 0u;
+        } else if constexpr (V == 4) {
+            special = *reinterpret_cast<const uint32_t*>(cp) != 0u;
+        } else {
+            special = *reinterpret_cast<const uint16_t*>(cp) != 0;
         }
-        else if constexpr (V == 4) special = *reinterpret_cast<const uint32_t*>(cp) != 0u;
-        else special = *reinterpret_cast<const uint16_t*>(cp) != 0;
     }
+    // row offsets of the pull sources, by (E_y, E_z)
+    long long roff[3][3];
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int ys = wrapi(y - dy, g.ny);
+            const int zs = (Q == 19) ? wrapi(z - dz, g.nz) : 0;
+            roff[dy + 1][dz + 1] = ((long long)zs * g.ny + ys) * g.nxp;
+        }
 
-    T f[Q][V];
+    // shifted source values: packed words for 16-bit formats, else elements
+    uint32_t w[Q][PACKED ? V / 2 : 1];
+    T f[Q][PACKED ? 1 : V];
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        const int ys = wrapi(y - EY<Q>(a), g.ny);
-        const int zs = (Q == 19) ? wrapi(z - EZ<Q>(a), g.nz) : 0;
-        const T* rp = src + (long long)a * g.sq + ((long long)zs * g.ny + ys) * g.nxp;
+        const T* rp = src + (long long)a * g.sq + roff[EY<Q>(a) + 1][EZ<Q>(a) + 1];
         Vec16<T, V> raw;
         raw.raw = __ldg(reinterpret_cast<const uint4*>(rp + x0));
-        if (EX<Q>(a) == 0) {
+        T edge = raw.e[0];
+        if (EX<Q>(a) == 1) {
+            edge = shfl_up1(raw.e[V - 1]);
+            if (lane == 0 || cx == 0) edge = rp[cx == 0 ? g.nx - 1 : x0 - 1];
+        } else if (EX<Q>(a) == -1) {
+            edge = shfl_down1(raw.e[0]);
+            if (lane == 31 || x0 + V >= g.nx) edge = rp[x0 + V >= g.nx ? 0 : x0 + V];
+        }
+        if constexpr (PACKED) {
+            const uint32_t rw[4] = {raw.raw.x, raw.raw.y, raw.raw.z, raw.raw.w};
+            Bits16<T> eb;
+            eb.t = edge;
+            const uint32_t ew = (uint32_t)eb.s;
+            if (EX<Q>(a) == 0) {
 #pragma unroll
-            for (int k = 0; k < V; ++k) f[a][k] = raw.e[k];
-        } else if (EX<Q>(a) == 1) {
-            T left = shfl_up1(raw.e[V - 1]);
-            if (lane == 0 || cx == 0) left = rp[cx == 0 ? g.nx - 1 : x0 - 1];
-            f[a][0] = left;
+                for (int i = 0; i < V / 2; ++i) w[a][i] = rw[i];
+            } else if (EX<Q>(a) == 1) {       // value k <- raw k-1
+                w[a][0] = __byte_perm(ew, rw[0], 0x5410);
 #pragma unroll
-            for (int k = 1; k < V; ++k) f[a][k] = raw.e[k - 1];
+                for (int i = 1; i < V / 2; ++i) w[a][i] = __byte_perm(rw[i - 1], rw[i], 0x5432);
+            } else {                           // value k <- raw k+1
+#pragma unroll
+                for (int i = 0; i < V / 2 - 1; ++i) w[a][i] = __byte_perm(rw[i], rw[i + 1], 0x5432);
+                w[a][V / 2 - 1] = __byte_perm(rw[V / 2 - 1], ew, 0x5432);
+            }
         } else {
-            T right = shfl_down1(raw.e[0]);
-            if (lane == 31 || x0 + V >= g.nx) right = rp[x0 + V >= g.nx ? 0 : x0 + V];
-            f[a][V - 1] = right;
+            if (EX<Q>(a) == 0) {
 #pragma unroll
-            for (int k = 0; k < V - 1; ++k) f[a][k] = raw.e[k + 1];
+                for (int k = 0; k < V; ++k) f[a][k] = raw.e[k];
+            } else if (EX<Q>(a) == 1) {
+                f[a][0] = edge;
+#pragma unroll
+                for (int k = 1; k < V; ++k) f[a][k] = raw.e[k - 1];
+            } else {
+#pragma unroll
+                for (int k = 0; k < V - 1; ++k) f[a][k] = raw.e[k + 1];
+                f[a][V - 1] = edge;
+            }
         }
     }
     if (!active) return;
 
     const long long base = row * g.nxp + x0;
     if (!special) {
+        if constexpr (PACKED) {
 #pragma unroll
-        for (int k = 0; k < V; ++k) {
-            R d[Q];
+            for (int i = 0; i < V / 2; ++i) {
+                R d0[Q], d1[Q];
 #pragma unroll
-            for (int a = 0; a < Q; ++a) d[a] = S::to_r(f[a][k]);
-            NodeM<R> m;
-            node_macro<R, Q, EXT>(d, p, m);
-            node_relax<R, Q, EXT>(d, p, m);
+                for (int a = 0; a < Q; ++a) {
+                    const float2 v = S::unpack2(w[a][i]);
+                    d0[a] = v.x;
+                    d1[a] = v.y;
+                }
+                NodeM<R> m0, m1;
+                node_macro<R, Q, EXT>(d0, p, m0);
+                node_macro<R, Q, EXT>(d1, p, m1);
+                node_relax<R, Q, EXT>(d0, p, m0);
+                node_relax<R, Q, EXT>(d1, p, m1);
 #pragma unroll
-            for (int a = 0; a < Q; ++a) f[a][k] = S::from_r(d[a]);
-        }
+                for (int a = 0; a < Q; ++a) w[a][i] = S::pack2(d0[a], d1[a]);
+            }
 #pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            Vec16<T, V> o;
+            for (int a = 0; a < Q; ++a)
+                *reinterpret_cast<uint4*>(dst + (long long)a * g.sq + base) = make_uint4(w[a][0], w[a][1], w[a][2], w[a][3]);
+        } else {
 #pragma unroll
-            for (int k = 0; k < V; ++k) o.e[k] = f[a][k];
-            *reinterpret_cast<uint4*>(dst + (long long)a * g.sq + base) = o.raw;
+            for (int k = 0; k < V; ++k) {
+                R d[Q];
+#pragma unroll
+                for (int a = 0; a < Q; ++a) d[a] = S::to_raw(f[a][k]);
+                NodeM<R> m;
+                node_macro<R, Q, EXT>(d, p, m);
+                node_relax<R, Q, EXT>(d, p, m);
+#pragma unroll
+                for (int a = 0; a < Q; ++a) f[a][k] = S::from_raw(d[a]);
+            }
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                Vec16<T, V> o;
+#pragma unroll
+                for (int k = 0; k < V; ++k) o.e[k] = f[a][k];
+                *reinterpret_cast<uint4*>(dst + (long long)a * g.sq + base) = o.raw;
+            }
         }
         return;
     }
@@ -161,16 +223,16 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
         const uint8_t c = cls[base + k];
         if (x >= g.nx || nc_solid(c) || c == NC_PAD) {
 #pragma unroll
-            for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + base + k] = S::from_r(R(0));
+            for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + base + k] = S::from_raw(R(0));
             continue;
         }
         R d[Q];
-        gather_node<Q, S>(src, cls, g, p, x, y, z, d);
+        gather_node<Q, S, true>(src, cls, g, p, x, y, z, d);
         NodeM<R> m;
         node_macro<R, Q, EXT>(d, p, m);
         node_relax<R, Q, EXT>(d, p, m);
 #pragma unroll
-        for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + base + k] = S::from_r(d[a]);
+        for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + base + k] = S::from_raw(d[a]);
     }
 }
 
@@ -625,6 +687,12 @@ template <class S> inline const KP<typename S::R>& kp_of(const Ctx& c)
     if constexpr (sizeof(typename S::R) == 8) return c.kpd;
     else return c.kpf;
 }
+// parameters in storage units, for the step kernels
+template <class S> inline const KP<typename S::R>& kp_step_of(const Ctx& c)
+{
+    if constexpr (sizeof(typename S::R) == 8) return c.kpd;
+    else return c.kps;
+}
 
 template <int Q, class S, bool EXT>
 cudaError_t launch_step_q(const Ctx& c, const void* src, void* dst, cudaStream_t st)
@@ -632,7 +700,7 @@ cudaError_t launch_step_q(const Ctx& c, const void* src, void* dst, cudaStream_t
     using T = typename S::T;
     const long long nch = (long long)(c.geo.nxp / S::V) * c.geo.ny * c.geo.nz;
     const int blocks = grid_for(nch, STEP_THREADS, 1ll << 31);
-    k_step<Q, S, EXT><<<blocks, STEP_THREADS, 0, st>>>((const T*)src, (T*)dst, c.cls, c.geo, kp_of<S>(c));
+    k_step<Q, S, EXT><<<blocks, STEP_THREADS, 0, st>>>((const T*)src, (T*)dst, c.cls, c.geo, kp_step_of<S>(c));
     return cudaGetLastError();
 }
 
@@ -650,8 +718,8 @@ cudaError_t launch_step_tile(const Ctx& c, const void* src, void* dst, cudaStrea
         if (occ < 1) return cudaErrorInvalidConfiguration;
         c.tile_blocks = (int)std::min<long long>((long long)c.sm_count * occ, c.tile_ntiles);
     }
-    kern<<<c.tile_blocks, TILE_THREADS, c.tile_smem, st>>>((const T*)src, (T*)dst, c.cls, c.geo, kp_of<S>(c),
-                                                            c.tile_R, c.tile_ntiles, c.errflag);
+    kern<<<c.tile_blocks, TILE_THREADS, c.tile_smem, st>>>((const T*)src, (T*)dst, c.cls, c.geo, kp_step_of<S>(c),
+                                                            c.tile_R, c.tile_ntiles, c.tile_stages, c.errflag);
     return cudaGetLastError();
 }
 
