@@ -221,6 +221,29 @@ lbm_status lbm_stress(lbm_ctx* ctx, int variant, void* sigma, void* S, void* rho
 lbm_status lbm_wall_force(lbm_ctx* ctx, int wall, unsigned flags, double weight, double* out,
                           int out_on_host, void* stream);
 
+/* lbm_wall_force_noalloc -- the paper has no counterpart; this is a service
+ * of the library.  It returns exactly what lbm_wall_force returns (same
+ * arguments, same reduction order), but it asks for no device memory: its
+ * block partial sums and its result slot live in a fixed static device array
+ * inside the library (98,368 bytes, held by every GPU that loads the library
+ * until the process exits), not in the context's scratch buffer.
+ * It is for callers that cannot allocate device memory when they need a
+ * force -- their memory is fully committed to population arrays, or is owned
+ * by a host application or another runtime that hands out no more -- while
+ * the context's scratch buffer is taken by another reduction of the same
+ * context queued on a different stream.
+ * Limits and caveats:
+ *   - at most 1,048,576 links per call (wall < 0 counts every link); larger
+ *     requests return LBM_ERR_ARG with a message naming the limit;
+ *   - the first call on a device looks up the array's device address (once
+ *     per device); make that first call before any stream capture;
+ *   - all calls share the one array, which keeps the last call's contents
+ *     (each call overwrites what it reads, so nothing needs clearing): calls
+ *     that overlap on the GPU -- on different streams, from different
+ *     contexts or threads on the same device -- race; serialise them. */
+lbm_status lbm_wall_force_noalloc(lbm_ctx* ctx, int wall, unsigned flags, double weight, double* out,
+                                  int out_on_host, void* stream);
+
 /* FP64 sums over fluid nodes of the canonical state f(T), times dx^D:
  * out[0] mass, out[1..3] momentum sum e f, out[4..6] body force sum rho a. */
 lbm_status lbm_balance(lbm_ctx* ctx, double* out, int out_on_host, void* stream);

@@ -79,6 +79,7 @@ _SIGS = {
     "lbm_device_status": [_vp, _P(ctypes.c_uint32), _i, _vp],
     "lbm_stress": [_vp, _i, _vp, _vp, _vp, _vp, _vp],
     "lbm_wall_force": [_vp, _i, ctypes.c_uint, _d, _vp, _i, _vp],
+    "lbm_wall_force_noalloc": [_vp, _i, ctypes.c_uint, _d, _vp, _i, _vp],
     "lbm_balance": [_vp, _vp, _i, _vp],
     "lbm_adjoint_buffer_bytes": [_vp, _P(ctypes.c_size_t)],
     "lbm_adjoint_reset": [_vp, _vp],
@@ -231,6 +232,13 @@ def lbm_stress(ctx, variant, sigma, S, rho, v, stream):
 def lbm_wall_force(ctx, wall, flags, weight, out, out_on_host, stream):
     _check(load().lbm_wall_force(ctx, int(wall), int(flags), float(weight), _ptr(out), int(out_on_host), stream),
            ctx)
+
+
+def lbm_wall_force_noalloc(ctx, wall, flags, weight, out, out_on_host, stream):
+    """lbm_wall_force without device memory from the caller (static library
+    scratch; at most 1,048,576 links per call; overlapping calls race)."""
+    _check(load().lbm_wall_force_noalloc(ctx, int(wall), int(flags), float(weight), _ptr(out),
+                                         int(out_on_host), stream), ctx)
 
 
 def lbm_balance(ctx, out, out_on_host, stream):
