@@ -123,16 +123,24 @@ void build_geometry(const lbm_config* c, const uint8_t* wid, int nxp, std::vecto
                     cls[np] = nc_make_solid(wid[n]);
                     continue;
                 }
-                bool bound = false;
+                bool face = false, solid = false;
                 for (int a = 1; a < Q; ++a) {
                     long long dn;
                     int wall;
                     if (!host_push_dest<Q>(c, wid, x, y, z, a, dn, wall)) {
-                        bound = true;
+                        // a wall link that stays inside the box hits a solid node
+                        const int px = x + EX<Q>(a), py = y + EY<Q>(a), pz = z + EZ<Q>(a);
+                        const bool in_box = (px >= 0 && px < c->nx) && (py >= 0 && py < c->ny) &&
+                                            (pz >= 0 && pz < c->nz);
+                        const bool wraps = (c->periodic[0] || (px >= 0 && px < c->nx)) &&
+                                           (c->periodic[1] || (py >= 0 && py < c->ny)) &&
+                                           ((Q == 9 || c->periodic[2]) || (pz >= 0 && pz < c->nz));
+                        if (in_box || wraps) solid = true;
+                        else face = true;
                         if (links) raw.push_back(Link{(uint32_t)np, (uint16_t)a, (uint16_t)wall});
                     }
                 }
-                cls[np] = bound ? NC_BOUND : NC_BULK;
+                cls[np] = solid ? NC_BOUND : (face ? NC_FACE : NC_BULK);
             }
     if (links) {
         links->clear();
@@ -174,7 +182,7 @@ template <typename R> void cast_kp(const KP<double>& s, KP<R>& d)
     d.maxwell = s.maxwell;
     for (int a = 0; a < 19; ++a) d.mx[a] = (R)s.mx[a];
     for (int k = 0; k < 6; ++k) d.Lh[k] = (R)s.Lh[k];
-    d.les = s.les; d.lesc = (R)s.lesc;
+    d.les = s.les; d.lesc = (R)s.lesc; d.face_ladd = s.face_ladd;
     for (int w = 0; w <= MAXW; ++w)
         for (int k = 0; k < 3; ++k) d.LW[w][k] = (R)s.LW[w][k];
     d.c = (R)s.c; d.dt = (R)s.dt; d.svol = (R)s.svol;
@@ -226,6 +234,15 @@ void fill_params(Ctx& x)
     }
     p.les = c->les;
     p.lesc = 18.0 * c->cs * c->cs;
+    p.face_ladd = 0;
+    for (int k = 0; k < D; ++k)
+        if (!c->periodic[k])
+            for (int sd = 0; sd < 2; ++sd) {
+                const int w = c->face_wall[2 * k + sd];
+                if (w >= 1 && w <= c->n_walls)
+                    for (int j = 0; j < D; ++j)
+                        if (c->wall_u[w - 1][j] != 0.0) p.face_ladd = 1;
+            }
     for (int w = 1; w <= c->n_walls; ++w)
         for (int k = 0; k < 3; ++k) p.LW[w][k] = (k < D) ? 6.0 * c->rho0 * c->wall_u[w - 1][k] / cc : 0.0;
     p.c = cc;

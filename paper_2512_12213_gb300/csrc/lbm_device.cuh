@@ -102,6 +102,16 @@ struct StoreF16 {
         memcpy(&h, &w, 4);
         return __half22float2(h);
     }
+    // one half of a packed word as float / the word with that half replaced
+    __device__ static float half_of(uint32_t w, bool hi)
+    {
+        return __half2float(__ushort_as_half((unsigned short)(hi ? (w >> 16) : (w & 0xFFFFu))));
+    }
+    __device__ static uint32_t put_half(uint32_t w, bool hi, float v)
+    {
+        const uint32_t b = (uint32_t)__half_as_ushort(__float2half_rn(v));
+        return hi ? __byte_perm(w, b, 0x5410) : __byte_perm(w, b, 0x3254);
+    }
     __device__ static uint32_t pack2(float a, float b)
     {
         __half2 h = __floats2half2_rn(a, b);
@@ -122,6 +132,15 @@ struct StoreBF16 {
         __nv_bfloat162 h;
         memcpy(&h, &w, 4);
         return __bfloat1622float2(h);
+    }
+    __device__ static float half_of(uint32_t w, bool hi)
+    {
+        return __uint_as_float(hi ? (w & 0xFFFF0000u) : (w << 16));
+    }
+    __device__ static uint32_t put_half(uint32_t w, bool hi, float v)
+    {
+        const uint32_t b = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v));
+        return hi ? __byte_perm(w, b, 0x5410) : __byte_perm(w, b, 0x3254);
     }
     __device__ static uint32_t pack2(float a, float b)
     {
@@ -149,7 +168,11 @@ struct Geo {
 };
 
 // node classes (one byte per node, padded layout)
-enum : uint8_t { NC_BULK = 0, NC_BOUND = 1, NC_PAD = 0xFF };
+// NC_BULK: every pull source is a fluid node (periodic wrap allowed);
+// NC_FACE: some links cross a closed face of the box, none hits a solid;
+// NC_BOUND: some link hits a solid node; 0x80 | id: solid of wall id; NC_PAD: padding
+enum : uint8_t { NC_BULK = 0, NC_BOUND = 1, NC_FACE = 2, NC_PAD = 0xFF };
+__host__ __device__ inline bool nc_has_wall(uint8_t c) { return c == NC_BOUND || c == NC_FACE; }
 __host__ __device__ inline bool nc_solid(uint8_t c) { return (c & 0x80) && c != NC_PAD; }
 __host__ __device__ inline int nc_wall(uint8_t c) { return c & 0x7F; }
 __host__ __device__ inline uint8_t nc_make_solid(int wall) { return (uint8_t)(0x80 | wall); }
@@ -171,6 +194,7 @@ template <typename R> struct KP {
     R Lh[6];          // L / c^2: xx yy zz xy xz yz (zero without the Maxwell term)
     int les;
     R lesc;           // 18 Cs^2
+    int face_ladd;    // some closed face of the box is a moving wall
     R LW[MAXW + 1][3];  // 6 rho0 u_w / c per wall id (Ladd term = w_a E_a . LW)
     // units for outputs
     R c, dt, svol;    // c, dt, dx^D / dt

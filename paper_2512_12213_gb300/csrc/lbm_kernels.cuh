@@ -78,8 +78,41 @@ __device__ __forceinline__ void block_sum(double (&v)[W], double* smem /* >= W *
 // boundary, solid or padding node is recomputed node by node with explicit
 // bounce-back.  Populations are in storage units (kernel parameters scaled
 // to match).
-template <int Q, class S, bool EXT>
-__global__ void __launch_bounds__(STEP_THREADS)
+// Ladd term w_a E_a . LW[wall] of an incoming population
+template <int Q, typename R>
+__device__ __forceinline__ R ladd_of(const KP<R>& p, int a, int wall)
+{
+    return R(WD<Q>(a)) * (R(EX<Q>(a)) * p.LW[wall][0] + R(EY<Q>(a)) * p.LW[wall][1] + R(EZ<Q>(a)) * p.LW[wall][2]);
+}
+
+// Box-face bounce-back inside the vectorised path (FACES = some axis is
+// closed).  For direction a at a chunk of row (y, z): the pull-source row is
+// outside a closed y or z face -> every node of the chunk bounces (own value
+// of opp(a)); the first / last node of a row with a closed x face bounces the
+// directions that pull across it.  The wall of a link follows the rule
+// "first closed axis crossed, in x, y, z order".
+struct FaceInfo {
+    bool closed_x;
+    bool yo_lo, yo_hi, zo_lo, zo_hi;     // pull rows y-(+1), y-(-1), z-(+1), z-(-1) outside
+    int wy_lo, wy_hi, wz_lo, wz_hi, wx_lo, wx_hi;
+};
+
+template <int Q>
+__device__ __forceinline__ bool row_out(const FaceInfo& fi, int a, int& wall)
+{
+    const int ey = EY<Q>(a), ez = EZ<Q>(a);
+    if (ey == 1 && fi.yo_lo) { wall = fi.wy_lo; return true; }
+    if (ey == -1 && fi.yo_hi) { wall = fi.wy_hi; return true; }
+    if (ez == 1 && fi.zo_lo) { wall = fi.wz_lo; return true; }
+    if (ez == -1 && fi.zo_hi) { wall = fi.wz_hi; return true; }
+    return false;
+}
+
+// blocks per SM the register allocation must allow (4 x 128 threads)
+template <class S> struct StepOcc { static constexpr int value = sizeof(typename S::T) == 8 ? 3 : 4; };
+
+template <int Q, class S, bool EXT, bool FACES>
+__global__ void __launch_bounds__(STEP_THREADS, StepOcc<S>::value)
 k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
        const uint8_t* __restrict__ cls, const Geo g, const KP<typename S::R> p)
 {
@@ -99,17 +132,36 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
     const int z = (int)(row / g.ny);
     const int x0 = cx * V;
 
-    bool special;
+    // class bytes of the chunk: fast path if all are bulk (or, with FACES, face)
+    bool special, face_chunk = false;
     {
         const uint8_t* cp = cls + row * g.nxp + x0;
+        unsigned long long cb;
         if constexpr (V == 8) {
             const uint2 cv = *reinterpret_cast<const uint2*>(cp);
-            special = (cv.x | cv.y) != 0u;
+            cb = ((unsigned long long)cv.y << 32) | cv.x;
         } else if constexpr (V == 4) {
-            special = *reinterpret_cast<const uint32_t*>(cp) != 0u;
+            cb = *reinterpret_cast<const uint32_t*>(cp);
         } else {
-            special = *reinterpret_cast<const uint16_t*>(cp) != 0;
+            cb = *reinterpret_cast<const uint16_t*>(cp);
         }
+        if (FACES) {
+            special = (cb & ~0x0202020202020202ull) != 0ull;
+            face_chunk = (cb & 0x0202020202020202ull) != 0ull;
+        } else {
+            special = cb != 0ull;
+        }
+    }
+    FaceInfo fi;
+    if (FACES) {
+        fi.closed_x = !g.periodic[0];
+        fi.yo_lo = !g.periodic[1] && y == 0;
+        fi.yo_hi = !g.periodic[1] && y == g.ny - 1;
+        fi.zo_lo = (Q == 19) && !g.periodic[2] && z == 0;
+        fi.zo_hi = (Q == 19) && !g.periodic[2] && z == g.nz - 1;
+        fi.wx_lo = g.face_wall[0]; fi.wx_hi = g.face_wall[1];
+        fi.wy_lo = g.face_wall[2]; fi.wy_hi = g.face_wall[3];
+        fi.wz_lo = g.face_wall[4]; fi.wz_hi = g.face_wall[5];
     }
     // row offsets of the pull sources, by (E_y, E_z)
     long long roff[3][3];
@@ -121,32 +173,57 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
             const int zs = (Q == 19) ? wrapi(z - dz, g.nz) : 0;
             roff[dy + 1][dz + 1] = ((long long)zs * g.ny + ys) * g.nxp;
         }
+    const long long own = row * g.nxp;
 
     // shifted source values: packed words for 16-bit formats, else elements
     uint32_t w[Q][PACKED ? V / 2 : 1];
     T f[Q][PACKED ? 1 : V];
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        const T* rp = src + (long long)a * g.sq + roff[EY<Q>(a) + 1][EZ<Q>(a) + 1];
+        int rwall = 0;
+        const bool rout = FACES && row_out<Q>(fi, a, rwall);
+        // bounced rows read the node's own value of the opposite direction
+        const T* rp = rout ? src + (long long)OPP<Q>(a) * g.sq + own
+                           : src + (long long)a * g.sq + roff[EY<Q>(a) + 1][EZ<Q>(a) + 1];
         Vec16<T, V> raw;
         raw.raw = __ldg(reinterpret_cast<const uint4*>(rp + x0));
+        const int ex = rout ? 0 : EX<Q>(a);
         T edge = raw.e[0];
-        if (EX<Q>(a) == 1) {
-            edge = shfl_up1(raw.e[V - 1]);
-            if (lane == 0 || cx == 0) edge = rp[cx == 0 ? g.nx - 1 : x0 - 1];
-        } else if (EX<Q>(a) == -1) {
-            edge = shfl_down1(raw.e[0]);
-            if (lane == 31 || x0 + V >= g.nx) edge = rp[x0 + V >= g.nx ? 0 : x0 + V];
+        if constexpr (!FACES) {
+            // periodic x: the wrap of a row edge and the warp edge are plain loads
+            if (EX<Q>(a) == 1) {
+                edge = shfl_up1(raw.e[V - 1]);
+                if (lane == 0 || cx == 0) edge = rp[cx == 0 ? g.nx - 1 : x0 - 1];
+            } else if (EX<Q>(a) == -1) {
+                edge = shfl_down1(raw.e[0]);
+                if (lane == 31 || x0 + V >= g.nx) edge = rp[x0 + V >= g.nx ? 0 : x0 + V];
+            }
+        } else {
+            if (EX<Q>(a) == 1) {
+                edge = shfl_up1(raw.e[V - 1]);
+                if (cx == 0) {
+                    edge = fi.closed_x ? src[(long long)OPP<Q>(a) * g.sq + own] : rp[g.nx - 1];
+                } else if (lane == 0) {
+                    edge = rp[x0 - 1];
+                }
+            } else if (EX<Q>(a) == -1) {
+                edge = shfl_down1(raw.e[0]);
+                if (x0 + V >= g.nx) {
+                    edge = fi.closed_x ? src[(long long)OPP<Q>(a) * g.sq + own + g.nx - 1] : rp[0];
+                } else if (lane == 31) {
+                    edge = rp[x0 + V];
+                }
+            }
         }
         if constexpr (PACKED) {
             const uint32_t rw[4] = {raw.raw.x, raw.raw.y, raw.raw.z, raw.raw.w};
             Bits16<T> eb;
             eb.t = edge;
             const uint32_t ew = (uint32_t)eb.s;
-            if (EX<Q>(a) == 0) {
+            if (ex == 0) {
 #pragma unroll
                 for (int i = 0; i < V / 2; ++i) w[a][i] = rw[i];
-            } else if (EX<Q>(a) == 1) {       // value k <- raw k-1
+            } else if (ex == 1) {             // value k <- raw k-1
                 w[a][0] = __byte_perm(ew, rw[0], 0x5410);
 #pragma unroll
                 for (int i = 1; i < V / 2; ++i) w[a][i] = __byte_perm(rw[i - 1], rw[i], 0x5432);
@@ -156,10 +233,10 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                 w[a][V / 2 - 1] = __byte_perm(rw[V / 2 - 1], ew, 0x5432);
             }
         } else {
-            if (EX<Q>(a) == 0) {
+            if (ex == 0) {
 #pragma unroll
                 for (int k = 0; k < V; ++k) f[a][k] = raw.e[k];
-            } else if (EX<Q>(a) == 1) {
+            } else if (ex == 1) {
                 f[a][0] = edge;
 #pragma unroll
                 for (int k = 1; k < V; ++k) f[a][k] = raw.e[k - 1];
@@ -172,40 +249,85 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
     }
     if (!active) return;
 
+    // Ladd terms of moving face walls, added after unpacking (face chunks only)
+    const bool ladd = FACES && face_chunk && p.face_ladd;
+    auto add_ladd = [&](R (&d)[Q], int k) {
+#pragma unroll
+        for (int a = 1; a < Q; ++a) {
+            int wall = 0;
+            bool hit = row_out<Q>(fi, a, wall);
+            if (fi.closed_x) {
+                if (EX<Q>(a) == 1 && x0 + k == 0) { hit = true; wall = fi.wx_lo; }
+                if (EX<Q>(a) == -1 && x0 + k == g.nx - 1) { hit = true; wall = fi.wx_hi; }
+            }
+            if (hit) d[a] += ladd_of<Q, R>(p, a, wall);
+        }
+    };
+
     const long long base = row * g.nxp + x0;
     if (!special) {
         if constexpr (PACKED) {
-#pragma unroll
+            // rolled loop over the V/2 packed words (two nodes each), used as a
+            // queue: relax the front word's two nodes, append the result at the
+            // back; after V/2 turns the words are the results, in order.  This
+            // keeps the code of two node updates instead of V.
+#pragma unroll 1
             for (int i = 0; i < V / 2; ++i) {
-                R d0[Q], d1[Q];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    R d[Q];
+#pragma unroll
+                    for (int a = 0; a < Q; ++a) d[a] = S::half_of(w[a][0], h == 1);
+                    if (ladd) add_ladd(d, 2 * i + h);
+                    NodeM<R> m;
+                    node_macro<R, Q, EXT>(d, p, m);
+                    node_relax<R, Q, EXT>(d, p, m);
+#pragma unroll
+                    for (int a = 0; a < Q; ++a) w[a][0] = S::put_half(w[a][0], h == 1, d[a]);
+                }
 #pragma unroll
                 for (int a = 0; a < Q; ++a) {
-                    const float2 v = S::unpack2(w[a][i]);
-                    d0[a] = v.x;
-                    d1[a] = v.y;
-                }
-                NodeM<R> m0, m1;
-                node_macro<R, Q, EXT>(d0, p, m0);
-                node_macro<R, Q, EXT>(d1, p, m1);
-                node_relax<R, Q, EXT>(d0, p, m0);
-                node_relax<R, Q, EXT>(d1, p, m1);
+                    const uint32_t front = w[a][0];
 #pragma unroll
-                for (int a = 0; a < Q; ++a) w[a][i] = S::pack2(d0[a], d1[a]);
+                    for (int j = 0; j < V / 2 - 1; ++j) w[a][j] = w[a][j + 1];
+                    w[a][V / 2 - 1] = front;
+                }
             }
 #pragma unroll
             for (int a = 0; a < Q; ++a)
                 *reinterpret_cast<uint4*>(dst + (long long)a * g.sq + base) = make_uint4(w[a][0], w[a][1], w[a][2], w[a][3]);
         } else {
+            if constexpr (EXT) {
+                // larger node code (Lorentz / Maxwell / LES): the same rolled queue
+#pragma unroll 1
+                for (int k = 0; k < V; ++k) {
+                    R d[Q];
 #pragma unroll
-            for (int k = 0; k < V; ++k) {
-                R d[Q];
+                    for (int a = 0; a < Q; ++a) d[a] = S::to_raw(f[a][0]);
+                    if (ladd) add_ladd(d, k);
+                    NodeM<R> m;
+                    node_macro<R, Q, EXT>(d, p, m);
+                    node_relax<R, Q, EXT>(d, p, m);
 #pragma unroll
-                for (int a = 0; a < Q; ++a) d[a] = S::to_raw(f[a][k]);
-                NodeM<R> m;
-                node_macro<R, Q, EXT>(d, p, m);
-                node_relax<R, Q, EXT>(d, p, m);
+                    for (int a = 0; a < Q; ++a) {
 #pragma unroll
-                for (int a = 0; a < Q; ++a) f[a][k] = S::from_raw(d[a]);
+                        for (int j = 0; j < V - 1; ++j) f[a][j] = f[a][j + 1];
+                        f[a][V - 1] = S::from_raw(d[a]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    R d[Q];
+#pragma unroll
+                    for (int a = 0; a < Q; ++a) d[a] = S::to_raw(f[a][k]);
+                    if (ladd) add_ladd(d, k);
+                    NodeM<R> m;
+                    node_macro<R, Q, EXT>(d, p, m);
+                    node_relax<R, Q, EXT>(d, p, m);
+#pragma unroll
+                    for (int a = 0; a < Q; ++a) f[a][k] = S::from_raw(d[a]);
+                }
             }
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
@@ -217,7 +339,7 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
         }
         return;
     }
-    // chunk with a boundary, solid or padding node: node by node
+    // chunk with a solid neighbour or padding: node by node
     for (int k = 0; k < V; ++k) {
         const int x = x0 + k;
         const uint8_t c = cls[base + k];
@@ -700,7 +822,13 @@ cudaError_t launch_step_q(const Ctx& c, const void* src, void* dst, cudaStream_t
     using T = typename S::T;
     const long long nch = (long long)(c.geo.nxp / S::V) * c.geo.ny * c.geo.nz;
     const int blocks = grid_for(nch, STEP_THREADS, 1ll << 31);
-    k_step<Q, S, EXT><<<blocks, STEP_THREADS, 0, st>>>((const T*)src, (T*)dst, c.cls, c.geo, kp_step_of<S>(c));
+    const bool faces = !c.geo.periodic[0] || !c.geo.periodic[1] || (Q == 19 && !c.geo.periodic[2]);
+    if (faces)
+        k_step<Q, S, EXT, true><<<blocks, STEP_THREADS, 0, st>>>((const T*)src, (T*)dst, c.cls, c.geo,
+                                                                 kp_step_of<S>(c));
+    else
+        k_step<Q, S, EXT, false><<<blocks, STEP_THREADS, 0, st>>>((const T*)src, (T*)dst, c.cls, c.geo,
+                                                                  kp_step_of<S>(c));
     return cudaGetLastError();
 }
 

@@ -269,7 +269,7 @@ __device__ __forceinline__ void tile_segment(const typename S::T* __restrict__ s
             R_ d[Q];
 #pragma unroll
             for (int a = 0; a < Q; ++a) d[a] = S::to_raw(srow[(size_t)a * dstride + wrap_x(x - EX<Q>(a), g.nx)]);
-            if (c == NC_BOUND) {
+            if (nc_has_wall(c)) {
 #pragma unroll
                 for (int a = 1; a < Q; ++a) {
                     long long sidx;
