@@ -282,8 +282,11 @@ def drag_errors(torch, lbm, workloads, steps):
     """Drag on the sphere after `steps` steps from rest (and its average over
     the window) in each storage format, relative to FP64."""
     res = {}
-    for storage in ("f64", "f32", "f16s", "bf16s"):
+    for key in ("f64", "f32", "f16s", "bf16s", "f16s_sr", "bf16s_sr"):
+        storage = key.split("_")[0]
         c, m = workloads.sphere(storage=storage)
+        if key.endswith("_sr"):
+            c = dict(c, rounding="stochastic", seed=2024)
         s = lbm.Sim(c, m)
         s.rest()
         st = s.stream
@@ -293,13 +296,13 @@ def drag_errors(torch, lbm, workloads, steps):
             lbm.lbm_step(s.ctx, 1, st)
             lbm.lbm_wall_force(s.ctx, 1, lbm.ACCUMULATE, 1.0 / steps, acc, 0, st)
         lbm.lbm_wall_force(s.ctx, 1, 0, 1.0, last, 0, st)
-        res[storage] = (float(last[0].item()), float(acc[0].item()))
+        res[key] = (float(last[0].item()), float(acc[0].item()))
         s.close()
         del s
         torch.cuda.empty_cache()
     ref_last, ref_avg = res["f64"]
     out = {"steps": steps, "f64_drag_last": ref_last, "f64_drag_mean": ref_avg}
-    for k in ("f32", "f16s", "bf16s"):
+    for k in ("f32", "f16s", "bf16s", "f16s_sr", "bf16s_sr"):
         out[k] = {"rel_err_last": abs(res[k][0] / ref_last - 1), "rel_err_mean": abs(res[k][1] / ref_avg - 1)}
     return out
 

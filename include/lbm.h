@@ -133,7 +133,18 @@ typedef struct lbm_config {
     int32_t n_walls;                 /* wall ids 1..n_walls, n_walls <= LBM_MAX_WALLS */
     double wall_u[LBM_MAX_WALLS][3]; /* velocity of wall k at index k-1 */
     int32_t face_wall[6];            /* wall id of each closed face: -x +x -y +y -z +z */
+    int32_t rounding;                /* LBM_ROUND_NEAREST, or LBM_ROUND_STOCHASTIC (16-bit storage only) */
+    uint32_t seed;                   /* stream of the stochastic rounding */
 } lbm_config;
+
+/* rounding of the populations stored by a step.  Stochastic rounding rounds
+ * a value up with probability equal to its distance from the value below, so
+ * that increments smaller than half a unit in the last place of the storage
+ * format accumulate in expectation instead of being lost.  The random bits
+ * are a counter-based function of (seed, step index, node, direction), so a
+ * step recomputed from a checkpoint (lbm_step_from with the same index)
+ * reproduces the original bit for bit. */
+enum { LBM_ROUND_NEAREST = 0, LBM_ROUND_STOCHASTIC = 1 };
 
 /* Required bytes of each buffer kind for this configuration and geometry.
  * host_wall_id: nx*ny*nz bytes (layout above), host memory.
@@ -187,8 +198,10 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps, void* stream);
 
 /* One step from a stored state `src` into `dst` (raw post-collision buffers
  * laid out like LBM_BUF_POP_*, e.g. checkpoints); does not touch the
- * context's own populations or time. */
-lbm_status lbm_step_from(lbm_ctx* ctx, const void* src, void* dst, void* stream);
+ * context's own populations or time.  `t` is the index of the step (the time
+ * of the canonical state f(t) that src propagates to); with stochastic
+ * rounding it selects the same random bits lbm_step used at time t. */
+lbm_status lbm_step_from(lbm_ctx* ctx, const void* src, void* dst, int64_t t, void* stream);
 
 /* Copy the current raw stored state out / back in (checkpointing).  Loading
  * sets T to `t` and marks the previous state as unavailable. */

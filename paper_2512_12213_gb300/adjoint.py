@@ -71,7 +71,7 @@ class DragProblem:
             t0, t1 = sg * self.k, min(self.T, (sg + 1) * self.k)
             states = [self.ckpt[sg]] + [self.seg[i] for i in range(t1 - t0 - 1)]
             for i in range(1, t1 - t0):          # recompute P_{t0}, ..., P_{t1-2}
-                lbm.lbm_step_from(ctx, states[i - 1], states[i], st)
+                lbm.lbm_step_from(ctx, states[i - 1], states[i], t0 + i - 1, st)
             for t in reversed(range(t0, t1)):
                 out = self.phi[cur]
                 lbm.lbm_adjoint_step(ctx, states[t - t0], phi_next, out, self.wall, self.d, 1.0 / self.T, st)

@@ -72,6 +72,10 @@ bool validate(const lbm_config* c, const uint8_t* wid, std::string& err)
     if (c->maxwell && c->lattice == LBM_D2Q9 && c->B[2] != 0.0)
         return fail("the 2-D Maxwell equilibrium needs an in-plane field (B[2] = 0)");
     if (c->les && !(c->cs >= 0)) return fail("cs must be >= 0");
+    if (c->rounding != LBM_ROUND_NEAREST && c->rounding != LBM_ROUND_STOCHASTIC)
+        return fail("rounding must be LBM_ROUND_NEAREST or LBM_ROUND_STOCHASTIC");
+    if (c->rounding == LBM_ROUND_STOCHASTIC && c->storage != LBM_STORE_F16S && c->storage != LBM_STORE_BF16S)
+        return fail("stochastic rounding applies to 16-bit storage only");
     if (!wid) return fail("wall_id is NULL");
     const long long N = nodes_of(c);
     for (long long n = 0; n < N; ++n)
@@ -284,7 +288,7 @@ void choose_tile(Ctx& x)
     // LBM_STEP_KERNEL=tile selects the shared-memory staged step where it fits;
     // the register-tiled step is the default
     const char* sel = getenv("LBM_STEP_KERNEL");
-    const bool want_tile = sel && strcmp(sel, "tile") == 0;
+    const bool want_tile = sel && strcmp(sel, "tile") == 0 && x.cfg.rounding == LBM_ROUND_NEAREST;
     const bool fits = want_tile && smem_for(R, ns) <= (size_t)x.smem_optin;
     x.tile_R = fits ? R : 0;
     x.tile_stages = fits ? ns : 0;
@@ -307,6 +311,13 @@ struct DeviceGuard {
         if (old >= 0 && cudaGetDevice(&now) == cudaSuccess && now != old) cudaSetDevice(old);
     }
 };
+
+// seed of the stochastic rounding of step t (the same for lbm_step at time t
+// and lbm_step_from(..., t, ...))
+uint32_t step_seed(const Ctx& x, int64_t t)
+{
+    return hash32(x.cfg.seed ^ hash32((uint32_t)t ^ (uint32_t)((uint64_t)t >> 32) * 0x9e3779b9u));
+}
 
 lbm_status cuda_fail(Ctx& x, cudaError_t e, const char* what)
 {
@@ -386,6 +397,7 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
     x.cfg = *cfg;
     if (x.cfg.lattice == LBM_D2Q9) x.cfg.periodic[2] = 1;
     x.ext = (cfg->lorentz || cfg->maxwell || cfg->les) ? 1 : 0;
+    x.sr = (cfg->rounding == LBM_ROUND_STOCHASTIC) ? 1 : 0;
     x.geo.nx = cfg->nx;
     x.geo.ny = cfg->ny;
     x.geo.nz = cfg->nz;
@@ -597,7 +609,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps, void* stream)
     GUARD(x);
     cudaStream_t st = (cudaStream_t)stream;
     for (int s = 0; s < nsteps; ++s) {
-        CK(x.ops->step(x, x.pop[x.cur], x.pop[1 - x.cur], st), "step kernel");
+        CK(x.ops->step(x, x.pop[x.cur], x.pop[1 - x.cur], step_seed(x, x.t), st), "step kernel");
         x.cur = 1 - x.cur;
         x.t += 1;
         x.prev_valid = true;
@@ -605,14 +617,15 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps, void* stream)
     return LBM_OK;
 }
 
-lbm_status lbm_step_from(lbm_ctx* ctx, const void* src, void* dst, void* stream)
+lbm_status lbm_step_from(lbm_ctx* ctx, const void* src, void* dst, int64_t t, void* stream)
 {
     if (!ctx) return LBM_ERR_ARG;
     Ctx& x = ctx->c;
     if (!src || !dst || src == dst) return arg_fail(x, "src and dst must be distinct non-NULL buffers");
     if (((uintptr_t)src) % 256 || ((uintptr_t)dst) % 256) return arg_fail(x, "buffers must be 256-byte aligned");
+    if (t < 0) return arg_fail(x, "t must be >= 0");
     GUARD(x);
-    CK(x.ops->step(x, src, dst, (cudaStream_t)stream), "step kernel");
+    CK(x.ops->step(x, src, dst, step_seed(x, t), (cudaStream_t)stream), "step kernel");
     return LBM_OK;
 }
 

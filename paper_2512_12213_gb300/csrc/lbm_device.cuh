@@ -112,6 +112,17 @@ struct StoreF16 {
         const uint32_t b = (uint32_t)__half_as_ushort(__float2half_rn(v));
         return hi ? __byte_perm(w, b, 0x5410) : __byte_perm(w, b, 0x3254);
     }
+    // stochastic rounding: add 13 random bits below the binary16 mantissa to
+    // the magnitude, then truncate (round up with probability = remainder)
+    __device__ static T from_raw_sr(float v, uint32_t r)
+    {
+        return __float2half_rz(__uint_as_float(__float_as_uint(v) + (r & 0x1FFFu)));
+    }
+    __device__ static uint32_t put_half_sr(uint32_t w, bool hi, float v, uint32_t r)
+    {
+        const uint32_t b = (uint32_t)__half_as_ushort(from_raw_sr(v, r));
+        return hi ? __byte_perm(w, b, 0x5410) : __byte_perm(w, b, 0x3254);
+    }
     __device__ static uint32_t pack2(float a, float b)
     {
         __half2 h = __floats2half2_rn(a, b);
@@ -142,6 +153,16 @@ struct StoreBF16 {
         const uint32_t b = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v));
         return hi ? __byte_perm(w, b, 0x5410) : __byte_perm(w, b, 0x3254);
     }
+    // stochastic rounding: 16 random bits below the bfloat16 mantissa, truncate
+    __device__ static T from_raw_sr(float v, uint32_t r)
+    {
+        return __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + (r & 0xFFFFu)) >> 16));
+    }
+    __device__ static uint32_t put_half_sr(uint32_t w, bool hi, float v, uint32_t r)
+    {
+        const uint32_t b = (uint32_t)__bfloat16_as_ushort(from_raw_sr(v, r));
+        return hi ? __byte_perm(w, b, 0x5410) : __byte_perm(w, b, 0x3254);
+    }
     __device__ static uint32_t pack2(float a, float b)
     {
         __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -154,6 +175,31 @@ struct StoreBF16 {
 template <class T, int V> union Vec16 {
     uint4 raw;
     T e[V];
+};
+
+// ------------------------------------------------- counter-based random bits
+// 32-bit integer hash (a multiply-xorshift finaliser) of a counter, and the
+// per-node stream: one hash of (node, step seed), then a linear congruential
+// step per pair of populations (16 bits each).
+__host__ __device__ inline uint32_t hash32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+struct NodeRng {
+    uint32_t s;
+    __device__ explicit NodeRng(uint32_t node, uint32_t seed) : s(hash32(node ^ hash32(seed))) {}
+    // random bits for population a (two populations per generator step)
+    __device__ uint32_t bits(int a)
+    {
+        if ((a & 1) == 0) s = s * 747796405u + 2891336453u;
+        const uint32_t r = s ^ (s >> 13);
+        return (a & 1) ? (r >> 16) : r;
+    }
 };
 
 // ------------------------------------------------------------- geometry

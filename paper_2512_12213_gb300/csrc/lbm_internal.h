@@ -33,7 +33,7 @@ constexpr size_t SCRATCH_DOUBLES = SCRATCH_FLAG_OFF + 8;
 struct Ctx;
 
 struct Dispatch {
-    cudaError_t (*step)(const Ctx&, const void* src, void* dst, cudaStream_t);
+    cudaError_t (*step)(const Ctx&, const void* src, void* dst, uint32_t seed, cudaStream_t);
     cudaError_t (*import_f)(const Ctx&, const void* src, int dtype, void* dst, cudaStream_t);
     cudaError_t (*init_fields)(const Ctx&, const double* rho, const double* u, const double* xi, void* dst,
                                cudaStream_t);
@@ -60,6 +60,7 @@ struct Ctx {
     lbm_config cfg;
     int device;
     int ext;                 // Lorentz force, Maxwell equilibrium or LES present
+    int sr;                  // stochastic rounding of 16-bit stores
     Geo geo;
     KP<double> kpd;          // physical units
     KP<float> kpf;           // physical units, float

@@ -111,10 +111,10 @@ __device__ __forceinline__ bool row_out(const FaceInfo& fi, int a, int& wall)
 // blocks per SM the register allocation must allow (4 x 128 threads)
 template <class S> struct StepOcc { static constexpr int value = sizeof(typename S::T) == 8 ? 3 : 4; };
 
-template <int Q, class S, bool EXT, bool FACES>
+template <int Q, class S, bool EXT, bool FACES, bool SR>
 __global__ void __launch_bounds__(STEP_THREADS, StepOcc<S>::value)
 k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
-       const uint8_t* __restrict__ cls, const Geo g, const KP<typename S::R> p)
+       const uint8_t* __restrict__ cls, const Geo g, const KP<typename S::R> p, uint32_t seed)
 {
     using T = typename S::T;
     using R = typename S::R;
@@ -282,8 +282,14 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                     NodeM<R> m;
                     node_macro<R, Q, EXT>(d, p, m);
                     node_relax<R, Q, EXT>(d, p, m);
+                    if constexpr (SR) {
+                        NodeRng rng((uint32_t)(base + 2 * i + h), seed);
 #pragma unroll
-                    for (int a = 0; a < Q; ++a) w[a][0] = S::put_half(w[a][0], h == 1, d[a]);
+                        for (int a = 0; a < Q; ++a) w[a][0] = S::put_half_sr(w[a][0], h == 1, d[a], rng.bits(a));
+                    } else {
+#pragma unroll
+                        for (int a = 0; a < Q; ++a) w[a][0] = S::put_half(w[a][0], h == 1, d[a]);
+                    }
                 }
 #pragma unroll
                 for (int a = 0; a < Q; ++a) {
@@ -353,8 +359,14 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
         NodeM<R> m;
         node_macro<R, Q, EXT>(d, p, m);
         node_relax<R, Q, EXT>(d, p, m);
+        if constexpr (SR) {
+            NodeRng rng((uint32_t)(base + k), seed);
 #pragma unroll
-        for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + base + k] = S::from_raw(d[a]);
+            for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + base + k] = S::from_raw_sr(d[a], rng.bits(a));
+        } else {
+#pragma unroll
+            for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + base + k] = S::from_raw(d[a]);
+        }
     }
 }
 
@@ -816,19 +828,19 @@ template <class S> inline const KP<typename S::R>& kp_step_of(const Ctx& c)
     else return c.kps;
 }
 
-template <int Q, class S, bool EXT>
-cudaError_t launch_step_q(const Ctx& c, const void* src, void* dst, cudaStream_t st)
+template <int Q, class S, bool EXT, bool SR>
+cudaError_t launch_step_q(const Ctx& c, const void* src, void* dst, uint32_t seed, cudaStream_t st)
 {
     using T = typename S::T;
     const long long nch = (long long)(c.geo.nxp / S::V) * c.geo.ny * c.geo.nz;
     const int blocks = grid_for(nch, STEP_THREADS, 1ll << 31);
     const bool faces = !c.geo.periodic[0] || !c.geo.periodic[1] || (Q == 19 && !c.geo.periodic[2]);
     if (faces)
-        k_step<Q, S, EXT, true><<<blocks, STEP_THREADS, 0, st>>>((const T*)src, (T*)dst, c.cls, c.geo,
-                                                                 kp_step_of<S>(c));
+        k_step<Q, S, EXT, true, SR><<<blocks, STEP_THREADS, 0, st>>>((const T*)src, (T*)dst, c.cls, c.geo,
+                                                                     kp_step_of<S>(c), seed);
     else
-        k_step<Q, S, EXT, false><<<blocks, STEP_THREADS, 0, st>>>((const T*)src, (T*)dst, c.cls, c.geo,
-                                                                  kp_step_of<S>(c));
+        k_step<Q, S, EXT, false, SR><<<blocks, STEP_THREADS, 0, st>>>((const T*)src, (T*)dst, c.cls, c.geo,
+                                                                      kp_step_of<S>(c), seed);
     return cudaGetLastError();
 }
 
@@ -852,11 +864,17 @@ cudaError_t launch_step_tile(const Ctx& c, const void* src, void* dst, cudaStrea
 }
 
 template <int Q, class S>
-cudaError_t launch_step(const Ctx& c, const void* src, void* dst, cudaStream_t st)
+cudaError_t launch_step(const Ctx& c, const void* src, void* dst, uint32_t seed, cudaStream_t st)
 {
     if (c.tile_R > 0)
         return c.ext ? launch_step_tile<Q, S, true>(c, src, dst, st) : launch_step_tile<Q, S, false>(c, src, dst, st);
-    return c.ext ? launch_step_q<Q, S, true>(c, src, dst, st) : launch_step_q<Q, S, false>(c, src, dst, st);
+    if constexpr (sizeof(typename S::T) == 2) {
+        if (c.sr)
+            return c.ext ? launch_step_q<Q, S, true, true>(c, src, dst, seed, st)
+                         : launch_step_q<Q, S, false, true>(c, src, dst, seed, st);
+    }
+    return c.ext ? launch_step_q<Q, S, true, false>(c, src, dst, seed, st)
+                 : launch_step_q<Q, S, false, false>(c, src, dst, seed, st);
 }
 
 template <int Q, class S>
@@ -959,8 +977,8 @@ cudaError_t launch_adjoint(const Ctx& c, const void* Pprev, const void* phin, vo
 template <class S> Dispatch make_dispatch()
 {
     Dispatch d;
-    d.step = [](const Ctx& c, const void* s, void* t, cudaStream_t st) {
-        return c.cfg.lattice == 9 ? launch_step<9, S>(c, s, t, st) : launch_step<19, S>(c, s, t, st);
+    d.step = [](const Ctx& c, const void* s, void* t, uint32_t seed, cudaStream_t st) {
+        return c.cfg.lattice == 9 ? launch_step<9, S>(c, s, t, seed, st) : launch_step<19, S>(c, s, t, seed, st);
     };
     d.import_f = [](const Ctx& c, const void* s, int dt, void* t, cudaStream_t st) {
         return c.cfg.lattice == 9 ? launch_import<9, S>(c, s, dt, t, st) : launch_import<19, S>(c, s, dt, t, st);

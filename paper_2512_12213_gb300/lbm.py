@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "liblbm.so")
 D2Q9, D3Q19 = 9, 19
 FORCE = {"a": 0, "b": 1, "c": 2, "d": 3, "e": 4}
 STORE = {"f64": 0, "f32": 1, "f16s": 2, "bf16s": 3}
+ROUND = {"nearest": 0, "stochastic": 1}
 S1, S2, S3, S4 = 1, 2, 3, 4
 MOVING_CORR, MAXWELL_REMOVE, ACCUMULATE = 1, 2, 4
 BUF_POP_A, BUF_POP_B, BUF_NODE, BUF_LINKS, BUF_SCRATCH, BUF_STAGE, NUM_BUFFERS = range(7)
@@ -51,6 +52,8 @@ class LbmConfig(ctypes.Structure):
         ("n_walls", ctypes.c_int32),
         ("wall_u", (ctypes.c_double * 3) * MAX_WALLS),
         ("face_wall", ctypes.c_int32 * 6),
+        ("rounding", ctypes.c_int32),
+        ("seed", ctypes.c_uint32),
     ]
 
 
@@ -72,7 +75,7 @@ _SIGS = {
     "lbm_import_f": [_vp, _vp, _i, _i, _vp],
     "lbm_export_f": [_vp, _vp, _i, _i, _vp],
     "lbm_step": [_vp, _i, _vp],
-    "lbm_step_from": [_vp, _vp, _vp, _vp],
+    "lbm_step_from": [_vp, _vp, _vp, ctypes.c_int64, _vp],
     "lbm_save_state": [_vp, _vp, _vp],
     "lbm_load_state": [_vp, _vp, ctypes.c_int64, _vp],
     "lbm_time": [_vp, _P(ctypes.c_int64)],
@@ -114,7 +117,7 @@ def _check(status, ctx=None):
 def make_config(lattice=9, nx=4, ny=4, nz=1, periodic=(1, 1, 1), dx=1.0, dt=1.0, tau=0.8, rho0=1.0,
                 force_model="e", g=(0.0, 0.0, 0.0), lorentz=0, B=(0.0, 0.0, 0.0), E=(0.0, 0.0, 0.0),
                 sigma_e=0.0, mu=1.0, maxwell=0, les=0, cs=0.1, storage="f64", wall_u=(),
-                face_wall=(1, 1, 1, 1, 1, 1), **_ignored) -> LbmConfig:
+                face_wall=(1, 1, 1, 1, 1, 1), rounding="nearest", seed=0, **_ignored) -> LbmConfig:
     c = LbmConfig()
     c.lattice, c.nx, c.ny, c.nz = int(lattice), int(nx), int(ny), int(nz)
     for k in range(3):
@@ -131,6 +134,8 @@ def make_config(lattice=9, nx=4, ny=4, nz=1, periodic=(1, 1, 1), dx=1.0, dt=1.0,
             c.wall_u[i][k] = float(u[k])
     for k in range(6):
         c.face_wall[k] = int(face_wall[k])
+    c.rounding = ROUND[rounding] if isinstance(rounding, str) else int(rounding)
+    c.seed = int(seed) & 0xFFFFFFFF
     return c
 
 
@@ -201,8 +206,8 @@ def lbm_step(ctx, nsteps, stream):
     _check(load().lbm_step(ctx, int(nsteps), stream), ctx)
 
 
-def lbm_step_from(ctx, src, dst, stream):
-    _check(load().lbm_step_from(ctx, _ptr(src), _ptr(dst), stream), ctx)
+def lbm_step_from(ctx, src, dst, t, stream):
+    _check(load().lbm_step_from(ctx, _ptr(src), _ptr(dst), int(t), stream), ctx)
 
 
 def lbm_save_state(ctx, dst, stream):

@@ -102,3 +102,10 @@ def test_2d_maxwell_needs_in_plane_field(lib):
     c = lbm.make_config(**dict(cfg, B=(0.0, 0.05, 0.01)))
     with pytest.raises(lbm.LbmError, match="in-plane"):
         lbm.lbm_buffer_sizes(c, mask)
+
+
+def test_stochastic_rounding_only_for_16_bit(lib):
+    cfg, mask = workloads.poiseuille(nx=8, ny=6, storage="f32")
+    with pytest.raises(lbm.LbmError, match="16-bit"):
+        lbm.lbm_buffer_sizes(lbm.make_config(**dict(cfg, rounding="stochastic")), mask)
+    lbm.lbm_buffer_sizes(lbm.make_config(**dict(cfg, storage="f16s", rounding="stochastic")), mask)

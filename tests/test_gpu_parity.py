@@ -226,3 +226,45 @@ def test_all_solid_domain():
     assert np.all(sim.wall_force(-1) == 0)
     m, M, b = sim.balance()
     assert m == 0 and np.all(M == 0) and np.all(b == 0)
+
+
+@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+def test_stochastic_rounding(orc, storage):
+    """Stochastic rounding of 16-bit stores: within the same bound of the
+    oracle as rounding to nearest, replayed bit for bit by lbm_step_from with
+    the same step index, and dependent on the seed."""
+    cfg, mask = _case("d3q19", "e", storage)
+    cfg = dict(cfg, rounding="stochastic", seed=1234)
+    ocfg, f0, _, _ = _initial(orc, cfg, mask)
+    sim = lbm.Sim(cfg, mask)
+    sim.import_f(f0)
+    sim.step(3)
+    saved = torch.empty(sim.sizes[lbm.BUF_POP_A], dtype=torch.uint8, device=sim.device)
+    lbm.lbm_save_state(sim.ctx, saved, sim.stream)
+    sim.step(7)
+    f_ref = orc.run(ocfg, mask, f0, 10)
+    assert _rel(sim.export_f().cpu().numpy(), f_ref) < TOL[storage]
+    # replay step 3 from the saved state
+    a = torch.empty_like(saved)
+    lbm.lbm_step_from(sim.ctx, saved, a, 3, sim.stream)
+    sim2 = lbm.Sim(cfg, mask)
+    sim2.import_f(f0)
+    sim2.step(4)
+    b = torch.empty_like(saved)
+    lbm.lbm_save_state(sim2.ctx, b, sim2.stream)
+    torch.cuda.synchronize()
+    # populations only (the buffer size is rounded up to 256 bytes)
+    nxp = (cfg["nx"] + 63) // 64 * 64
+    n = cfg["lattice"] * nxp * cfg["ny"] * cfg["nz"] * 2
+    a, b = a[:n], b[:n]
+    assert torch.equal(a, b)
+    # another step index or seed gives other bits
+    c = torch.empty_like(saved)
+    lbm.lbm_step_from(sim.ctx, saved, c, 4, sim.stream)
+    sim3 = lbm.Sim(dict(cfg, seed=99), mask)
+    sim3.import_f(f0)
+    sim3.step(4)
+    e = torch.empty_like(saved)
+    lbm.lbm_save_state(sim3.ctx, e, sim3.stream)
+    torch.cuda.synchronize()
+    assert not torch.equal(a, c[:n]) and not torch.equal(a, e[:n])
