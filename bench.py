@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="headline only")
     p.add_argument("--storage", default="f16s", choices=["f64", "f32", "f16s", "bf16s"],
                    help="storage of the headline run (profiling)")
+    p.add_argument("--rounding", default="stochastic", choices=["nearest", "stochastic"],
+                   help="rounding of 16-bit stores in the headline run")
     p.add_argument("--workload", default="sphere", choices=["sphere", "cavity"],
                    help="headline workload (profiling): sphere 256x128x128 or cavity 256^3 LES")
     return p.parse_args()
@@ -195,6 +197,9 @@ def run_ours(args):
     else:
         cfg, mask = workloads.cavity(n=256, storage=args.storage)
         hwall = 2
+    sr = args.storage in ("f16s", "bf16s") and args.rounding == "stochastic"
+    if sr:
+        cfg = dict(cfg, rounding="stochastic", seed=2024)
     sim = lbm.Sim(cfg, mask)
     sim.rest()
     N = cfg["nx"] * cfg["ny"] * cfg["nz"]
@@ -215,20 +220,24 @@ def run_ours(args):
     value = ws * N * args.steps / (total_ms * 1e-3) / 1e6
     achieved = N * bpn / (kern_ms * 1e-3) / 1e9
     kname = {"f64": "StoreF64", "f32": "StoreF32", "f16s": "StoreF16", "bf16s": "StoreBF16"}[args.storage]
-    roof = {"kernel": f"k_step<19,{kname},{'true' if cfg.get('les') else 'false'}>", "bound": "hbm", "achieved": round(achieved, 1),
+    roof = {"kernel": f"k_step<19,{kname},EXT={int(bool(cfg.get('les')))},SR={int(sr)}>", "bound": "hbm", "achieved": round(achieved, 1),
             "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "peak_source": peak_kind,
             "bytes_per_node": bpn, "step_kernel_ms": round(kern_ms, 5),
             "kernel_mlups": round(N / (kern_ms * 1e-3) / 1e6, 1),
-            "traffic": traffic_for(f"{args.workload}256_{args.storage}")}
+            "traffic": traffic_for(f"{args.workload}256_{args.storage}{'_sr' if sr else ''}")}
     sim.close()
     del sim
     torch.cuda.empty_cache()
 
-    if rank == 0 and not args.no_extras and args.workload == "sphere" and args.storage == "f16s":
+    if rank == 0 and not args.no_extras and args.workload == "sphere" and args.storage == "f16s" and sr:
         # ---- the same workload in the other storage formats, and drag error vs FP64
         variants = {}
-        for storage, steps in (("f32", args.steps), ("bf16s", args.steps), ("f64", max(args.steps // 4, 50))):
+        for key, steps in (("f32", args.steps), ("f16s", args.steps), ("bf16s_sr", args.steps),
+                           ("f64", max(args.steps // 4, 50))):
+            storage = key.split("_")[0]
             c, m = workloads.sphere(storage=storage)
+            if key.endswith("_sr"):
+                c = dict(c, rounding="stochastic", seed=2024)
             s = lbm.Sim(c, m)
             s.rest()
             clocks.active = True
@@ -236,14 +245,14 @@ def run_ours(args):
             clocks.active = False
             bp = bytes_per_node(19, storage)
             ach = N * bp / (k * 1e-3) / 1e9
-            variants[storage] = {"mlups": round(N * steps / (t * 1e-3) / 1e6, 1),
+            variants[key] = {"mlups": round(N * steps / (t * 1e-3) / 1e6, 1),
                                  "kernel_mlups": round(N / (k * 1e-3) / 1e6, 1),
                                  "achieved_gbs": round(ach, 1), "frac": round(ach / hbm, 4)}
             s.close()
             del s
             torch.cuda.empty_cache()
-        variants["f16s"] = {"mlups": round(value / ws, 1), "kernel_mlups": roof["kernel_mlups"],
-                            "achieved_gbs": roof["achieved"], "frac": roof["frac"]}
+        variants["f16s_sr"] = {"mlups": round(value / ws, 1), "kernel_mlups": roof["kernel_mlups"],
+                               "achieved_gbs": roof["achieved"], "frac": roof["frac"]}
         out["storage_variants"] = variants
         out["drag_error_vs_f64"] = drag_errors(torch, lbm, workloads, args.drag_steps)
         out["cavity_les_f32"] = cavity_bench(torch, lbm, workloads, hbm, args)
@@ -260,7 +269,9 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD if args.workload == "sphere" else "D3Q19 LES cavity 256^3",
-                       "nodes": N, "fluid_nodes": fluid, "storage": args.storage,
+                       "nodes": N, "fluid_nodes": fluid,
+                       "storage": args.storage + (" (shifted x2^12, stochastic rounding)" if sr and args.storage == "f16s"
+                                                  else (" (stochastic rounding)" if sr else "")),
                        "compute": "f32", "step": "fused collide-stream + FP64 drag reduction",
                        "l2": f"inputs larger than L2: {N * (bpn - 1) / 2 / 1e6:.0f} MB of populations read and the same "
                   "written per step",
@@ -366,6 +377,7 @@ def e2e_bench(torch, lbm, workloads, args):
     copied from pinned host memory, every step reads its drag back to the host,
     and the final state is copied back to the host."""
     c, m = workloads.sphere(storage="f16s")
+    c = dict(c, rounding="stochastic", seed=2024)
     s = lbm.Sim(c, m)
     N = c["nx"] * c["ny"] * c["nz"]
     s.rest()

@@ -33,9 +33,8 @@ class DragProblem:
         dev = sim.device
         pb = sim.sizes[lbm.BUF_POP_A]
         self.ckpt = torch.empty((self.nseg, pb), dtype=torch.uint8, device=dev)
-        self.seg = torch.empty((max(self.k - 1, 1), pb), dtype=torch.uint8, device=dev)
-        ab = lbm.lbm_adjoint_buffer_bytes(sim.ctx)
-        self.phi = [torch.empty(ab, dtype=torch.uint8, device=dev) for _ in range(2)]
+        self.seg = None        # recomputed states and adjoint buffers: allocated by backward()
+        self.phi = None
         self.Facc = torch.zeros(3, dtype=torch.float64, device=dev)
         self.theta = None
 
@@ -65,6 +64,11 @@ class DragProblem:
         s = self.sim
         st = s.stream
         ctx = s.ctx
+        if self.seg is None:
+            pb = s.sizes[lbm.BUF_POP_A]
+            self.seg = torch.empty((max(self.k - 1, 1), pb), dtype=torch.uint8, device=s.device)
+            ab = lbm.lbm_adjoint_buffer_bytes(ctx)
+            self.phi = [torch.empty(ab, dtype=torch.uint8, device=s.device) for _ in range(2)]
         lbm.lbm_adjoint_reset(ctx, st)
         phi_next, cur = None, 0
         for sg in reversed(range(self.nseg)):

@@ -118,6 +118,10 @@ void build_geometry(const lbm_config* c, const uint8_t* wid, int nxp, std::vecto
 {
     cls.assign((size_t)nxp * c->ny * c->nz, NC_PAD);
     std::vector<Link> raw;
+    const long long N = (long long)c->nx * c->ny * c->nz;
+    bool any_solid = false;
+    for (long long n = 0; n < N && !any_solid; ++n) any_solid = wid[n] != 0;
+    const int per[3] = {c->periodic[0], c->periodic[1], Q == 9 ? 1 : c->periodic[2]};
     for (int z = 0; z < c->nz; ++z)
         for (int y = 0; y < c->ny; ++y)
             for (int x = 0; x < c->nx; ++x) {
@@ -125,6 +129,12 @@ void build_geometry(const lbm_config* c, const uint8_t* wid, int nxp, std::vecto
                 const long long np = ((long long)z * c->ny + y) * nxp + x;
                 if (wid[n]) {
                     cls[np] = nc_make_solid(wid[n]);
+                    continue;
+                }
+                // all-fluid geometry: only nodes on a closed face have wall links
+                if (!any_solid && (per[0] || (x > 0 && x < c->nx - 1)) && (per[1] || (y > 0 && y < c->ny - 1)) &&
+                    (per[2] || (z > 0 && z < c->nz - 1))) {
+                    cls[np] = NC_BULK;
                     continue;
                 }
                 bool face = false, solid = false;
