@@ -674,8 +674,11 @@ k_stress(const typename S::T* __restrict__ cur, const typename S::T* __restrict_
 // One reverse step of the drag adjoint (uniform body force, any model).
 // psi_a(x) = phi_next_a(x + E_a) through a fluid link, or phi_next_opp(a)(x)
 // plus the drag seed through a link into the target wall; then
-// phi_b = (1 - om) psi_b + A_rho + E_b . B_j from the omega-weighted moments
-// of psi (see the transpose of node_macro/node_relax in the comments below).
+// phi_b = (1 - om) psi_b + A_rho + E_b . B_j, where A_rho and B_j collect the
+// derivatives of G = f^eq/tau + F with respect to rho and j, formed from the
+// weighted moments s0 = sum w psi, s1 = sum w psi E, s2 = sum w psi E E.
+// The node streams its data: the forward populations only feed the
+// moments, psi is read once for the moments and again for the output.
 template <int Q, class S>
 __global__ void __launch_bounds__(RED_THREADS)
 k_adjoint(const typename S::T* __restrict__ Pprev, const typename S::R* __restrict__ phin,
@@ -699,41 +702,62 @@ k_adjoint(const typename S::T* __restrict__ Pprev, const typename S::R* __restri
             for (int a = 0; a < Q; ++a) phio[(long long)a * g.sq + n] = R(0);
             continue;
         }
-        // transpose of propagation and drag seeds
-        R psi[Q];
+        const bool bulk = (cl == NC_BULK);
+        // index of x + E_a (periodic wrap), for bulk nodes
+        auto plus = [&](int a) -> long long {
+            const int xp = wrapi(x + EX<Q>(a), g.nx), yp = wrapi(y + EY<Q>(a), g.ny);
+            const int zp = (Q == 19) ? wrapi(z + EZ<Q>(a), g.nz) : 0;
+            return ((long long)zp * g.ny + yp) * g.nxp + xp;
+        };
+        // forward state f(t): moments only
+        Mom<R> mo;
+        mom_zero(mo);
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
+            R v;
+            if (bulk) {
+                v = S::to_r(Pprev[(long long)a * g.sq + plus(OPP<Q>(a))]);
+            } else {
+                long long sidx;
+                int wall;
+                if (a == 0) v = S::to_r(Pprev[n]);
+                else if (pull_source(g, cls, x, y, z, EX<Q>(a), EY<Q>(a), EZ<Q>(a), sidx, wall))
+                    v = S::to_r(Pprev[(long long)a * g.sq + sidx]);
+                else
+                    v = S::to_r(Pprev[(long long)OPP<Q>(a) * g.sq + n]) + ladd_of<Q, R>(p, a, wall);
+            }
+            mom_add<R, Q, false>(mo, a, v);
+        }
+        NodeM<R> m;
+        macro_from_moments<R, Q, false>(mo, p, m);
+        // psi_a, with the drag seeds; `grads` adds the u_w terms (first pass only)
+        auto psi_of = [&](int a, bool grads) -> R {
+            if (bulk) return phin ? phin[(long long)a * g.sq + plus(a)] : R(0);
             long long dn;
             int wall;
-            if (a == 0) {
-                psi[0] = phin ? phin[n] : R(0);
-            } else if (pull_source(g, cls, x, y, z, EX<Q>(OPP<Q>(a)), EY<Q>(OPP<Q>(a)), EZ<Q>(OPP<Q>(a)), dn, wall)) {
-                psi[a] = phin ? phin[(long long)a * g.sq + dn] : R(0);
-            } else {
-                const double back = phin ? (double)phin[(long long)OPP<Q>(a) * g.sq + n] : 0.0;
-                double ps = back;
-                if (wall == target) {
-                    const double de = c * (d0 * EX<Q>(a) + d1 * EY<Q>(a) + d2 * EZ<Q>(a));
-                    ps += seedw * 2.0 * svol * de;
+            if (a == 0) return phin ? phin[n] : R(0);
+            if (pull_source(g, cls, x, y, z, EX<Q>(OPP<Q>(a)), EY<Q>(OPP<Q>(a)), EZ<Q>(OPP<Q>(a)), dn, wall))
+                return phin ? phin[(long long)a * g.sq + dn] : R(0);
+            const double back = phin ? (double)phin[(long long)OPP<Q>(a) * g.sq + n] : 0.0;
+            double ps = back;
+            if (wall == target) {
+                const double de = c * (d0 * EX<Q>(a) + d1 * EY<Q>(a) + d2 * EZ<Q>(a));
+                ps += seedw * 2.0 * svol * de;
+                if (grads) {
                     // u_w enters f(t+1) and F_t through the Ladd term -6 w rho0 E.u_w / c
                     const double gl = -6.0 * WD<Q>(a) * rho0 / c * (back + seedw * svol * de);
                     acc[3] += gl * EX<Q>(a);
                     acc[4] += gl * EY<Q>(a);
                     acc[5] += gl * EZ<Q>(a);
                 }
-                psi[a] = R(ps);
             }
-        }
-        // forward node state at f(t)
-        R d[Q];
-        gather_node<Q, S>(Pprev, cls, g, p, x, y, z, d);
-        NodeM<R> m;
-        node_macro<R, Q, false>(d, p, m);
+            return R(ps);
+        };
         // omega-weighted moments of psi
         R s0 = 0, s1[3] = {0, 0, 0}, s2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            const R wp = R(WD<Q>(a)) * psi[a];
+            const R wp = R(WD<Q>(a)) * psi_of(a, true);
             const int e[3] = {EX<Q>(a), EY<Q>(a), EZ<Q>(a)};
             s0 += wp;
 #pragma unroll
@@ -791,7 +815,7 @@ k_adjoint(const typename S::T* __restrict__ Pprev, const typename S::R* __restri
         }
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
-            const R phib = (R(1) - m.om) * psi[b] + Arho + R(EX<Q>(b)) * Bj[0] + R(EY<Q>(b)) * Bj[1] +
+            const R phib = (R(1) - m.om) * psi_of(b, false) + Arho + R(EX<Q>(b)) * Bj[0] + R(EY<Q>(b)) * Bj[1] +
                            R(EZ<Q>(b)) * Bj[2];
             phio[(long long)b * g.sq + n] = phib;
         }
@@ -969,8 +993,11 @@ cudaError_t launch_adjoint(const Ctx& c, const void* Pprev, const void* phin, vo
 {
     using T = typename S::T;
     using R = typename S::R;
-    k_adjoint<Q, S><<<ADJ_BLOCKS, RED_THREADS, 0, st>>>((const T*)Pprev, (const R*)phin, (R*)phio, c.cls, c.geo,
-                                                        kp_of<S>(c), wall, dir[0], dir[1], dir[2], seedw, partials);
+    // a fixed grid per context, so every block owns the same partial row each step
+    const long long NP = (long long)c.geo.nxp * c.geo.ny * c.geo.nz;
+    const int blocks = grid_for(NP, RED_THREADS, ADJ_BLOCKS);
+    k_adjoint<Q, S><<<blocks, RED_THREADS, 0, st>>>((const T*)Pprev, (const R*)phin, (R*)phio, c.cls, c.geo,
+                                                    kp_of<S>(c), wall, dir[0], dir[1], dir[2], seedw, partials);
     return cudaGetLastError();
 }
 

@@ -77,8 +77,17 @@ def test_hartmann_256x128_closed_form(storage, tau):
     assert abs(Fb[0] - L * nu * dudy(-H)) < 3e-3 * scale
     assert abs(Ft[0] + L * nu * dudy(H)) < 3e-3 * scale
     _, _, body = sim.balance()
-    tol = 1e-9 if storage == "f64" else 1e-4
-    assert abs((Fb[0] + Ft[0]) / body[0] - 1) < tol
+    imbalance = abs(Fb[0] + Ft[0] - body[0])
+    if storage == "f64":
+        assert imbalance < 1e-9 * abs(body[0])
+    else:
+        # a rounded fixed point conserves momentum per step only up to the
+        # rounding of every stored deviation, N Q 2^-24 max|d|; the flow is
+        # uniform in x, so the columns' rounding errors add coherently
+        w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+        d = sim.export_f().cpu().numpy()[:, 0] - w[:, None, None] * cfg.get("rho0", 1.0)
+        bound = 256 * 128 * 9 * 2.0 ** -24 * np.abs(d).max()
+        assert imbalance < bound
 
 
 def test_hartmann_full_size_parity_and_maxwell_removal(orc):
