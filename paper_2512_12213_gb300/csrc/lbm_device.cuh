@@ -89,7 +89,7 @@ struct StoreF32 {
 // binary16 holds 2^12 d: typical deviations 1e-5..1e-1 then sit in the normal
 // range of the format (min normal 6.1e-5, max 65504).
 struct StoreF16 {
-    using T = __half; using R = float; static constexpr int V = 8;
+    using T = __half; using R = float; static constexpr int V = 4;
     static constexpr double SCALE = 4096.0;
     __device__ static R to_r(T x) { return __half2float(x) * (1.0f / 4096.0f); }
     __device__ static T from_r(R x) { return __float2half_rn(x * 4096.0f); }
@@ -130,9 +130,19 @@ struct StoreF16 {
         memcpy(&w, &h, 4);
         return w;
     }
+    // a (low half) and b (high half) rounded stochastically: the bits are
+    // added as in from_raw_sr, then one truncating conversion packs both
+    __device__ static uint32_t pack2_sr(float a, float b, uint32_t ra, uint32_t rb)
+    {
+        const float ta = __uint_as_float(__float_as_uint(a) + (ra & 0x1FFFu));
+        const float tb = __uint_as_float(__float_as_uint(b) + (rb & 0x1FFFu));
+        uint32_t w;
+        asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(tb), "f"(ta));   // first source -> high half
+        return w;
+    }
 };
 struct StoreBF16 {
-    using T = __nv_bfloat16; using R = float; static constexpr int V = 8;
+    using T = __nv_bfloat16; using R = float; static constexpr int V = 4;
     static constexpr double SCALE = 1.0;
     __device__ static R to_r(T x) { return __bfloat162float(x); }
     __device__ static T from_r(R x) { return __float2bfloat16_rn(x); }
@@ -170,11 +180,23 @@ struct StoreBF16 {
         memcpy(&w, &h, 4);
         return w;
     }
+    // a (low half) and b (high half) rounded stochastically, as from_raw_sr
+    __device__ static uint32_t pack2_sr(float a, float b, uint32_t ra, uint32_t rb)
+    {
+        const uint32_t ua = __float_as_uint(a) + (ra & 0xFFFFu);
+        const uint32_t ub = __float_as_uint(b) + (rb & 0xFFFFu);
+        return __byte_perm(ua, ub, 0x7632);
+    }
 };
 
-template <class T, int V> union Vec16 {
-    uint4 raw;
+// one thread's vector of V consecutive stored values (16 or 8 bytes)
+template <int B> struct RawVec;
+template <> struct RawVec<16> { using type = uint4; };
+template <> struct RawVec<8> { using type = uint2; };
+template <class T, int V> union VecN {
+    typename RawVec<sizeof(T) * V>::type raw;
     T e[V];
+    uint32_t u[sizeof(T) * V / 4];
 };
 
 // ------------------------------------------------- counter-based random bits

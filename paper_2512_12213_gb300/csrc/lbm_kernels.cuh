@@ -108,8 +108,13 @@ __device__ __forceinline__ bool row_out(const FaceInfo& fi, int a, int& wall)
     return false;
 }
 
-// blocks per SM the register allocation must allow (4 x 128 threads)
-template <class S> struct StepOcc { static constexpr int value = sizeof(typename S::T) == 8 ? 3 : 4; };
+// blocks of 128 threads per SM the register allocation must allow
+#ifndef LBM_OCC16
+#define LBM_OCC16 5
+#endif
+template <class S> struct StepOcc {
+    static constexpr int value = sizeof(typename S::T) == 8 ? 3 : (sizeof(typename S::T) == 2 ? LBM_OCC16 : 4);
+};
 
 template <int Q, class S, bool EXT, bool FACES, bool SR>
 __global__ void __launch_bounds__(STEP_THREADS, StepOcc<S>::value)
@@ -185,8 +190,9 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
         // bounced rows read the node's own value of the opposite direction
         const T* rp = rout ? src + (long long)OPP<Q>(a) * g.sq + own
                            : src + (long long)a * g.sq + roff[EY<Q>(a) + 1][EZ<Q>(a) + 1];
-        Vec16<T, V> raw;
-        raw.raw = __ldg(reinterpret_cast<const uint4*>(rp + x0));
+        using RawT = typename RawVec<sizeof(T) * V>::type;
+        VecN<T, V> raw;
+        raw.raw = __ldg(reinterpret_cast<const RawT*>(rp + x0));
         const int ex = rout ? 0 : EX<Q>(a);
         T edge = raw.e[0];
         if constexpr (!FACES) {
@@ -216,7 +222,7 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
             }
         }
         if constexpr (PACKED) {
-            const uint32_t rw[4] = {raw.raw.x, raw.raw.y, raw.raw.z, raw.raw.w};
+            const uint32_t* rw = raw.u;
             Bits16<T> eb;
             eb.t = edge;
             const uint32_t ew = (uint32_t)eb.s;
@@ -267,41 +273,47 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
     const long long base = row * g.nxp + x0;
     if (!special) {
         if constexpr (PACKED) {
-            // rolled loop over the V/2 packed words (two nodes each), used as a
-            // queue: relax the front word's two nodes, append the result at the
-            // back; after V/2 turns the words are the results, in order.  This
-            // keeps the code of two node updates instead of V.
-#pragma unroll 1
+            // two nodes per packed word: unpack both, relax them, pack both
+            // with one conversion
+#pragma unroll
             for (int i = 0; i < V / 2; ++i) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    R d[Q];
-#pragma unroll
-                    for (int a = 0; a < Q; ++a) d[a] = S::half_of(w[a][0], h == 1);
-                    if (ladd) add_ladd(d, 2 * i + h);
-                    NodeM<R> m;
-                    node_macro<R, Q, EXT>(d, p, m);
-                    node_relax<R, Q, EXT>(d, p, m);
-                    if constexpr (SR) {
-                        NodeRng rng((uint32_t)(base + 2 * i + h), seed);
-#pragma unroll
-                        for (int a = 0; a < Q; ++a) w[a][0] = S::put_half_sr(w[a][0], h == 1, d[a], rng.bits(a));
-                    } else {
-#pragma unroll
-                        for (int a = 0; a < Q; ++a) w[a][0] = S::put_half(w[a][0], h == 1, d[a]);
-                    }
-                }
+                R d0[Q], d1[Q];
 #pragma unroll
                 for (int a = 0; a < Q; ++a) {
-                    const uint32_t front = w[a][0];
+                    const float2 v = S::unpack2(w[a][i]);
+                    d0[a] = v.x;
+                    d1[a] = v.y;
+                }
+                if (ladd) {
+                    add_ladd(d0, 2 * i);
+                    add_ladd(d1, 2 * i + 1);
+                }
+                {
+                    NodeM<R> m;
+                    node_macro<R, Q, EXT>(d0, p, m);
+                    node_relax<R, Q, EXT>(d0, p, m);
+                }
+                {
+                    NodeM<R> m;
+                    node_macro<R, Q, EXT>(d1, p, m);
+                    node_relax<R, Q, EXT>(d1, p, m);
+                }
+                if constexpr (SR) {
+                    NodeRng r0((uint32_t)(base + 2 * i), seed), r1((uint32_t)(base + 2 * i + 1), seed);
 #pragma unroll
-                    for (int j = 0; j < V / 2 - 1; ++j) w[a][j] = w[a][j + 1];
-                    w[a][V / 2 - 1] = front;
+                    for (int a = 0; a < Q; ++a) w[a][i] = S::pack2_sr(d0[a], d1[a], r0.bits(a), r1.bits(a));
+                } else {
+#pragma unroll
+                    for (int a = 0; a < Q; ++a) w[a][i] = S::pack2(d0[a], d1[a]);
                 }
             }
 #pragma unroll
-            for (int a = 0; a < Q; ++a)
-                *reinterpret_cast<uint4*>(dst + (long long)a * g.sq + base) = make_uint4(w[a][0], w[a][1], w[a][2], w[a][3]);
+            for (int a = 0; a < Q; ++a) {
+                VecN<T, V> o;
+#pragma unroll
+                for (int i = 0; i < V / 2; ++i) o.u[i] = w[a][i];
+                *reinterpret_cast<typename RawVec<sizeof(T) * V>::type*>(dst + (long long)a * g.sq + base) = o.raw;
+            }
         } else {
             if constexpr (EXT) {
                 // larger node code (Lorentz / Maxwell / LES): the same rolled queue
@@ -337,10 +349,10 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
             }
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
-                Vec16<T, V> o;
+                VecN<T, V> o;
 #pragma unroll
                 for (int k = 0; k < V; ++k) o.e[k] = f[a][k];
-                *reinterpret_cast<uint4*>(dst + (long long)a * g.sq + base) = o.raw;
+                *reinterpret_cast<typename RawVec<sizeof(T) * V>::type*>(dst + (long long)a * g.sq + base) = o.raw;
             }
         }
         return;
