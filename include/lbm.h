@@ -26,7 +26,16 @@
  *              Device pointers must be 256-byte aligned.
  *   Streams  : `stream` is a cudaStream_t passed as void* (NULL = the legacy
  *              default stream).  Device work is asynchronous on it; a call that
- *              writes a host buffer synchronises that stream before returning.
+ *              writes a host buffer synchronises that stream before returning,
+ *              except a reduction asked for LBM_OUT_HOST_ASYNC output.
+ *   Outputs  : the reductions (wall force, balance, adjoint gradient) take
+ *              `out_on_host`: LBM_OUT_DEVICE (0) device memory written in
+ *              stream order; LBM_OUT_HOST (1) any host memory, the call
+ *              synchronises; LBM_OUT_HOST_ASYNC (2) page-locked host memory
+ *              written by a copy in stream order, valid once the stream has
+ *              been synchronised (LBM_ERR_ARG for pageable memory or with
+ *              LBM_ACCUMULATE).  Reductions of one context share its scratch,
+ *              so they must not be in flight on two streams at once.
  *   Units    : physical (dx, dt, c = dx/dt); forces are per unit depth in 2-D.
  *   Layout   : canonical arrays exchanged with the caller are dense C arrays,
  *              node index n = (z*ny + y)*nx + x; populations f[a][n] (a the
@@ -99,6 +108,9 @@ enum {
     LBM_MAXWELL_REMOVE = 2,   /* subtract 2 e_a' Delta_a' per link (Maxwell stress) */
     LBM_ACCUMULATE = 4        /* out += weight * F instead of out = weight * F */
 };
+
+/* where the `out` argument of a reduction lives (see Outputs above) */
+enum { LBM_OUT_DEVICE = 0, LBM_OUT_HOST = 1, LBM_OUT_HOST_ASYNC = 2 };
 
 /* caller-allocated device buffers, indexed by kind */
 enum {
@@ -228,9 +240,11 @@ lbm_status lbm_stress(lbm_ctx* ctx, int variant, void* sigma, void* S, void* rho
 
 /* Momentum-exchange force of Eq. (25) exerted during the last step (T-1 -> T)
  * on wall `wall` (every wall if wall < 0), times `weight`; flags
- * LBM_MOVING_CORR | LBM_MAXWELL_REMOVE | LBM_ACCUMULATE.  out: 3 doubles on
- * the host (synchronises) or device.  Needs T >= 1.  Reduction: per-link FP64
- * terms, warp shuffle, block, then a fixed-order pass (deterministic). */
+ * LBM_MOVING_CORR | LBM_MAXWELL_REMOVE | LBM_ACCUMULATE.  out: 3 doubles,
+ * placed as out_on_host says.  Needs T >= 1.  Reduction: per-link FP64 terms,
+ * warp shuffle, block, then a fixed-order pass (deterministic).  It reads the
+ * stored state only, so it may run beside the lbm_step that advances from
+ * the same state (on another stream, ordered after the previous step). */
 lbm_status lbm_wall_force(lbm_ctx* ctx, int wall, unsigned flags, double weight, double* out,
                           int out_on_host, void* stream);
 

@@ -355,15 +355,20 @@ size_t pop_bytes(const Ctx& x) { return (size_t)x.cfg.lattice * x.geo.sq * x.ele
     if (!guard_.ok) return cuda_fail((x), cudaErrorInvalidDevice, "set device");
 
 // reduce nb partial rows of width W into out (device or host)
-lbm_status finish_reduce(Ctx& x, const double* partials, int nb, int W, double* out, bool on_host, double weight,
+// the mode was checked by out_mode_ok before any launch
+lbm_status finish_reduce(Ctx& x, const double* partials, int nb, int W, double* out, int mode, double weight,
                          bool accumulate, cudaStream_t st)
 {
-    if (!on_host) {
+    if (mode == LBM_OUT_DEVICE) {
         CK(launch_reduce_rows(partials, nb, W, out, weight, accumulate ? 1 : 0, st), "reduce");
         return LBM_OK;
     }
     double* slot = x.scratch + SCRATCH_OUT_OFF;
     CK(launch_reduce_rows(partials, nb, W, slot, weight, 0, st), "reduce");
+    if (mode == LBM_OUT_HOST_ASYNC) {
+        CK(cudaMemcpyAsync(out, slot, sizeof(double) * W, cudaMemcpyDeviceToHost, st), "copy result");
+        return LBM_OK;
+    }
     double tmp[8];
     CK(cudaMemcpyAsync(tmp, slot, sizeof(double) * W, cudaMemcpyDeviceToHost, st), "copy result");
     CK(cudaStreamSynchronize(st), "synchronize");
@@ -708,13 +713,14 @@ lbm_status lbm_wall_force(lbm_ctx* ctx, int wall, unsigned flags, double weight,
         return LBM_ERR_STATE;
     }
     GUARD(x);
+    if (!out_mode_ok(out_on_host, (flags & LBM_ACCUMULATE) != 0, out, x.err)) return LBM_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const long long b = wall < 0 ? 0 : x.wall_begin[wall];
     const long long e = wall < 0 ? x.n_links : x.wall_begin[wall + 1];
     double* part = x.scratch + SCRATCH_RED_OFF;
     int nb = 0;
     if (e > b) CK(x.ops->links(x, x.pop[x.cur], b, e, flags & 3u, part, &nb, st), "link kernel");
-    return finish_reduce(x, part, nb, 3, out, out_on_host != 0, weight, (flags & LBM_ACCUMULATE) != 0, st);
+    return finish_reduce(x, part, nb, 3, out, out_on_host, weight, (flags & LBM_ACCUMULATE) != 0, st);
 }
 
 lbm_status lbm_balance(lbm_ctx* ctx, double* out, int out_on_host, void* stream)
@@ -723,11 +729,12 @@ lbm_status lbm_balance(lbm_ctx* ctx, double* out, int out_on_host, void* stream)
     Ctx& x = ctx->c;
     if (!out) return arg_fail(x, "out is NULL");
     GUARD(x);
+    if (!out_mode_ok(out_on_host, false, out, x.err)) return LBM_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     double* part = x.scratch + SCRATCH_RED_OFF;
     int nb = 0;
     CK(x.ops->balance(x, x.pop[x.cur], part, &nb, st), "balance kernel");
-    return finish_reduce(x, part, nb, 7, out, out_on_host != 0, 1.0, false, st);
+    return finish_reduce(x, part, nb, 7, out, out_on_host, 1.0, false, st);
 }
 
 lbm_status lbm_adjoint_buffer_bytes(const lbm_ctx* ctx, size_t* bytes)
@@ -770,7 +777,8 @@ lbm_status lbm_adjoint_gradient(lbm_ctx* ctx, double* out, int out_on_host, void
     Ctx& x = ctx->c;
     if (!out) return arg_fail(x, "out is NULL");
     GUARD(x);
-    return finish_reduce(x, x.scratch + SCRATCH_ADJ_OFF, ADJ_BLOCKS, 6, out, out_on_host != 0, 1.0, false,
+    if (!out_mode_ok(out_on_host, false, out, x.err)) return LBM_ERR_ARG;
+    return finish_reduce(x, x.scratch + SCRATCH_ADJ_OFF, ADJ_BLOCKS, 6, out, out_on_host, 1.0, false,
                          (cudaStream_t)stream);
 }
 

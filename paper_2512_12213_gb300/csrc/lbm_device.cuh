@@ -102,26 +102,20 @@ struct StoreF16 {
         memcpy(&h, &w, 4);
         return __half22float2(h);
     }
-    // one half of a packed word as float / the word with that half replaced
-    __device__ static float half_of(uint32_t w, bool hi)
+    // stochastic rounding by the sm_100-family convert: the magnitude is
+    // rounded up with probability equal to the discarded fraction of one unit
+    // in the last place (13 random bits per value: bits 0-12 of r for the low
+    // half, 16-28 for the high half; exact in the subnormal range too),
+    // saturating to the largest finite value
+    __device__ static uint32_t cvt_rs(float hi, float lo, uint32_t r)
     {
-        return __half2float(__ushort_as_half((unsigned short)(hi ? (w >> 16) : (w & 0xFFFFu))));
+        uint32_t w;
+        asm volatile("cvt.rs.satfinite.f16x2.f32 %0, %1, %2, %3;" : "=r"(w) : "f"(hi), "f"(lo), "r"(r));
+        return w;
     }
-    __device__ static uint32_t put_half(uint32_t w, bool hi, float v)
-    {
-        const uint32_t b = (uint32_t)__half_as_ushort(__float2half_rn(v));
-        return hi ? __byte_perm(w, b, 0x5410) : __byte_perm(w, b, 0x3254);
-    }
-    // stochastic rounding: add 13 random bits below the binary16 mantissa to
-    // the magnitude, then truncate (round up with probability = remainder)
     __device__ static T from_raw_sr(float v, uint32_t r)
     {
-        return __float2half_rz(__uint_as_float(__float_as_uint(v) + (r & 0x1FFFu)));
-    }
-    __device__ static uint32_t put_half_sr(uint32_t w, bool hi, float v, uint32_t r)
-    {
-        const uint32_t b = (uint32_t)__half_as_ushort(from_raw_sr(v, r));
-        return hi ? __byte_perm(w, b, 0x5410) : __byte_perm(w, b, 0x3254);
+        return __ushort_as_half((unsigned short)(cvt_rs(0.0f, v, r) & 0xFFFFu));
     }
     __device__ static uint32_t pack2(float a, float b)
     {
@@ -130,16 +124,9 @@ struct StoreF16 {
         memcpy(&w, &h, 4);
         return w;
     }
-    // a (low half) and b (high half) rounded stochastically: the bits are
-    // added as in from_raw_sr, then one truncating conversion packs both
-    __device__ static uint32_t pack2_sr(float a, float b, uint32_t ra, uint32_t rb)
-    {
-        const float ta = __uint_as_float(__float_as_uint(a) + (ra & 0x1FFFu));
-        const float tb = __uint_as_float(__float_as_uint(b) + (rb & 0x1FFFu));
-        uint32_t w;
-        asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(tb), "f"(ta));   // first source -> high half
-        return w;
-    }
+    // a (low half) and b (high half) rounded stochastically with the two
+    // 13-bit fields of one random word
+    __device__ static uint32_t pack2_sr(float a, float b, uint32_t r) { return cvt_rs(b, a, r); }
 };
 struct StoreBF16 {
     using T = __nv_bfloat16; using R = float; static constexpr int V = 4;
@@ -154,24 +141,18 @@ struct StoreBF16 {
         memcpy(&h, &w, 4);
         return __bfloat1622float2(h);
     }
-    __device__ static float half_of(uint32_t w, bool hi)
+    // stochastic rounding by the sm_100-family convert: 16 random bits per
+    // value (bits 0-15 of r for the low half, 16-31 for the high half), the
+    // magnitude rounded up with probability equal to the discarded fraction
+    __device__ static uint32_t cvt_rs(float hi, float lo, uint32_t r)
     {
-        return __uint_as_float(hi ? (w & 0xFFFF0000u) : (w << 16));
+        uint32_t w;
+        asm volatile("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;" : "=r"(w) : "f"(hi), "f"(lo), "r"(r));
+        return w;
     }
-    __device__ static uint32_t put_half(uint32_t w, bool hi, float v)
-    {
-        const uint32_t b = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v));
-        return hi ? __byte_perm(w, b, 0x5410) : __byte_perm(w, b, 0x3254);
-    }
-    // stochastic rounding: 16 random bits below the bfloat16 mantissa, truncate
     __device__ static T from_raw_sr(float v, uint32_t r)
     {
-        return __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + (r & 0xFFFFu)) >> 16));
-    }
-    __device__ static uint32_t put_half_sr(uint32_t w, bool hi, float v, uint32_t r)
-    {
-        const uint32_t b = (uint32_t)__bfloat16_as_ushort(from_raw_sr(v, r));
-        return hi ? __byte_perm(w, b, 0x5410) : __byte_perm(w, b, 0x3254);
+        return __ushort_as_bfloat16((unsigned short)(cvt_rs(0.0f, v, r) & 0xFFFFu));
     }
     __device__ static uint32_t pack2(float a, float b)
     {
@@ -180,13 +161,9 @@ struct StoreBF16 {
         memcpy(&w, &h, 4);
         return w;
     }
-    // a (low half) and b (high half) rounded stochastically, as from_raw_sr
-    __device__ static uint32_t pack2_sr(float a, float b, uint32_t ra, uint32_t rb)
-    {
-        const uint32_t ua = __float_as_uint(a) + (ra & 0xFFFFu);
-        const uint32_t ub = __float_as_uint(b) + (rb & 0xFFFFu);
-        return __byte_perm(ua, ub, 0x7632);
-    }
+    // a (low half) and b (high half) rounded stochastically with the two
+    // 16-bit fields of one random word
+    __device__ static uint32_t pack2_sr(float a, float b, uint32_t r) { return cvt_rs(b, a, r); }
 };
 
 // one thread's vector of V consecutive stored values (16 or 8 bytes)
@@ -202,7 +179,9 @@ template <class T, int V> union VecN {
 // ------------------------------------------------- counter-based random bits
 // 32-bit integer hash (a multiply-xorshift finaliser) of a counter, and the
 // per-node stream: one hash of (node, step seed), then a linear congruential
-// step per pair of populations (16 bits each).
+// step per random word.  bits(a) gives a node's populations 16 bits each
+// (two per word); word() gives one 32-bit word, whose two halves round the
+// same direction of the two nodes of a packed pair.
 __host__ __device__ inline uint32_t hash32(uint32_t x)
 {
     x ^= x >> 16;
@@ -221,6 +200,14 @@ struct NodeRng {
         if ((a & 1) == 0) s = s * 747796405u + 2891336453u;
         const uint32_t r = s ^ (s >> 13);
         return (a & 1) ? (r >> 16) : r;
+    }
+    // (the empty volatile statement keeps each word next to the conversion
+    // that consumes it, instead of all of them held in registers at once)
+    __device__ uint32_t word()
+    {
+        s = s * 747796405u + 2891336453u;
+        asm volatile("" : "+r"(s));
+        return s ^ (s >> 13);
     }
 };
 

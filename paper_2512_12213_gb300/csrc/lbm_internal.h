@@ -20,6 +20,33 @@ struct Link {
     uint16_t wall;
 };
 
+// out_on_host of a reduction: LBM_OUT_DEVICE / LBM_OUT_HOST always; the
+// asynchronous host copy only into page-locked memory and without
+// accumulation (the host value would be read before the copy lands)
+inline bool out_mode_ok(int mode, bool accumulate, const void* out, std::string& err)
+{
+    if (mode < LBM_OUT_DEVICE || mode > LBM_OUT_HOST_ASYNC) {
+        err = "out_on_host must be LBM_OUT_DEVICE, LBM_OUT_HOST or LBM_OUT_HOST_ASYNC";
+        return false;
+    }
+    if (mode != LBM_OUT_HOST_ASYNC) return true;
+    if (accumulate) {
+        err = "LBM_OUT_HOST_ASYNC cannot be combined with LBM_ACCUMULATE";
+        return false;
+    }
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, out) != cudaSuccess) {
+        cudaGetLastError();
+        err = "LBM_OUT_HOST_ASYNC: cannot query the output pointer";
+        return false;
+    }
+    if (a.type != cudaMemoryTypeHost) {
+        err = "LBM_OUT_HOST_ASYNC needs page-locked host memory";
+        return false;
+    }
+    return true;
+}
+
 constexpr int MAX_PARTIAL_ROWS = 1024;   // block partials of one reduction
 constexpr int ADJ_BLOCKS = 2048;         // fixed grid of the adjoint kernel
 constexpr int PARTIAL_WIDTH = 8;         // doubles per partial row

@@ -108,16 +108,14 @@ __device__ __forceinline__ bool row_out(const FaceInfo& fi, int a, int& wall)
     return false;
 }
 
-// blocks of 128 threads per SM the register allocation must allow
-#ifndef LBM_OCC16
-#define LBM_OCC16 5
-#endif
-template <class S> struct StepOcc {
-    static constexpr int value = sizeof(typename S::T) == 8 ? 3 : (sizeof(typename S::T) == 2 ? LBM_OCC16 : 4);
+// blocks of 128 threads per SM the register allocation must allow: FP64 3
+// (168 registers), FP32 and the larger node code of EXT 4 (128), 16-bit 5 (96)
+template <class S, bool EXT> struct StepOcc {
+    static constexpr int value = sizeof(typename S::T) == 8 ? 3 : ((sizeof(typename S::T) == 2 && !EXT) ? 5 : 4);
 };
 
 template <int Q, class S, bool EXT, bool FACES, bool SR>
-__global__ void __launch_bounds__(STEP_THREADS, StepOcc<S>::value)
+__global__ void __launch_bounds__(STEP_THREADS, StepOcc<S, EXT>::value)
 k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
        const uint8_t* __restrict__ cls, const Geo g, const KP<typename S::R> p, uint32_t seed)
 {
@@ -299,9 +297,9 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                     node_relax<R, Q, EXT>(d1, p, m);
                 }
                 if constexpr (SR) {
-                    NodeRng r0((uint32_t)(base + 2 * i), seed), r1((uint32_t)(base + 2 * i + 1), seed);
+                    NodeRng rp((uint32_t)(base + 2 * i), seed);     // the pair's first node
 #pragma unroll
-                    for (int a = 0; a < Q; ++a) w[a][i] = S::pack2_sr(d0[a], d1[a], r0.bits(a), r1.bits(a));
+                    for (int a = 0; a < Q; ++a) w[a][i] = S::pack2_sr(d0[a], d1[a], rp.word());
                 } else {
 #pragma unroll
                     for (int a = 0; a < Q; ++a) w[a][i] = S::pack2(d0[a], d1[a]);

@@ -118,6 +118,10 @@ extern "C" lbm_status lbm_wall_force_noalloc(lbm_ctx* ctx, int wall, unsigned fl
         x.err = "cudaSetDevice failed";
         return LBM_ERR_CUDA;
     }
+    if (!out_mode_ok(out_on_host, (flags & LBM_ACCUMULATE) != 0, out, x.err)) {
+        if (old != x.device) cudaSetDevice(old);
+        return LBM_ERR_ARG;
+    }
     lbm_status status = LBM_OK;
     double* scratch = nullptr;
     cudaStream_t st = (cudaStream_t)stream;
@@ -138,8 +142,12 @@ extern "C" lbm_status lbm_wall_force_noalloc(lbm_ctx* ctx, int wall, unsigned fl
         }
         const bool acc = (flags & LBM_ACCUMULATE) != 0;
         if (ce == cudaSuccess) {
-            if (!out_on_host) {
+            if (out_on_host == LBM_OUT_DEVICE) {
                 ce = launch_reduce_rows(scratch, rows, 3, out, weight, acc ? 1 : 0, st);
+            } else if (out_on_host == LBM_OUT_HOST_ASYNC) {
+                double* slot = scratch + NOALLOC_RESULT;
+                ce = launch_reduce_rows(scratch, rows, 3, slot, weight, 0, st);
+                if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, slot, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
             } else {
                 double* slot = scratch + NOALLOC_RESULT;
                 double tmp[3];

@@ -24,6 +24,7 @@ STORE = {"f64": 0, "f32": 1, "f16s": 2, "bf16s": 3}
 ROUND = {"nearest": 0, "stochastic": 1}
 S1, S2, S3, S4 = 1, 2, 3, 4
 MOVING_CORR, MAXWELL_REMOVE, ACCUMULATE = 1, 2, 4
+OUT_DEVICE, OUT_HOST, OUT_HOST_ASYNC = 0, 1, 2
 BUF_POP_A, BUF_POP_B, BUF_NODE, BUF_LINKS, BUF_SCRATCH, BUF_STAGE, NUM_BUFFERS = range(7)
 MAX_WALLS = 16
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_UNSUPPORTED", 5: "ERR_NAN",
