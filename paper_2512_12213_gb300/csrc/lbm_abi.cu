@@ -200,6 +200,33 @@ template <typename R> void cast_kp(const KP<double>& s, KP<R>& d)
     for (int w = 0; w <= MAXW; ++w)
         for (int k = 0; k < 3; ++k) d.LW[w][k] = (R)s.LW[w][k];
     d.c = (R)s.c; d.dt = (R)s.dt; d.svol = (R)s.svol;
+    for (int k = 0; k < 3; ++k) {
+        d.ueq_c[k] = (R)s.ueq_c[k];
+        d.uf_c[k] = (R)s.uf_c[k];
+    }
+    d.uf_u = (R)s.uf_u;
+    d.Cf = (R)s.Cf;
+    for (int a = 0; a < 19; ++a) d.pe[a] = (R)s.pe[a];
+}
+
+// constants of the node-pair path: the force model of Sec. 2 as u^eq = u +
+// ueq_c, u^F = uf_u u + uf_c and C = Cf for a uniform A, and E_a . A
+template <int Q> void pair_consts(KP<double>& p)
+{
+    const double h = 0.5;
+    for (int k = 0; k < 3; ++k) {
+        p.ueq_c[k] = (p.model == MODEL_E) ? h * p.AG[k] : 0.0;
+        switch (p.model) {
+        case MODEL_A: p.uf_c[k] = 0.0; break;
+        case MODEL_B: p.uf_c[k] = 0.0; break;
+        case MODEL_C: p.uf_c[k] = h * p.tau0 * p.AG[k]; break;
+        default: p.uf_c[k] = h * p.AG[k]; break;
+        }
+    }
+    p.uf_u = (p.model == MODEL_A) ? 0.0 : 1.0;
+    p.Cf = (p.model == MODEL_E) ? 1.0 - h * p.om0 : 1.0;
+    for (int a = 0; a < 19; ++a)
+        p.pe[a] = (a < Q) ? EX<Q>(a) * p.AG[0] + EY<Q>(a) * p.AG[1] + EZ<Q>(a) * p.AG[2] : 0.0;
 }
 
 template <int Q> void maxwell_table(const lbm_config* c, double* mx)
@@ -262,6 +289,8 @@ void fill_params(Ctx& x)
     p.c = cc;
     p.dt = c->dt;
     p.svol = (D == 3 ? c->dx * c->dx * c->dx : c->dx * c->dx) / c->dt;
+    if (c->lattice == 9) pair_consts<9>(p);
+    else pair_consts<19>(p);
     cast_kp(p, x.kpf);
     // storage units: every term that adds to or is compared with a stored
     // deviation scales with it (rho0 enters rho = rho0 + sum d); velocities,

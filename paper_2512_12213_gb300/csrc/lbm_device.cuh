@@ -251,6 +251,10 @@ template <typename R> struct KP {
     R lesc;           // 18 Cs^2
     int face_ladd;    // some closed face of the box is a moving wall
     R LW[MAXW + 1][3];  // 6 rho0 u_w / c per wall id (Ladd term = w_a E_a . LW)
+    // per-launch constants of the node-pair path (uniform body force only):
+    // u^eq = u + ueq_c, u^F = uf_u u + uf_c, C = Cf, E_a . A = pe[a]
+    R ueq_c[3], uf_u, uf_c[3], Cf;
+    R pe[19];
     // units for outputs
     R c, dt, svol;    // c, dt, dx^D / dt
 };
@@ -474,6 +478,112 @@ __device__ __forceinline__ void node_relax(R (&d)[Q], const KP<R>& p, const Node
         const R da = d[a], db = d[b];
         d[a] = om1 * da + (ps + pa);
         d[b] = om1 * db + (ps - pa);
+    }
+}
+
+// ------------------------------------------------ node pairs in FP32x2
+// Two nodes relaxed together with the packed FP32 instructions of the sm_100
+// family: one instruction performs the same operation on both nodes
+// (x = first node, y = second).  The arithmetic is that of node_macro and
+// node_relax without the Lorentz force, Maxwell term and LES, with the force
+// model folded into per-launch constants: u^eq = u + ueq_c,
+// u^F = uf_u u + uf_c, C = Cf, and E_a . A = pe[a] (A is uniform).
+struct F2 {
+    float2 v;
+};
+__device__ __forceinline__ F2 f2s(float x) { return F2{make_float2(x, x)}; }
+__device__ __forceinline__ F2 f2add(F2 a, F2 b) { return F2{__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 f2mul(F2 a, F2 b) { return F2{__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 f2fma(F2 a, F2 b, F2 c) { return F2{__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ F2 f2sub(F2 a, F2 b) { return f2fma(b, f2s(-1.0f), a); }
+
+// E_a . x for a vector of pairs: positive components first, so no negation
+template <int Q>
+__device__ __forceinline__ F2 f2dot(int a, const F2 (&x)[3])
+{
+    const int e[3] = {EX<Q>(a), EY<Q>(a), EZ<Q>(a)};
+    F2 s = f2s(0.0f);
+    bool has = false;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        if (e[c] == 1) {
+            s = has ? f2add(s, x[c]) : x[c];
+            has = true;
+        }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        if (e[c] == -1) {
+            s = has ? f2sub(s, x[c]) : f2mul(x[c], f2s(-1.0f));
+            has = true;
+        }
+    return s;
+}
+
+// Eq. (2) with Eqs. (1) and (3) for two nodes: d <- (1 - om) d + om d^eq + F,
+// per opposite pair d_a' = (1 - om) d_a + w (X + Y), d_opp' = (1 - om) d_opp
+// + w (X - Y) with X = base + 9/2 om rho t^2 + 9 C rho (E_a.u^F)(E_a.A),
+// Y = 3 om rho t + 3 C rho (E_a.A), t = E_a.u^eq
+template <int Q>
+__device__ __forceinline__ void pair_collide(F2 (&d)[Q], const KP<float>& p)
+{
+    constexpr int D = LatDim<Q>::D, NP = LatDim<Q>::NP;
+    // moments, from the even and odd parts of each opposite pair
+    F2 drho = d[0];
+    F2 j[3] = {f2s(0.0f), f2s(0.0f), f2s(0.0f)};
+    bool has[3] = {false, false, false};
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const int a = PAIR<Q>(k), b = OPP<Q>(a);
+        drho = f2add(drho, f2add(d[a], d[b]));
+        const F2 t = f2sub(d[a], d[b]);
+        const int e[3] = {EX<Q>(a), EY<Q>(a), EZ<Q>(a)};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (e[c] == 0) continue;
+            if (!has[c]) j[c] = (e[c] > 0) ? t : f2mul(t, f2s(-1.0f));
+            else j[c] = (e[c] > 0) ? f2add(j[c], t) : f2sub(j[c], t);
+            has[c] = true;
+        }
+    }
+    // macroscopic quantities (text after Eq. 1, Sec. 2)
+    const F2 rho = f2add(f2s(p.rho0), drho);
+    const F2 ir = F2{make_float2(__frcp_rn(rho.v.x), __frcp_rn(rho.v.y))};
+    F2 weq[3], wf[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (c < D) {
+            const F2 u = f2mul(j[c], ir);
+            weq[c] = f2add(u, f2s(p.ueq_c[c]));
+            wf[c] = f2fma(f2s(p.uf_u), u, f2s(p.uf_c[c]));
+        } else {
+            weq[c] = f2s(0.0f);
+            wf[c] = f2s(0.0f);
+        }
+    }
+    const float om = p.om0, om1 = 1.0f - om;
+    F2 q = f2mul(weq[0], weq[0]);
+    F2 fa = f2mul(wf[0], f2s(p.AG[0]));
+#pragma unroll
+    for (int c = 1; c < D; ++c) {
+        q = f2fma(weq[c], weq[c], q);
+        fa = f2fma(wf[c], f2s(p.AG[c]), fa);
+    }
+    const F2 Crho = f2mul(f2s(p.Cf), rho);
+    // base = om (drho - 3/2 rho u^eq.u^eq) - 3 C rho u^F.A
+    F2 base = f2fma(rho, f2mul(q, f2s(-1.5f)), drho);
+    base = f2fma(f2s(om), base, f2mul(Crho, f2mul(fa, f2s(-3.0f))));
+    d[0] = f2fma(f2s(om1), d[0], f2mul(f2s((float)WD<Q>(0)), base));
+    const F2 k1 = f2mul(rho, f2s(4.5f * om)), kl = f2mul(rho, f2s(3.0f * om));
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const int a = PAIR<Q>(k), b = OPP<Q>(a);
+        const float w = (float)WD<Q>(a);
+        const F2 t = f2dot<Q>(a, weq), ef = f2dot<Q>(a, wf);
+        F2 X = f2fma(k1, f2mul(t, t), base);
+        X = f2fma(f2mul(Crho, f2s(9.0f * p.pe[a])), ef, X);
+        const F2 Y = f2fma(kl, t, f2mul(Crho, f2s(3.0f * p.pe[a])));
+        d[a] = f2fma(f2s(w), f2add(X, Y), f2mul(f2s(om1), d[a]));
+        d[b] = f2fma(f2s(w), f2sub(X, Y), f2mul(f2s(om1), d[b]));
     }
 }
 

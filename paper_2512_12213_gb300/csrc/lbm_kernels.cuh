@@ -109,9 +109,10 @@ __device__ __forceinline__ bool row_out(const FaceInfo& fi, int a, int& wall)
 }
 
 // blocks of 128 threads per SM the register allocation must allow: FP64 3
-// (168 registers), FP32 and the larger node code of EXT 4 (128), 16-bit 5 (96)
+// (168 registers), else 4 (128; for 16-bit storage measured faster than 5
+// blocks at 96 registers, which spill with the FP32x2 node pairs)
 template <class S, bool EXT> struct StepOcc {
-    static constexpr int value = sizeof(typename S::T) == 8 ? 3 : ((sizeof(typename S::T) == 2 && !EXT) ? 5 : 4);
+    static constexpr int value = sizeof(typename S::T) == 8 ? 3 : 4;
 };
 
 template <int Q, class S, bool EXT, bool FACES, bool SR>
@@ -268,9 +269,54 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
         }
     };
 
+    // the same for two consecutive nodes k, k+1 held as pairs
+    auto add_ladd2 = [&](F2 (&d)[Q], int k) {
+#pragma unroll
+        for (int a = 1; a < Q; ++a) {
+            int wall = 0;
+            const bool hit = row_out<Q>(fi, a, wall);
+            int w0 = wall, w1 = wall;
+            bool h0 = hit, h1 = hit;
+            if (fi.closed_x) {
+                if (EX<Q>(a) == 1 && x0 + k == 0) { h0 = true; w0 = fi.wx_lo; }
+                if (EX<Q>(a) == -1 && x0 + k == g.nx - 1) { h0 = true; w0 = fi.wx_hi; }
+                if (EX<Q>(a) == -1 && x0 + k + 1 == g.nx - 1) { h1 = true; w1 = fi.wx_hi; }
+            }
+            if (h0) d[a].v.x += ladd_of<Q, R>(p, a, w0);
+            if (h1) d[a].v.y += ladd_of<Q, R>(p, a, w1);
+        }
+    };
+    // two nodes at a time in packed FP32x2 arithmetic (FP32 compute without
+    // the Lorentz force, Maxwell term or LES)
+    constexpr bool PAIR2 = !EXT && sizeof(R) == 4;
+
     const long long base = row * g.nxp + x0;
     if (!special) {
-        if constexpr (PACKED) {
+        if constexpr (PACKED && PAIR2) {
+#pragma unroll
+            for (int i = 0; i < V / 2; ++i) {
+                F2 dd[Q];
+#pragma unroll
+                for (int a = 0; a < Q; ++a) dd[a] = F2{S::unpack2(w[a][i])};
+                if (ladd) add_ladd2(dd, 2 * i);
+                pair_collide<Q>(dd, p);
+                if constexpr (SR) {
+                    NodeRng rp((uint32_t)(base + 2 * i), seed);     // the pair's first node
+#pragma unroll
+                    for (int a = 0; a < Q; ++a) w[a][i] = S::pack2_sr(dd[a].v.x, dd[a].v.y, rp.word());
+                } else {
+#pragma unroll
+                    for (int a = 0; a < Q; ++a) w[a][i] = S::pack2(dd[a].v.x, dd[a].v.y);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                VecN<T, V> o;
+#pragma unroll
+                for (int i = 0; i < V / 2; ++i) o.u[i] = w[a][i];
+                *reinterpret_cast<typename RawVec<sizeof(T) * V>::type*>(dst + (long long)a * g.sq + base) = o.raw;
+            }
+        } else if constexpr (PACKED) {
             // two nodes per packed word: unpack both, relax them, pack both
             // with one conversion
 #pragma unroll
@@ -329,6 +375,20 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
 #pragma unroll
                         for (int j = 0; j < V - 1; ++j) f[a][j] = f[a][j + 1];
                         f[a][V - 1] = S::from_raw(d[a]);
+                    }
+                }
+            } else if constexpr (PAIR2) {
+#pragma unroll
+                for (int i = 0; i < V / 2; ++i) {
+                    F2 dd[Q];
+#pragma unroll
+                    for (int a = 0; a < Q; ++a) dd[a] = F2{make_float2(S::to_raw(f[a][2 * i]), S::to_raw(f[a][2 * i + 1]))};
+                    if (ladd) add_ladd2(dd, 2 * i);
+                    pair_collide<Q>(dd, p);
+#pragma unroll
+                    for (int a = 0; a < Q; ++a) {
+                        f[a][2 * i] = S::from_raw(dd[a].v.x);
+                        f[a][2 * i + 1] = S::from_raw(dd[a].v.y);
                     }
                 }
             } else {

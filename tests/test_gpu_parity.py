@@ -62,6 +62,12 @@ def _case(name, model="e", storage="f64"):
         mask = inputs.empty_mask(n, n, n)
         cfg = dict(lattice=19, nx=n, ny=n, nz=n, periodic=(0, 0, 0), tau=0.55, force_model=model, les=1, cs=0.1,
                    storage=storage, wall_u=((0, 0, 0), (0.1, 0, 0)), face_wall=(1, 1, 1, 1, 1, 2))
+    elif name == "closed_x":   # every face closed, moving x faces, no LES: the vector path's x-face bounce
+        nx, ny, nz = 37, 9, 7
+        mask = inputs.random_solids(nx, ny, nz, 0.03, n_walls=1, seed=17)
+        cfg = dict(lattice=19, nx=nx, ny=ny, nz=nz, periodic=(0, 0, 0), tau=0.62, force_model=model,
+                   g=(1e-4, -5e-5, 2e-5), storage=storage,
+                   wall_u=((0, 0, 0), (0.0, 0.03, 0.01), (0.0, -0.02, 0.02)), face_wall=(2, 3, 1, 1, 1, 1))
     elif name == "column":     # nx = 1: every chunk is mostly padding
         mask = inputs.empty_mask(1, 24)
         cfg = dict(lattice=9, nx=1, ny=24, nz=1, periodic=(1, 0, 1), tau=0.9, force_model=model, g=(1e-4, 0, 0),
@@ -99,7 +105,7 @@ def _rel(a, b):
 
 
 CASES = [("d2q9", m) for m in "abcde"] + [("d3q19", m) for m in "abcde"] + [
-    ("d2q9_mhd", "d"), ("d2q9_mhd", "e"), ("d3q19_ext", "c"), ("d3q19_ext", "e"), ("cavity", "e"),
+    ("d2q9_mhd", "d"), ("d2q9_mhd", "e"), ("d3q19_ext", "c"), ("d3q19_ext", "e"), ("cavity", "e"), ("closed_x", "e"),
     ("column", "b"), ("single", "c"), ("wide", "a"), ("ultrawide", "d")]
 
 
@@ -123,6 +129,23 @@ def test_populations_fp64(orc, name, model):
 @pytest.mark.parametrize("name,model", [("d2q9", "d"), ("d3q19", "e"), ("d3q19_ext", "c"), ("cavity", "e"),
                                         ("ultrawide", "b")])
 def test_populations_reduced_precision(orc, name, model, storage):
+    cfg, mask = _case(name, model, storage)
+    ocfg, f0, _, _ = _initial(orc, cfg, mask)
+    sim = lbm.Sim(cfg, mask)
+    sim.import_f(f0)
+    steps = 10
+    sim.step(steps)
+    f_ref = orc.run(ocfg, mask, f0, steps)
+    err = _rel(sim.export_f().cpu().numpy(), f_ref)
+    assert err < TOL[storage], err
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+@pytest.mark.parametrize("model", "abcde")
+@pytest.mark.parametrize("name", ["d2q9", "d3q19", "closed_x"])
+def test_force_models_fp32_paths(orc, name, model, storage):
+    """Every force model through the FP32 node-pair path (uniform body force,
+    moving closed faces on y/z, and on x for closed_x)."""
     cfg, mask = _case(name, model, storage)
     ocfg, f0, _, _ = _initial(orc, cfg, mask)
     sim = lbm.Sim(cfg, mask)
