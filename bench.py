@@ -72,12 +72,18 @@ def peaks():
         return FALLBACK_HBM, "fallback"
 
 
+# sources that compile into the step kernel (host code, the adjoint and the
+# allocation-free wall force are left out)
+STEP_SOURCES = ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_tile.cuh", "lbm_internal.h",
+                "inst_f64.cu", "inst_f32.cu", "inst_f16.cu", "inst_bf16.cu")
+
+
 def source_hash():
+    """Hash of the step kernel's sources, to match committed ncu figures."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2512_12213_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in STEP_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -267,7 +273,7 @@ def run_ours(args):
         out["storage_variants"] = variants
         out["drag_error_vs_f64"] = drag_errors(torch, lbm, workloads, args.drag_steps)
         out["cavity_les_f32"] = cavity_bench(torch, lbm, workloads, hbm, args)
-        out["adjoint"] = adjoint_bench(torch, lbm, workloads)
+        out["adjoint"] = adjoint_bench(torch, lbm, workloads, hbm)
         e2e = e2e_bench(torch, lbm, workloads, args)
         cpu = cpu_baseline()
     else:
@@ -300,9 +306,12 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def drag_errors(torch, lbm, workloads, steps):
-    """Drag on the sphere after `steps` steps from rest (and its average over
-    the window) in each storage format, relative to FP64."""
+def drag_errors(torch, lbm, workloads, steps, checkpoints=(1000, 5000, 20000), radius=12):
+    """Drag on the sphere from rest in each storage format, relative to FP64:
+    at fixed steps of the transient (`checkpoints`), averaged over the first
+    `steps` steps, and as the drag coefficient C_d = F / (rho U^2 pi r^2 / 2)
+    at the last checkpoint, U the mean fluid velocity there."""
+    T = max(max(checkpoints), steps)
     res = {}
     for key in ("f64", "f32", "f16s", "bf16s", "f16s_sr", "bf16s_sr"):
         storage = key.split("_")[0]
@@ -313,19 +322,32 @@ def drag_errors(torch, lbm, workloads, steps):
         s.rest()
         st = s.stream
         acc = torch.zeros(3, dtype=torch.float64, device=s.device)
-        last = torch.zeros(3, dtype=torch.float64, device=s.device)
-        for i in range(steps):
+        at = torch.zeros((len(checkpoints), 3), dtype=torch.float64, device=s.device)
+        for i in range(T):
             lbm.lbm_step(s.ctx, 1, st)
-            lbm.lbm_wall_force(s.ctx, 1, lbm.ACCUMULATE, 1.0 / steps, acc, 0, st)
-        lbm.lbm_wall_force(s.ctx, 1, 0, 1.0, last, 0, st)
-        res[key] = (float(last[0].item()), float(acc[0].item()))
+            if i < steps:
+                lbm.lbm_wall_force(s.ctx, 1, lbm.ACCUMULATE, 1.0 / steps, acc, 0, st)
+            if i + 1 in checkpoints:
+                lbm.lbm_wall_force(s.ctx, 1, 0, 1.0, at[checkpoints.index(i + 1)], 0, st)
+        mass, mom, _ = s.balance()
+        fluid = int((m == 0).sum())
+        U = mom[0] / mass
+        rho = mass / fluid
+        Fx = at[:, 0].cpu().numpy()
+        res[key] = {"at": Fx, "mean": float(acc[0].item()),
+                    "cd": float(Fx[-1] / (0.5 * rho * U * U * np.pi * radius ** 2)),
+                    "re": float(U * 2 * radius / ((c["tau"] - 0.5) / 3))}
         s.close()
         del s
         torch.cuda.empty_cache()
-    ref_last, ref_avg = res["f64"]
-    out = {"steps": steps, "f64_drag_last": ref_last, "f64_drag_mean": ref_avg}
+    ref = res["f64"]
+    out = {"checkpoints": list(checkpoints), "mean_window": steps,
+           "f64_drag_at": [float(v) for v in ref["at"]], "f64_drag_mean": ref["mean"],
+           "f64_cd_at_last": ref["cd"], "re_at_last": ref["re"]}
     for k in ("f32", "f16s", "bf16s", "f16s_sr", "bf16s_sr"):
-        out[k] = {"rel_err_last": abs(res[k][0] / ref_last - 1), "rel_err_mean": abs(res[k][1] / ref_avg - 1)}
+        out[k] = {"rel_err_at": [float(abs(a / b - 1)) for a, b in zip(res[k]["at"], ref["at"])],
+                  "rel_err_mean": abs(res[k]["mean"] / ref["mean"] - 1),
+                  "cd_rel_err": abs(res[k]["cd"] / ref["cd"] - 1)}
     return out
 
 
@@ -347,9 +369,9 @@ def cavity_bench(torch, lbm, workloads, hbm, args):
             "achieved_gbs": round(ach, 1), "frac": round(ach / hbm, 4), "steps": steps}
 
 
-def adjoint_bench(torch, lbm, workloads, T=400):
-    from paper_2512_12213_gb300 import adjoint
-    c, m = workloads.cylinder(storage="f32")
+def adjoint_case(torch, lbm, adjoint, c, m, T, hbm):
+    """Forward (with checkpoints), backward (with recomputation) and the
+    reverse-step kernel alone, on one configuration."""
     s = lbm.Sim(c, m)
     prob = adjoint.DragProblem(s, T, 1)
     theta = list(c["g"]) + [0.0, 0.0, 0.0]
@@ -363,8 +385,8 @@ def adjoint_bench(torch, lbm, workloads, T=400):
     g = prob.backward()
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    N = c["nx"] * c["ny"]
-    # adjoint kernel alone
+    N = c["nx"] * c["ny"] * c["nz"]
+    Q = c["lattice"]
     st = s.stream
     cs = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -377,10 +399,27 @@ def adjoint_bench(torch, lbm, workloads, T=400):
     torch.cuda.synchronize()
     ka = e0.elapsed_time(e1) / T
     s.close()
-    return {"workload": f"D2Q9 cylinder r=20 in 512x256, T={T} (sqrt(T) checkpoints), FP32 forward/adjoint",
-            "adjoint_kernel_mlups": round(N / (ka * 1e-3) / 1e6, 1),
+    bpn = 3 * Q * 4 + 1           # FP32 state, phi_{t+1} and phi_t per node, plus the class byte
+    gbs = N * bpn / (ka * 1e-3) / 1e9
+    return {"adjoint_kernel_mlups": round(N / (ka * 1e-3) / 1e6, 1),
+            "adjoint_kernel_gbs": round(gbs, 1), "adjoint_kernel_frac": round(gbs / hbm, 4),
+            "bytes_per_node": bpn,
             "backward_mlups_with_recompute": round(N * T / (t2 - t1) / 1e6, 1),
             "forward_mlups": round(N * T / (t1 - t0) / 1e6, 1), "grad": [float(x) for x in g]}
+
+
+def adjoint_bench(torch, lbm, workloads, hbm):
+    from paper_2512_12213_gb300 import adjoint
+    out = {}
+    c, m = workloads.cylinder(storage="f32")
+    T = 400
+    out["cylinder_2d"] = dict(workload=f"D2Q9 cylinder r=20 in 512x256, T={T} (sqrt(T) checkpoints), FP32",
+                              **adjoint_case(torch, lbm, adjoint, c, m, T, hbm))
+    c, m = workloads.sphere_small(storage="f32")
+    T = 100
+    out["sphere_3d"] = dict(workload=f"D3Q19 sphere r=10 in 128^3, T={T} (sqrt(T) checkpoints), FP32",
+                            **adjoint_case(torch, lbm, adjoint, c, m, T, hbm))
+    return out
 
 
 def e2e_bench(torch, lbm, workloads, args):

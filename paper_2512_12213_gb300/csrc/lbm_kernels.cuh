@@ -740,166 +740,11 @@ k_stress(const typename S::T* __restrict__ cur, const typename S::T* __restrict_
     }
 }
 
-// ---------------------------------------------------------------- adjoint
-// One reverse step of the drag adjoint (uniform body force, any model).
-// psi_a(x) = phi_next_a(x + E_a) through a fluid link, or phi_next_opp(a)(x)
-// plus the drag seed through a link into the target wall; then
-// phi_b = (1 - om) psi_b + A_rho + E_b . B_j, where A_rho and B_j collect the
-// derivatives of G = f^eq/tau + F with respect to rho and j, formed from the
-// weighted moments s0 = sum w psi, s1 = sum w psi E, s2 = sum w psi E E.
-// The node streams its data: the forward populations only feed the
-// moments, psi is read once for the moments and again for the output.
-template <int Q, class S>
-__global__ void __launch_bounds__(RED_THREADS)
-k_adjoint(const typename S::T* __restrict__ Pprev, const typename S::R* __restrict__ phin,
-          typename S::R* __restrict__ phio, const uint8_t* __restrict__ cls, const Geo g,
-          const KP<typename S::R> p, int target, double d0, double d1, double d2, double seedw,
-          double* __restrict__ partials)
-{
-    using R = typename S::R;
-    constexpr int D = LatDim<Q>::D;
-    __shared__ double sm[6 * 32];
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    const long long NP = (long long)g.nxp * g.ny * g.nz;
-    const double c = (double)p.c, svol = (double)p.svol, rho0 = (double)p.rho0;
-    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < NP; n += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(n % g.nxp);
-        const long long r = n / g.nxp;
-        const int y = (int)(r % g.ny), z = (int)(r / g.ny);
-        const uint8_t cl = cls[n];
-        if (x >= g.nx || nc_solid(cl) || cl == NC_PAD) {
-#pragma unroll
-            for (int a = 0; a < Q; ++a) phio[(long long)a * g.sq + n] = R(0);
-            continue;
-        }
-        const bool bulk = (cl == NC_BULK);
-        // index of x + E_a (periodic wrap), for bulk nodes
-        auto plus = [&](int a) -> long long {
-            const int xp = wrapi(x + EX<Q>(a), g.nx), yp = wrapi(y + EY<Q>(a), g.ny);
-            const int zp = (Q == 19) ? wrapi(z + EZ<Q>(a), g.nz) : 0;
-            return ((long long)zp * g.ny + yp) * g.nxp + xp;
-        };
-        // forward state f(t): moments only
-        Mom<R> mo;
-        mom_zero(mo);
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            R v;
-            if (bulk) {
-                v = S::to_r(Pprev[(long long)a * g.sq + plus(OPP<Q>(a))]);
-            } else {
-                long long sidx;
-                int wall;
-                if (a == 0) v = S::to_r(Pprev[n]);
-                else if (pull_source(g, cls, x, y, z, EX<Q>(a), EY<Q>(a), EZ<Q>(a), sidx, wall))
-                    v = S::to_r(Pprev[(long long)a * g.sq + sidx]);
-                else
-                    v = S::to_r(Pprev[(long long)OPP<Q>(a) * g.sq + n]) + ladd_of<Q, R>(p, a, wall);
-            }
-            mom_add<R, Q, false>(mo, a, v);
-        }
-        NodeM<R> m;
-        macro_from_moments<R, Q, false>(mo, p, m);
-        // psi_a, with the drag seeds; `grads` adds the u_w terms (first pass only)
-        auto psi_of = [&](int a, bool grads) -> R {
-            if (bulk) return phin ? phin[(long long)a * g.sq + plus(a)] : R(0);
-            long long dn;
-            int wall;
-            if (a == 0) return phin ? phin[n] : R(0);
-            if (pull_source(g, cls, x, y, z, EX<Q>(OPP<Q>(a)), EY<Q>(OPP<Q>(a)), EZ<Q>(OPP<Q>(a)), dn, wall))
-                return phin ? phin[(long long)a * g.sq + dn] : R(0);
-            const double back = phin ? (double)phin[(long long)OPP<Q>(a) * g.sq + n] : 0.0;
-            double ps = back;
-            if (wall == target) {
-                const double de = c * (d0 * EX<Q>(a) + d1 * EY<Q>(a) + d2 * EZ<Q>(a));
-                ps += seedw * 2.0 * svol * de;
-                if (grads) {
-                    // u_w enters f(t+1) and F_t through the Ladd term -6 w rho0 E.u_w / c
-                    const double gl = -6.0 * WD<Q>(a) * rho0 / c * (back + seedw * svol * de);
-                    acc[3] += gl * EX<Q>(a);
-                    acc[4] += gl * EY<Q>(a);
-                    acc[5] += gl * EZ<Q>(a);
-                }
-            }
-            return R(ps);
-        };
-        // omega-weighted moments of psi
-        R s0 = 0, s1[3] = {0, 0, 0}, s2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const R wp = R(WD<Q>(a)) * psi_of(a, true);
-            const int e[3] = {EX<Q>(a), EY<Q>(a), EZ<Q>(a)};
-            s0 += wp;
-#pragma unroll
-            for (int i = 0; i < D; ++i) {
-                if (e[i]) s1[i] += R(e[i]) * wp;
-#pragma unroll
-                for (int j = 0; j < D; ++j)
-                    if (e[i] * e[j]) s2[i][j] += R(e[i] * e[j]) * wp;
-            }
-        }
-        // sum psi f^eq(rho, W) = rho Psi_e(W); grad_W = rho (3 s1 + 9 s2 W - 3 s0 W)
-        // sum psi F = C rho Psi_f; grad_Wf = C rho (9 s2 A - 3 s0 A); grad_A = C rho (3 s1 - 3 s0 Wf + 9 s2 Wf)
-        const R* W = m.weq;
-        const R* Wf = m.wf;
-        const R* A = m.A;
-        R s2W[3] = {0, 0, 0}, s2A[3] = {0, 0, 0}, s2F[3] = {0, 0, 0};
-#pragma unroll
-        for (int i = 0; i < D; ++i)
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                s2W[i] += s2[i][j] * W[j];
-                s2A[i] += s2[i][j] * A[j];
-                s2F[i] += s2[i][j] * Wf[j];
-            }
-        R WW = 0, s1W = 0, WsW = 0, s1A = 0, FA = 0, FsA = 0;
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            WW += W[i] * W[i];
-            s1W += s1[i] * W[i];
-            WsW += W[i] * s2W[i];
-            s1A += s1[i] * A[i];
-            FA += Wf[i] * A[i];
-            FsA += Wf[i] * s2A[i];
-        }
-        const bool ma = (p.model == MODEL_A);
-        const R Psi_e = s0 + R(3) * s1W + R(4.5) * WsW - R(1.5) * WW * s0;
-        const R Psi_f = ma ? R(3) * s1A : (R(3) * s1A - R(3) * FA * s0 + R(9) * FsA);
-        R Ge[3], Gf[3], GA[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            Ge[i] = (i < D) ? m.om * m.rho * (R(3) * s1[i] + R(9) * s2W[i] - R(3) * s0 * W[i]) : R(0);
-            Gf[i] = (i < D && !ma) ? m.C * m.rho * (R(9) * s2A[i] - R(3) * s0 * A[i]) : R(0);
-            GA[i] = (i < D) ? (ma ? m.C * m.rho * R(3) * s1[i]
-                                  : m.C * m.rho * (R(3) * s1[i] - R(3) * s0 * Wf[i] + R(9) * s2F[i]))
-                            : R(0);
-        }
-        // W and Wf move with u = j/rho: d/dj = I/rho, d/drho = -u/rho
-        const R ir = R(1) / m.rho;
-        R Arho = m.om * Psi_e + m.C * Psi_f;
-        R Bj[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            Arho -= (Ge[i] + Gf[i]) * m.u[i] * ir;
-            Bj[i] = (Ge[i] + Gf[i]) * ir;
-        }
-#pragma unroll
-        for (int b = 0; b < Q; ++b) {
-            const R phib = (R(1) - m.om) * psi_of(b, false) + Arho + R(EX<Q>(b)) * Bj[0] + R(EY<Q>(b)) * Bj[1] +
-                           R(EZ<Q>(b)) * Bj[2];
-            phio[(long long)b * g.sq + n] = phib;
-        }
-        // dJ/dg: A = dt g / c; W^eq moves with A/2 for [e]; W^F with tau/2 ([c]) or 1/2 ([d], [e])
-        const R keq = (p.model == MODEL_E) ? R(0.5) : R(0);
-        const R kf = (p.model == MODEL_C) ? R(0.5) * m.tau : ((p.model == MODEL_D || p.model == MODEL_E) ? R(0.5) : R(0));
-        const double sc = (double)p.dt / c;
-#pragma unroll
-        for (int i = 0; i < D; ++i) acc[i] += sc * (double)(GA[i] + keq * Ge[i] + kf * Gf[i]);
-    }
-    block_sum<6>(acc, sm);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 6; ++k) partials[(long long)blockIdx.x * 6 + k] += acc[k];
-}
+}  // namespace lbm
+
+#include "lbm_adjoint.cuh"  // uses block_sum, ladd_of and RED_THREADS above
+
+namespace lbm {
 
 // ================================================================ launchers
 inline int grid_for(long long n, int threads, long long cap)
