@@ -13,10 +13,11 @@ namespace lbm {
 // phi_b = (1 - om) psi_b + A_rho + E_b . B_j, where A_rho and B_j collect the
 // derivatives of G = f^eq/tau + F with respect to rho and j, formed from the
 // weighted moments s0 = sum w psi, s1 = sum w psi E, s2 = sum w psi E E.
-// The node streams its data: the forward populations only feed the
-// moments, psi is read once for the moments and again for the output.
+// One node per thread; the forward populations only feed the moments, psi
+// stays in registers.  Bulk nodes off the box edge address their neighbours
+// by constant offsets; two 256-thread blocks per SM in FP32.
 template <int Q, class S>
-__global__ void __launch_bounds__(RED_THREADS)
+__global__ void __launch_bounds__(RED_THREADS, sizeof(typename S::R) == 8 ? 1 : 2)
 k_adjoint(const typename S::T* __restrict__ Pprev, const typename S::R* __restrict__ phin,
           typename S::R* __restrict__ phio, const uint8_t* __restrict__ cls, const Geo g,
           const KP<typename S::R> p, int target, double d0, double d1, double d2, double seedw,
@@ -27,6 +28,7 @@ k_adjoint(const typename S::T* __restrict__ Pprev, const typename S::R* __restri
     __shared__ double sm[6 * 32];
     double acc[6] = {0, 0, 0, 0, 0, 0};
     const long long NP = (long long)g.nxp * g.ny * g.nz;
+    const long long plane = (long long)g.nxp * g.ny;
     const double c = (double)p.c, svol = (double)p.svol, rho0 = (double)p.rho0;
     // node indices fit in 32 bits (the padded node count is below 2^31)
     const unsigned nxp = (unsigned)g.nxp, ny = (unsigned)g.ny;
@@ -41,8 +43,11 @@ k_adjoint(const typename S::T* __restrict__ Pprev, const typename S::R* __restri
             continue;
         }
         const bool bulk = (cl == NC_BULK);
-        // index of x + E_a (periodic wrap), for bulk nodes
+        const bool inner = bulk && x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 &&
+                           (Q == 9 || (z > 0 && z < g.nz - 1));
+        // index of x + E_a for bulk nodes (periodic wrap on the box edge)
         auto plus = [&](int a) -> long long {
+            if (inner) return n + EX<Q>(a) + EY<Q>(a) * (long long)g.nxp + EZ<Q>(a) * plane;
             const int xp = wrapi(x + EX<Q>(a), g.nx), yp = wrapi(y + EY<Q>(a), g.ny);
             const int zp = (Q == 19) ? wrapi(z + EZ<Q>(a), g.nz) : 0;
             return (long long)(((unsigned)zp * ny + (unsigned)yp) * nxp + (unsigned)xp);
@@ -68,8 +73,8 @@ k_adjoint(const typename S::T* __restrict__ Pprev, const typename S::R* __restri
         }
         NodeM<R> m;
         macro_from_moments<R, Q, false>(mo, p, m);
-        // psi_a, with the drag seeds; `grads` adds the u_w terms (first pass only)
-        auto psi_of = [&](int a, bool grads) -> R {
+        // psi_a, with the drag seeds and the u_w gradient terms
+        auto psi_of = [&](int a) -> R {
             if (bulk) return phin ? phin[(long long)a * g.sq + plus(a)] : R(0);
             long long dn;
             int wall;
@@ -81,21 +86,21 @@ k_adjoint(const typename S::T* __restrict__ Pprev, const typename S::R* __restri
             if (wall == target) {
                 const double de = c * (d0 * EX<Q>(a) + d1 * EY<Q>(a) + d2 * EZ<Q>(a));
                 ps += seedw * 2.0 * svol * de;
-                if (grads) {
-                    // u_w enters f(t+1) and F_t through the Ladd term -6 w rho0 E.u_w / c
-                    const double gl = -6.0 * WD<Q>(a) * rho0 / c * (back + seedw * svol * de);
-                    acc[3] += gl * EX<Q>(a);
-                    acc[4] += gl * EY<Q>(a);
-                    acc[5] += gl * EZ<Q>(a);
-                }
+                // u_w enters f(t+1) and F_t through the Ladd term -6 w rho0 E.u_w / c
+                const double gl = -6.0 * WD<Q>(a) * rho0 / c * (back + seedw * svol * de);
+                acc[3] += gl * EX<Q>(a);
+                acc[4] += gl * EY<Q>(a);
+                acc[5] += gl * EZ<Q>(a);
             }
             return R(ps);
         };
         // omega-weighted moments of psi
+        R psi[Q];
         R s0 = 0, s1[3] = {0, 0, 0}, s2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            const R wp = R(WD<Q>(a)) * psi_of(a, true);
+            psi[a] = psi_of(a);
+            const R wp = R(WD<Q>(a)) * psi[a];
             const int e[3] = {EX<Q>(a), EY<Q>(a), EZ<Q>(a)};
             s0 += wp;
 #pragma unroll
@@ -153,7 +158,7 @@ k_adjoint(const typename S::T* __restrict__ Pprev, const typename S::R* __restri
         }
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
-            const R phib = (R(1) - m.om) * psi_of(b, false) + Arho + R(EX<Q>(b)) * Bj[0] + R(EY<Q>(b)) * Bj[1] +
+            const R phib = (R(1) - m.om) * psi[b] + Arho + R(EX<Q>(b)) * Bj[0] + R(EY<Q>(b)) * Bj[1] +
                            R(EZ<Q>(b)) * Bj[2];
             phio[(long long)b * g.sq + n] = phib;
         }
