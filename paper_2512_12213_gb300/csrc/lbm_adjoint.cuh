@@ -1,10 +1,20 @@
 // lbm_adjoint.cuh -- the reverse step of the discrete adjoint of the
 // collide-stream step and the momentum-exchange drag (arXiv 2512.12213,
 // Eqs. 1-3 and 25), for gradients of time-averaged drag with respect to the
-// body force and a wall velocity.  Included by lbm_kernels.cuh.
+// body force and a wall velocity, and its launcher.  Included by
+// lbm_kernels.cuh after the other launchers.
 #pragma once
 
 namespace lbm {
+
+// per-launch constants of a reverse step, per direction a of a link into the
+// target wall: the drag seed 2 w_J svol c (d . E_a) that the link adds to
+// psi_a, and -6 w_a rho0 / c, the derivative of the Ladd term with respect
+// to E_a . u_w
+template <typename R> struct AdjConst {
+    R seed[19];
+    R gl[19];
+};
 
 // ---------------------------------------------------------------- adjoint
 // One reverse step of the drag adjoint (uniform body force, any model).
@@ -13,23 +23,23 @@ namespace lbm {
 // phi_b = (1 - om) psi_b + A_rho + E_b . B_j, where A_rho and B_j collect the
 // derivatives of G = f^eq/tau + F with respect to rho and j, formed from the
 // weighted moments s0 = sum w psi, s1 = sum w psi E, s2 = sum w psi E E.
-// One node per thread; the forward populations only feed the moments, psi
-// stays in registers.  Bulk nodes off the box edge address their neighbours
-// by constant offsets; two 256-thread blocks per SM in FP32.
+// One node per thread, psi in registers.  Bulk nodes (every link to a fluid
+// node, periodic wrap allowed) address their neighbours through nine
+// precomputed row offsets and three x positions, without branches; nodes
+// next to a wall or a closed face take the general path.  Gradient terms are
+// summed per thread in the compute precision and per block in FP64.
 template <int Q, class S>
 __global__ void __launch_bounds__(RED_THREADS, sizeof(typename S::R) == 8 ? 1 : 2)
 k_adjoint(const typename S::T* __restrict__ Pprev, const typename S::R* __restrict__ phin,
           typename S::R* __restrict__ phio, const uint8_t* __restrict__ cls, const Geo g,
-          const KP<typename S::R> p, int target, double d0, double d1, double d2, double seedw,
+          const KP<typename S::R> p, int target, const AdjConst<typename S::R> ac, double gscale,
           double* __restrict__ partials)
 {
     using R = typename S::R;
     constexpr int D = LatDim<Q>::D;
     __shared__ double sm[6 * 32];
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    R accg[3] = {0, 0, 0}, accw[3] = {0, 0, 0};
     const long long NP = (long long)g.nxp * g.ny * g.nz;
-    const long long plane = (long long)g.nxp * g.ny;
-    const double c = (double)p.c, svol = (double)p.svol, rho0 = (double)p.rho0;
     // node indices fit in 32 bits (the padded node count is below 2^31)
     const unsigned nxp = (unsigned)g.nxp, ny = (unsigned)g.ny;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < NP; n += (long long)gridDim.x * blockDim.x) {
@@ -42,25 +52,32 @@ k_adjoint(const typename S::T* __restrict__ Pprev, const typename S::R* __restri
             for (int a = 0; a < Q; ++a) phio[(long long)a * g.sq + n] = R(0);
             continue;
         }
-        const bool bulk = (cl == NC_BULK);
-        const bool inner = bulk && x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 &&
-                           (Q == 9 || (z > 0 && z < g.nz - 1));
-        // index of x + E_a for bulk nodes (periodic wrap on the box edge)
-        auto plus = [&](int a) -> long long {
-            if (inner) return n + EX<Q>(a) + EY<Q>(a) * (long long)g.nxp + EZ<Q>(a) * plane;
-            const int xp = wrapi(x + EX<Q>(a), g.nx), yp = wrapi(y + EY<Q>(a), g.ny);
-            const int zp = (Q == 19) ? wrapi(z + EZ<Q>(a), g.nz) : 0;
-            return (long long)(((unsigned)zp * ny + (unsigned)yp) * nxp + (unsigned)xp);
-        };
-        // forward state f(t): moments only
         Mom<R> mo;
         mom_zero(mo);
+        R psi[Q];
+        if (cl == NC_BULK) {
+            // rows (y + dy, z + dz) and x +- 1, wrapped (bulk nodes wrap only on periodic axes)
+            unsigned rows[3][3];
 #pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            R v;
-            if (bulk) {
-                v = S::to_r(Pprev[(long long)a * g.sq + plus(OPP<Q>(a))]);
-            } else {
+            for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                for (int dz = -1; dz <= 1; ++dz) {
+                    const int yy = wrapi(y + dy, g.ny);
+                    const int zz = (Q == 19) ? wrapi(z + dz, g.nz) : 0;
+                    rows[dy + 1][dz + 1] = ((unsigned)zz * ny + (unsigned)yy) * nxp;
+                }
+            const unsigned xs[3] = {(unsigned)(x == 0 ? g.nx - 1 : x - 1), (unsigned)x,
+                                    (unsigned)(x == g.nx - 1 ? 0 : x + 1)};
+            auto at = [&](int ex, int ey, int ez) -> unsigned { return rows[ey + 1][ez + 1] + xs[ex + 1]; };
+#pragma unroll
+            for (int a = 0; a < Q; ++a)
+                mom_add<R, Q, false>(mo, a, S::to_r(Pprev[(long long)a * g.sq + at(-EX<Q>(a), -EY<Q>(a), -EZ<Q>(a))]));
+#pragma unroll
+            for (int a = 0; a < Q; ++a) psi[a] = phin ? phin[(long long)a * g.sq + at(EX<Q>(a), EY<Q>(a), EZ<Q>(a))] : R(0);
+        } else {
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                R v;
                 long long sidx;
                 int wall;
                 if (a == 0) v = S::to_r(Pprev[n]);
@@ -68,38 +85,37 @@ k_adjoint(const typename S::T* __restrict__ Pprev, const typename S::R* __restri
                     v = S::to_r(Pprev[(long long)a * g.sq + sidx]);
                 else
                     v = S::to_r(Pprev[(long long)OPP<Q>(a) * g.sq + n]) + ladd_of<Q, R>(p, a, wall);
+                mom_add<R, Q, false>(mo, a, v);
             }
-            mom_add<R, Q, false>(mo, a, v);
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                long long dn;
+                int wall;
+                if (a == 0) {
+                    psi[0] = phin ? phin[n] : R(0);
+                } else if (pull_source(g, cls, x, y, z, EX<Q>(OPP<Q>(a)), EY<Q>(OPP<Q>(a)), EZ<Q>(OPP<Q>(a)), dn,
+                                       wall)) {
+                    psi[a] = phin ? phin[(long long)a * g.sq + dn] : R(0);
+                } else {
+                    const R back = phin ? phin[(long long)OPP<Q>(a) * g.sq + n] : R(0);
+                    psi[a] = back;
+                    if (wall == target) {
+                        psi[a] += ac.seed[a];
+                        // u_w enters f(t+1) and F_t through the Ladd term
+                        const R gl = ac.gl[a] * (back + R(0.5) * ac.seed[a]);
+                        accw[0] += gl * R(EX<Q>(a));
+                        accw[1] += gl * R(EY<Q>(a));
+                        accw[2] += gl * R(EZ<Q>(a));
+                    }
+                }
+            }
         }
         NodeM<R> m;
         macro_from_moments<R, Q, false>(mo, p, m);
-        // psi_a, with the drag seeds and the u_w gradient terms
-        auto psi_of = [&](int a) -> R {
-            if (bulk) return phin ? phin[(long long)a * g.sq + plus(a)] : R(0);
-            long long dn;
-            int wall;
-            if (a == 0) return phin ? phin[n] : R(0);
-            if (pull_source(g, cls, x, y, z, EX<Q>(OPP<Q>(a)), EY<Q>(OPP<Q>(a)), EZ<Q>(OPP<Q>(a)), dn, wall))
-                return phin ? phin[(long long)a * g.sq + dn] : R(0);
-            const double back = phin ? (double)phin[(long long)OPP<Q>(a) * g.sq + n] : 0.0;
-            double ps = back;
-            if (wall == target) {
-                const double de = c * (d0 * EX<Q>(a) + d1 * EY<Q>(a) + d2 * EZ<Q>(a));
-                ps += seedw * 2.0 * svol * de;
-                // u_w enters f(t+1) and F_t through the Ladd term -6 w rho0 E.u_w / c
-                const double gl = -6.0 * WD<Q>(a) * rho0 / c * (back + seedw * svol * de);
-                acc[3] += gl * EX<Q>(a);
-                acc[4] += gl * EY<Q>(a);
-                acc[5] += gl * EZ<Q>(a);
-            }
-            return R(ps);
-        };
         // omega-weighted moments of psi
-        R psi[Q];
         R s0 = 0, s1[3] = {0, 0, 0}, s2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            psi[a] = psi_of(a);
             const R wp = R(WD<Q>(a)) * psi[a];
             const int e[3] = {EX<Q>(a), EY<Q>(a), EZ<Q>(a)};
             s0 += wp;
@@ -165,13 +181,45 @@ k_adjoint(const typename S::T* __restrict__ Pprev, const typename S::R* __restri
         // dJ/dg: A = dt g / c; W^eq moves with A/2 for [e]; W^F with tau/2 ([c]) or 1/2 ([d], [e])
         const R keq = (p.model == MODEL_E) ? R(0.5) : R(0);
         const R kf = (p.model == MODEL_C) ? R(0.5) * m.tau : ((p.model == MODEL_D || p.model == MODEL_E) ? R(0.5) : R(0));
-        const double sc = (double)p.dt / c;
 #pragma unroll
-        for (int i = 0; i < D; ++i) acc[i] += sc * (double)(GA[i] + keq * Ge[i] + kf * Gf[i]);
+        for (int i = 0; i < D; ++i) accg[i] += GA[i] + keq * Ge[i] + kf * Gf[i];
+    }
+    double acc[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        acc[k] = gscale * (double)accg[k];
+        acc[3 + k] = (double)accw[k];
     }
     block_sum<6>(acc, sm);
     if (threadIdx.x == 0)
         for (int k = 0; k < 6; ++k) partials[(long long)blockIdx.x * 6 + k] += acc[k];
+}
+
+// ---------------------------------------------------------------- launcher
+template <int Q, class S>
+cudaError_t launch_adjoint(const Ctx& c, const void* Pprev, const void* phin, void* phio, int wall,
+                           const double* dir, double seedw, double* partials, cudaStream_t st)
+{
+    using T = typename S::T;
+    using R = typename S::R;
+    // a fixed grid per context, so every block owns the same partial row each step
+    const long long NP = (long long)c.geo.nxp * c.geo.ny * c.geo.nz;
+    const int blocks = grid_for(NP, RED_THREADS, ADJ_BLOCKS);
+    const KP<R>& p = kp_of<S>(c);
+    const KP<double>& pd = c.kpd;
+    AdjConst<R> ac;
+    for (int a = 0; a < 19; ++a) {
+        ac.seed[a] = R(0);
+        ac.gl[a] = R(0);
+    }
+    for (int a = 0; a < Q; ++a) {
+        const double de = pd.c * (dir[0] * EX<Q>(a) + dir[1] * EY<Q>(a) + dir[2] * EZ<Q>(a));
+        ac.seed[a] = R(seedw * 2.0 * pd.svol * de);
+        ac.gl[a] = R(-6.0 * WD<Q>(a) * pd.rho0 / pd.c);
+    }
+    k_adjoint<Q, S><<<blocks, RED_THREADS, 0, st>>>((const T*)Pprev, (const R*)phin, (R*)phio, c.cls, c.geo, p, wall,
+                                                    ac, pd.dt / pd.c, partials);
+    return cudaGetLastError();
 }
 
 }  // namespace lbm

@@ -740,12 +740,6 @@ k_stress(const typename S::T* __restrict__ cur, const typename S::T* __restrict_
     }
 }
 
-}  // namespace lbm
-
-#include "lbm_adjoint.cuh"  // uses block_sum, ladd_of and RED_THREADS above
-
-namespace lbm {
-
 // ================================================================ launchers
 inline int grid_for(long long n, int threads, long long cap)
 {
@@ -902,19 +896,11 @@ cudaError_t launch_stress(const Ctx& c, const void* cur, const void* prev, int v
     return cudaGetLastError();
 }
 
-template <int Q, class S>
-cudaError_t launch_adjoint(const Ctx& c, const void* Pprev, const void* phin, void* phio, int wall,
-                           const double* dir, double seedw, double* partials, cudaStream_t st)
-{
-    using T = typename S::T;
-    using R = typename S::R;
-    // a fixed grid per context, so every block owns the same partial row each step
-    const long long NP = (long long)c.geo.nxp * c.geo.ny * c.geo.nz;
-    const int blocks = grid_for(NP, RED_THREADS, ADJ_BLOCKS);
-    k_adjoint<Q, S><<<blocks, RED_THREADS, 0, st>>>((const T*)Pprev, (const R*)phin, (R*)phio, c.cls, c.geo,
-                                                    kp_of<S>(c), wall, dir[0], dir[1], dir[2], seedw, partials);
-    return cudaGetLastError();
-}
+}  // namespace lbm
+
+#include "lbm_adjoint.cuh"  // the adjoint kernel and launch_adjoint; uses block_sum, grid_for, kp_of
+
+namespace lbm {
 
 template <class S> Dispatch make_dispatch()
 {
