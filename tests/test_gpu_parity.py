@@ -68,6 +68,21 @@ def _case(name, model="e", storage="f64"):
         cfg = dict(lattice=19, nx=nx, ny=ny, nz=nz, periodic=(0, 0, 0), tau=0.62, force_model=model,
                    g=(1e-4, -5e-5, 2e-5), storage=storage,
                    wall_u=((0, 0, 0), (0.0, 0.03, 0.01), (0.0, -0.02, 0.02)), face_wall=(2, 3, 1, 1, 1, 1))
+    elif name == "periodic_ragged":   # fully periodic D3Q19, ragged x, last warp of chunks half full
+        nx, ny, nz = 50, 13, 11
+        mask = inputs.sphere_mask(nx, ny, nz, (21.3, 6.2, 5.4), 3.3, wall=1)
+        cfg = dict(lattice=19, nx=nx, ny=ny, nz=nz, periodic=(1, 1, 1), tau=0.66, force_model=model,
+                   g=(2e-4, -1e-4, 5e-5), storage=storage, wall_u=((0, 0, 0),))
+    elif name == "periodic_multi":    # a box of 3072 blocks of chunks
+        nx, ny, nz = 128, 64, 48
+        mask = inputs.sphere_mask(nx, ny, nz, (40.5, 30.2, 20.7), 8.4, wall=1)
+        cfg = dict(lattice=19, nx=nx, ny=ny, nz=nz, periodic=(1, 1, 1), tau=0.7, force_model=model,
+                   g=(1e-4, 0, 0), storage=storage, wall_u=((0, 0, 0),))
+    elif name == "periodic_2d":       # fully periodic D2Q9 with a cylinder, ragged x
+        nx, ny = 203, 37
+        mask = inputs.cylinder_mask(nx, ny, (60.4, 18.3), 7.1, wall=1)
+        cfg = dict(lattice=9, nx=nx, ny=ny, nz=1, periodic=(1, 1, 1), tau=0.74, force_model=model,
+                   g=(3e-4, 1e-4, 0), storage=storage, wall_u=((0, 0, 0),))
     elif name == "column":     # nx = 1: every chunk is mostly padding
         mask = inputs.empty_mask(1, 24)
         cfg = dict(lattice=9, nx=1, ny=24, nz=1, periodic=(1, 0, 1), tau=0.9, force_model=model, g=(1e-4, 0, 0),
@@ -249,6 +264,26 @@ def test_all_solid_domain():
     assert np.all(sim.wall_force(-1) == 0)
     m, M, b = sim.balance()
     assert m == 0 and np.all(M == 0) and np.all(b == 0)
+
+
+@pytest.mark.parametrize("rounding", ["nearest", "stochastic"])
+@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+@pytest.mark.parametrize("name,model", [("periodic_ragged", "e"), ("periodic_ragged", "c"), ("periodic_multi", "e"),
+                                        ("periodic_2d", "d"), ("periodic_2d", "a")])
+def test_periodic_16bit_against_oracle(orc, name, model, storage, rounding):
+    """16-bit storage in fully periodic boxes (the benchmark's kind of box):
+    rows whose length is not a multiple of the vector width, a last warp of
+    chunks half full, and a box of many thousand blocks."""
+    cfg, mask = _case(name, model, storage)
+    cfg = dict(cfg, rounding=rounding, seed=77)
+    ocfg, f0, _, _ = _initial(orc, cfg, mask)
+    sim = lbm.Sim(cfg, mask)
+    sim.import_f(f0)
+    steps = 6
+    sim.step(steps)
+    f_ref = orc.run(ocfg, mask, f0, steps)
+    err = _rel(sim.export_f().cpu().numpy(), f_ref)
+    assert err < TOL[storage], err
 
 
 @pytest.mark.parametrize("storage", ["f16s", "bf16s"])
