@@ -216,12 +216,15 @@ void orc_init(const orc_cfg* c, const unsigned char* wid, const double* rho,
     }
 }
 
-/* one step with caller work arrays frel (N*Q) and fnew (N*Q) */
+/* one step with caller work arrays frel (N*Q) and fnew (N*Q); vmean (if not
+ * NULL) receives the mean flow velocity v over the fluid nodes */
 static void step_work(const orc_cfg* c, const lat_t* L, const unsigned char* wid,
-                      double* f, double* frel, double* fnew)
+                      double* f, double* frel, double* fnew, double* vmean)
 {
     const long N = nnodes(c);
     const int Q = L->q;
+    double vs[3] = {0.0, 0.0, 0.0};
+    long nf = 0;
     /* relaxation with the force term at every fluid node, Eq. (2) */
     for (long n = 0; n < N; ++n) {
         if (wid[n] != 0) {
@@ -232,7 +235,15 @@ static void step_work(const orc_cfg* c, const lat_t* L, const unsigned char* wid
         for (int a = 0; a < Q; ++a) fl[a] = f[a * N + n];
         collide_r(c, L, fl, c->g, out);
         for (int a = 0; a < Q; ++a) frel[a * N + n] = out[a];
+        if (vmean) {
+            macro_t_r m;
+            macro_r(c, L, fl, c->g, &m);
+            for (int k = 0; k < 3; ++k) vs[k] += m.v[k];
+            ++nf;
+        }
     }
+    if (vmean)
+        for (int k = 0; k < 3; ++k) vmean[k] = nf ? vs[k] / (double)nf : 0.0;
     /* propagation to x + dt e_a, halfway bounce-back at solids */
     memset(fnew, 0, sizeof(double) * N * Q);
     for (int z = 0; z < c->nz; ++z)
@@ -250,29 +261,61 @@ static void step_work(const orc_cfg* c, const lat_t* L, const unsigned char* wid
     memcpy(f, fnew, sizeof(double) * N * Q);
 }
 
-void orc_step(const orc_cfg* c, const unsigned char* wid, double* f, double* frel_out)
+/* insulating walls (Eq. 36): the field that makes the net current
+ * sigma_e sum (E + v x B) over fluid nodes vanish, E = -<v> x B */
+static void insulating_field(const orc_cfg* c, const double* vmean, double* E)
+{
+    E[0] = -(vmean[1] * c->B[2] - vmean[2] * c->B[1]);
+    E[1] = -(vmean[2] * c->B[0] - vmean[0] * c->B[2]);
+    E[2] = -(vmean[0] * c->B[1] - vmean[1] * c->B[0]);
+}
+
+void orc_run_e(const orc_cfg* c, const unsigned char* wid, double* f, int nsteps, double* E)
 {
     lat_t L;
     get_lat(c->q, &L);
     const long N = nnodes(c);
     double* frel = (double*)malloc(sizeof(double) * N * L.q);
     double* fnew = (double*)malloc(sizeof(double) * N * L.q);
-    step_work(c, &L, wid, f, frel, fnew);
+    orc_cfg cc = *c;
+    for (int k = 0; k < 3; ++k) cc.E[k] = E[k];
+    for (int s = 0; s < nsteps; ++s) {
+        double vm[3];
+        step_work(&cc, &L, wid, f, frel, fnew, vm);
+        if (c->insulating && c->lorentz) insulating_field(c, vm, cc.E);
+    }
+    for (int k = 0; k < 3; ++k) E[k] = cc.E[k];
+    free(frel);
+    free(fnew);
+}
+
+void orc_step_e(const orc_cfg* c, const unsigned char* wid, double* f, double* frel_out, double* E)
+{
+    lat_t L;
+    get_lat(c->q, &L);
+    const long N = nnodes(c);
+    double* frel = (double*)malloc(sizeof(double) * N * L.q);
+    double* fnew = (double*)malloc(sizeof(double) * N * L.q);
+    orc_cfg cc = *c;
+    for (int k = 0; k < 3; ++k) cc.E[k] = E[k];
+    double vm[3];
+    step_work(&cc, &L, wid, f, frel, fnew, vm);
+    if (c->insulating && c->lorentz) insulating_field(c, vm, E);
     if (frel_out) memcpy(frel_out, frel, sizeof(double) * N * L.q);
     free(frel);
     free(fnew);
 }
 
+void orc_step(const orc_cfg* c, const unsigned char* wid, double* f, double* frel_out)
+{
+    double E[3] = {c->E[0], c->E[1], c->E[2]};
+    orc_step_e(c, wid, f, frel_out, E);
+}
+
 void orc_run(const orc_cfg* c, const unsigned char* wid, double* f, int nsteps)
 {
-    lat_t L;
-    get_lat(c->q, &L);
-    const long N = nnodes(c);
-    double* frel = (double*)malloc(sizeof(double) * N * L.q);
-    double* fnew = (double*)malloc(sizeof(double) * N * L.q);
-    for (int s = 0; s < nsteps; ++s) step_work(c, &L, wid, f, frel, fnew);
-    free(frel);
-    free(fnew);
+    double E[3] = {c->E[0], c->E[1], c->E[2]};
+    orc_run_e(c, wid, f, nsteps, E);
 }
 
 void orc_wall_force(const orc_cfg* c, const unsigned char* wid, const double* frel,
@@ -447,7 +490,7 @@ static double drag_forward(const orc_cfg* c, const lat_t* L, const unsigned char
     double J = 0.0;
     for (int t = 0; t < T; ++t) {
         if (hist) memcpy(hist + (size_t)t * N * Q, f, sizeof(double) * N * Q);
-        step_work(c, L, wid, f, frel, fnew);
+        step_work(c, L, wid, f, frel, fnew, NULL);
         double F[3];
         orc_wall_force(c, wid, frel, f, wall, 0, F);
         J += (d[0] * F[0] + d[1] * F[1] + d[2] * F[2]) / T;

@@ -61,6 +61,10 @@ typedef struct orc_cfg {
     int n_walls;           /* wall ids 1..n_walls */
     double wall_u[ORC_MAX_WALLS][3];   /* velocity of wall k at index k-1 */
     int face_wall[6];
+    int insulating;        /* 1 (with lorentz): insulating walls, no net current.  The
+                              field E of step t is -<v> x B with <v> the mean flow
+                              velocity over fluid nodes of step t-1 (the first step
+                              uses E as given); see orc_step_e / orc_run_e */
 } orc_cfg;
 
 /* lattice tables: e (unit-speed integers, Q*3), w (Q), opposite index (Q) */
@@ -89,8 +93,15 @@ void orc_init(const orc_cfg* c, const unsigned char* wall_id, const double* rho,
  * f^rel(t) if not NULL */
 void orc_step(const orc_cfg* c, const unsigned char* wall_id, double* f, double* frel);
 
-/* run n steps in place */
+/* run n steps in place (with cfg->insulating, E starts at cfg->E and is
+ * updated from step to step) */
 void orc_run(const orc_cfg* c, const unsigned char* wall_id, double* f, int n);
+
+/* the same with the field as explicit state: E[3] is the field of the first
+ * step on entry and, with cfg->insulating, the field of the next step on exit
+ * (-<v> x B of the last step, Eq. 36); frel as in orc_step (last step) */
+void orc_step_e(const orc_cfg* c, const unsigned char* wall_id, double* f, double* frel, double* E);
+void orc_run_e(const orc_cfg* c, const unsigned char* wall_id, double* f, int n, double* E);
 
 /* momentum-exchange force of Eq. (25) on wall `wall` (or every wall if
  * wall < 0) during the step t -> t+dt, from frel = f^rel(t) and

@@ -55,6 +55,7 @@ class OrcCfg(ctypes.Structure):
         ("n_walls", ctypes.c_int),
         ("wall_u", (ctypes.c_double * 3) * MAX_WALLS),
         ("face_wall", ctypes.c_int * 6),
+        ("insulating", ctypes.c_int),
     ]
 
 
@@ -79,6 +80,8 @@ def lib():
             "orc_init": (None, [cp, ub, dp, dp, dp, dp]),
             "orc_step": (None, [cp, ub, dp, dp]),
             "orc_run": (None, [cp, ub, dp, ctypes.c_int]),
+            "orc_step_e": (None, [cp, ub, dp, dp, dp]),
+            "orc_run_e": (None, [cp, ub, dp, ctypes.c_int, dp]),
             "orc_wall_force": (None, [cp, ub, dp, dp, ctypes.c_int, ctypes.c_int, dp]),
             "orc_count_links": (ctypes.c_long, [cp, ub, ctypes.c_int]),
             "orc_stress": (None, [cp, ub, dp, dp, dp, ctypes.c_int, dp, dp, dp, dp]),
@@ -96,7 +99,7 @@ def lib():
 def make_cfg(q=9, nx=4, ny=4, nz=1, periodic=(1, 1, 1), dx=1.0, dt=1.0, tau=0.8, rho0=1.0,
              force_model="e", g=(0.0, 0.0, 0.0), lorentz=0, B=(0.0, 0.0, 0.0), E=(0.0, 0.0, 0.0),
              sigma_e=0.0, mu=1.0, maxwell=0, les=0, cs=0.1, wall_u=(), face_wall=(1, 1, 1, 1, 1, 1),
-             **_ignored) -> OrcCfg:
+             insulating=0, **_ignored) -> OrcCfg:
     """Build an oracle configuration.  ``wall_u`` lists the velocity of walls
     1..n; ``force_model`` is one of 'a'..'e' (Sec. 2)."""
     c = OrcCfg()
@@ -116,6 +119,7 @@ def make_cfg(q=9, nx=4, ny=4, nz=1, periodic=(1, 1, 1), dx=1.0, dt=1.0, tau=0.8,
             c.wall_u[i][k] = float(u[k])
     for k in range(6):
         c.face_wall[k] = int(face_wall[k])
+    c.insulating = int(insulating)
     return c
 
 
@@ -195,6 +199,25 @@ def run(cfg, wall_id, f, n):
     fn = _f64(f).copy()
     lib().orc_run(ctypes.byref(cfg), _ub(_u8(wall_id)), _dp(fn), int(n))
     return fn
+
+
+def run_e(cfg, wall_id, f, n, E=None):
+    """n steps with the field E as state (insulating walls update it each
+    step, Eq. 36); returns (f, E of the next step)."""
+    fn = _f64(f).copy()
+    e = np.array(list(cfg.E) if E is None else E, dtype=np.float64)
+    lib().orc_run_e(ctypes.byref(cfg), _ub(_u8(wall_id)), _dp(fn), int(n), _dp(e))
+    return fn, e
+
+
+def step_e(cfg, wall_id, f, E=None):
+    """One step with the field E as state; returns (f(t+dt), f^rel(t), E of
+    the next step)."""
+    fn = _f64(f).copy()
+    frel = np.zeros_like(fn)
+    e = np.array(list(cfg.E) if E is None else E, dtype=np.float64)
+    lib().orc_step_e(ctypes.byref(cfg), _ub(_u8(wall_id)), _dp(fn), _dp(frel), _dp(e))
+    return fn, frel, e
 
 
 def wall_force(cfg, wall_id, frel, fnext, wall=-1, flags=0):

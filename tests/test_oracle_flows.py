@@ -16,7 +16,11 @@ identities (no GPU).
   momentum exchange contains -L n per flat wall node (Sec. 5, Eq. 28), its
   removal restores the field-free force, and it cancels on a closed body
   (Eq. 36);
-* half-step consistency at steady state (Eqs. 29-30).
+* half-step consistency at steady state (Eqs. 29-30);
+* insulating walls (Eq. 36): with E = -<v> x B the Hartmann profile
+  converges at second order to nu u'' + g - K (u - <u>) = 0, u(+-H) = 0, and at
+  steady state the total Lorentz force vanishes, so the walls carry exactly
+  the body force of g (Eq. 34 with a zero Lorentz term).
 """
 import numpy as np
 import pytest
@@ -281,3 +285,61 @@ def test_maxwell_equilibrium_shift_and_removal(orc, q):
             assert np.allclose(PB - P0, -n_nodes * area * (L @ n), rtol=0, atol=tol)
             assert np.allclose(PR, P0, rtol=0, atol=tol)
         f0, fB = f0n, fBn
+
+
+def _insulating(orc, H, tau=0.8, Ha=4.0, nx=2):
+    ny = 2 * H
+    nu = (tau - 0.5) / 3
+    K = nu * Ha ** 2 / H ** 2
+    B0 = 0.05
+    m = Ha / H
+    g = 1e-5 * (16.0 / H) ** 2
+    kw = dict(q=9, nx=nx, ny=ny, nz=1, periodic=(1, 0, 1), tau=tau, force_model="e", g=(g, 0, 0),
+              lorentz=1, B=(0, B0, 0), sigma_e=K / B0 ** 2, insulating=1, wall_u=((0, 0, 0),))
+    cfg = orc.make_cfg(**kw)
+    mask = np.zeros((1, ny, nx), np.uint8)
+    f0 = orc.init(cfg, mask, np.ones((1, ny, nx)), np.zeros((3, 1, ny, nx)))
+    f, E = orc.run_e(cfg, mask, f0, int(60 * H * H))
+    y = np.arange(ny) - H + 0.5
+    # nu u'' + g - K (u - <u>) = 0 with u(+-H) = 0:
+    # u = (g/K) mH coth(mH) (1 - cosh(m y)/cosh(m H)), m = Ha/H
+    u_exact = (g / K) * m * H / np.tanh(m * H) * (1 - np.cosh(m * y) / np.cosh(m * H))
+    return dict(cfg=orc.make_cfg(**dict(kw, E=tuple(E))), kw=kw, mask=mask, f=f, E=E, u_exact=u_exact, g=g, B0=B0)
+
+
+def test_insulating_hartmann_convergence_and_zero_lorentz_force(orc):
+    """Insulating walls, E = -<v> x B updated every step from the previous
+    step's mean flow velocity: second-order convergence to the closed form,
+    E_z = -B0 <v_x> at steady state, zero total Lorentz force, and the walls
+    carry exactly sum rho g."""
+    errs = []
+    for H in (8, 16, 32):
+        r = _insulating(orc, H)
+        cfg, mask, f = r["cfg"], r["mask"], r["f"]
+        vx = np.array([orc.node_macro(cfg, f[:, 0, j, 0])["v"][0] for j in range(2 * H)])
+        errs.append(np.abs(vx - r["u_exact"]).max() / r["u_exact"].max())
+        # the field is the zero-current field of the (steady) flow
+        assert abs(r["E"][2] / (-r["B0"] * vx.mean()) - 1) < 1e-10
+        assert abs(r["E"][0]) < 1e-20 and abs(r["E"][1]) < 1e-20
+        # total Lorentz force: sum rho a = sum rho g (Eq. 36)
+        mass, _, rhoa = orc.balance(cfg, mask, f)
+        assert abs(rhoa[0] / (r["g"] * mass) - 1) < 1e-9
+        # the walls carry the body force of g alone (steady Eq. 34)
+        fn, fr, _ = orc.step_e(cfg, mask, f, r["E"])
+        Fb = orc.wall_force(cfg, mask, fr, fn, 1)
+        assert abs(Fb[0] / (r["g"] * mass) - 1) < 1e-8
+    assert errs[-1] < 1.5e-3
+    assert 2.5 < errs[0] / errs[1] < 4.5 and 2.5 < errs[1] / errs[2] < 4.5
+
+
+def test_insulating_field_differs_from_conducting(orc):
+    """Without the zero-current field (E = 0, conducting walls) the same
+    channel runs slower: the Lorentz force then brakes the mean flow too."""
+    r = _insulating(orc, 16)
+    kw = dict(r["kw"], insulating=0)
+    cfg = orc.make_cfg(**kw)
+    f0 = orc.init(cfg, r["mask"], np.ones((1, 32, 2)), np.zeros((3, 1, 32, 2)))
+    fc = orc.run(cfg, r["mask"], f0, 60 * 16 * 16)
+    vi = orc.node_macro(r["cfg"], r["f"][:, 0, 16, 0])["v"][0]
+    vc = orc.node_macro(cfg, fc[:, 0, 16, 0])["v"][0]
+    assert vc < 0.5 * vi
