@@ -147,7 +147,20 @@ typedef struct lbm_config {
     int32_t face_wall[6];            /* wall id of each closed face: -x +x -y +y -z +z */
     int32_t rounding;                /* LBM_ROUND_NEAREST, or LBM_ROUND_STOCHASTIC (16-bit storage only) */
     uint32_t seed;                   /* stream of the stochastic rounding */
+    int32_t insulating;              /* 1 (needs lorentz): insulating walls, see below */
 } lbm_config;
+
+/* Insulating walls (Sec. 6, Eq. 36).  No current leaves the fluid, so the
+ * electric field is the one that makes the net current sigma_e sum(E + v x B)
+ * over fluid nodes vanish: E = -<v> x B, <v> the mean flow velocity of the
+ * fluid nodes.  The library keeps E on the device and sets it after every
+ * step from that step's mean flow velocity, so step t uses E = -<v(t-1)> x B
+ * (a one-step lag; exact zero total Lorentz force at steady state).  The
+ * first step after lbm_create, lbm_init_equilibrium, lbm_import_f or
+ * lbm_load_state uses the configured E.  E is state that a population
+ * checkpoint does not hold, so lbm_step_from returns LBM_ERR_UNSUPPORTED, and
+ * the reductions of the step run on the stepping stream.  Costs a scratch
+ * row of 3 doubles per step thread (see lbm_buffer_sizes). */
 
 /* rounding of the populations stored by a step.  Stochastic rounding rounds
  * a value up with probability equal to its distance from the value below, so
@@ -222,6 +235,11 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, int64_t t, void* stream
 
 /* Current time T. */
 lbm_status lbm_time(const lbm_ctx* ctx, int64_t* t);
+
+/* The imposed electric field that the next step uses (3 doubles, host
+ * memory; synchronises the stream): the configured E, or with insulating
+ * walls the field set by the last step. */
+lbm_status lbm_electric_field(lbm_ctx* ctx, double* E, void* stream);
 
 /* Error flags raised by kernels since the last clear (synchronises the
  * stream): bit 0 = a bounded wait for staged input expired (the step was not

@@ -76,6 +76,8 @@ bool validate(const lbm_config* c, const uint8_t* wid, std::string& err)
         return fail("rounding must be LBM_ROUND_NEAREST or LBM_ROUND_STOCHASTIC");
     if (c->rounding == LBM_ROUND_STOCHASTIC && c->storage != LBM_STORE_F16S && c->storage != LBM_STORE_BF16S)
         return fail("stochastic rounding applies to 16-bit storage only");
+    if (c->insulating != 0 && c->insulating != 1) return fail("insulating must be 0 or 1");
+    if (c->insulating && !c->lorentz) return fail("insulating walls need the Lorentz force (lorentz = 1)");
     if (!wid) return fail("wall_id is NULL");
     const long long N = nodes_of(c);
     for (long long n = 0; n < N; ++n)
@@ -175,6 +177,13 @@ void count_links(const lbm_config* c, const uint8_t* wid, long long* per_wall /*
     for (const Link& L : links) per_wall[L.wall]++;
 }
 
+// threads of the register-tiled step kernel: one per vector chunk
+long long step_threads_of(const lbm_config* c)
+{
+    const int V = (c->storage == LBM_STORE_F64) ? 2 : 4;
+    return (long long)(pitch_of(c->nx) / V) * c->ny * c->nz;
+}
+
 void sizes_of(const lbm_config* c, long long n_links, size_t s[LBM_NUM_BUFFERS])
 {
     const long long sq = (long long)pitch_of(c->nx) * c->ny * c->nz;
@@ -183,6 +192,8 @@ void sizes_of(const lbm_config* c, long long n_links, size_t s[LBM_NUM_BUFFERS])
     s[LBM_BUF_NODE] = round256((size_t)sq);
     s[LBM_BUF_LINKS] = n_links ? round256((size_t)n_links * sizeof(Link)) : 0;
     s[LBM_BUF_SCRATCH] = round256(SCRATCH_DOUBLES * sizeof(double));
+    if (c->insulating)
+        s[LBM_BUF_SCRATCH] = round256((SCRATCH_INS_ROWS + 3 * (size_t)step_threads_of(c)) * sizeof(double));
     s[LBM_BUF_STAGE] = round256((size_t)(c->lattice + 4) * N * sizeof(double));
 }
 
@@ -241,6 +252,18 @@ template <int Q> void maxwell_table(const lbm_config* c, double* mx)
         if (Q == 19) m -= B2 / 6.0;
         mx[a] = 9.0 * WD<Q>(a) / (2.0 * cc * cc * c->mu) * m;
     }
+}
+
+// insulating walls: the kernels read the force coefficient of the current
+// field from the scratch block and the step writes its velocity rows there
+void bind_insulating(Ctx& x)
+{
+    if (!x.insulating || !x.scratch) return;
+    double* blk = x.scratch + SCRATCH_INS_OFF;
+    x.kpd.aeb_dev = blk + INS_AEB_D;
+    x.kpf.aeb_dev = reinterpret_cast<const float*>(blk + INS_AEB_F);
+    x.kps.aeb_dev = reinterpret_cast<const float*>(blk + INS_AEB_S);
+    x.kpd.ins_rows = x.kpf.ins_rows = x.kps.ins_rows = x.scratch + SCRATCH_INS_ROWS;
 }
 
 void fill_params(Ctx& x)
@@ -305,6 +328,7 @@ void fill_params(Ctx& x)
     for (int w = 0; w <= MAXW; ++w)
         for (int k = 0; k < 3; ++k) q.LW[w][k] *= s;
     cast_kp(q, x.kps);
+    bind_insulating(x);
 }
 
 // shape of the shared-memory staged step: R rows per tile so that each of
@@ -327,7 +351,7 @@ void choose_tile(Ctx& x)
     // LBM_STEP_KERNEL=tile selects the shared-memory staged step where it fits;
     // the register-tiled step is the default
     const char* sel = getenv("LBM_STEP_KERNEL");
-    const bool want_tile = sel && strcmp(sel, "tile") == 0 && x.cfg.rounding == LBM_ROUND_NEAREST;
+    const bool want_tile = sel && strcmp(sel, "tile") == 0 && x.cfg.rounding == LBM_ROUND_NEAREST && !x.insulating;
     const bool fits = want_tile && smem_for(R, ns) <= (size_t)x.smem_optin;
     x.tile_R = fits ? R : 0;
     x.tile_stages = fits ? ns : 0;
@@ -442,6 +466,10 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
     if (x.cfg.lattice == LBM_D2Q9) x.cfg.periodic[2] = 1;
     x.ext = (cfg->lorentz || cfg->maxwell || cfg->les) ? 1 : 0;
     x.sr = (cfg->rounding == LBM_ROUND_STOCHASTIC) ? 1 : 0;
+    x.insulating = cfg->insulating != 0;
+    x.ins_threads = step_threads_of(cfg);
+    x.n_fluid = 0;
+    for (long long n = 0; n < (long long)cfg->nx * cfg->ny * cfg->nz; ++n) x.n_fluid += host_wall_id[n] == 0;
     x.geo.nx = cfg->nx;
     x.geo.ny = cfg->ny;
     x.geo.nz = cfg->nz;
@@ -502,6 +530,7 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
     x.cls = (uint8_t*)buffers[LBM_BUF_NODE];
     x.links = (Link*)buffers[LBM_BUF_LINKS];
     x.scratch = (double*)buffers[LBM_BUF_SCRATCH];
+    bind_insulating(x);
     x.stage = buffers[LBM_BUF_STAGE];
     x.stage_bytes = x.stage ? sizes[LBM_BUF_STAGE] : 0;
     x.t = 0;
@@ -524,6 +553,7 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
     if (e == cudaSuccess && x.n_links)
         e = cudaMemcpyAsync(x.links, links.data(), links.size() * sizeof(Link), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = launch_zero(x.scratch, (long long)SCRATCH_DOUBLES, st);
+    if (e == cudaSuccess && x.insulating) e = ins_reset(x, st);
     // solid and padding entries of both population buffers start defined
     if (e == cudaSuccess) e = cudaMemsetAsync(x.pop[0], 0, need[LBM_BUF_POP_A], st);
     if (e == cudaSuccess) e = cudaMemsetAsync(x.pop[1], 0, need[LBM_BUF_POP_B], st);
@@ -597,6 +627,7 @@ lbm_status lbm_init_equilibrium(lbm_ctx* ctx, const double* rho, const double* u
         dxi = xi ? s + 4 * N : nullptr;
     }
     CK(x.ops->init_fields(x, dr, du, dxi, x.pop[x.cur], st), "init kernel");
+    if (x.insulating) CK(ins_reset(x, st), "insulating-wall field");
     if (on_host) CK(cudaStreamSynchronize(st), "synchronize");
     x.t = 0;
     x.prev_valid = false;
@@ -618,6 +649,7 @@ lbm_status lbm_import_f(lbm_ctx* ctx, const void* src, int dtype, int on_host, v
         dsrc = x.stage;
     }
     CK(x.ops->import_f(x, dsrc, dtype, x.pop[x.cur], st), "import kernel");
+    if (x.insulating) CK(ins_reset(x, st), "insulating-wall field");
     if (on_host) CK(cudaStreamSynchronize(st), "synchronize");
     x.t = 0;
     x.prev_valid = false;
@@ -654,6 +686,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps, void* stream)
     cudaStream_t st = (cudaStream_t)stream;
     for (int s = 0; s < nsteps; ++s) {
         CK(x.ops->step(x, x.pop[x.cur], x.pop[1 - x.cur], step_seed(x, x.t), st), "step kernel");
+        if (x.insulating) CK(ins_update(x, st), "insulating-wall field");
         x.cur = 1 - x.cur;
         x.t += 1;
         x.prev_valid = true;
@@ -668,6 +701,10 @@ lbm_status lbm_step_from(lbm_ctx* ctx, const void* src, void* dst, int64_t t, vo
     if (!src || !dst || src == dst) return arg_fail(x, "src and dst must be distinct non-NULL buffers");
     if (((uintptr_t)src) % 256 || ((uintptr_t)dst) % 256) return arg_fail(x, "buffers must be 256-byte aligned");
     if (t < 0) return arg_fail(x, "t must be >= 0");
+    if (x.insulating) {
+        x.err = "lbm_step_from: with insulating walls the field is state a population checkpoint does not hold";
+        return LBM_ERR_UNSUPPORTED;
+    }
     GUARD(x);
     CK(x.ops->step(x, src, dst, step_seed(x, t), (cudaStream_t)stream), "step kernel");
     return LBM_OK;
@@ -690,6 +727,7 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, int64_t t, void* stream
     if (!src || t < 0) return arg_fail(x, "src is NULL or t < 0");
     GUARD(x);
     CK(cudaMemcpyAsync(x.pop[x.cur], src, pop_bytes(x), cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "load");
+    if (x.insulating) CK(ins_reset(x, (cudaStream_t)stream), "insulating-wall field");
     x.t = t;
     x.prev_valid = false;
     return LBM_OK;
@@ -711,6 +749,23 @@ lbm_status lbm_time(const lbm_ctx* ctx, int64_t* t)
 {
     if (!ctx || !t) return LBM_ERR_ARG;
     *t = ctx->c.t;
+    return LBM_OK;
+}
+
+lbm_status lbm_electric_field(lbm_ctx* ctx, double* E, void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (!E) return arg_fail(x, "E is NULL");
+    if (!x.insulating) {
+        for (int k = 0; k < 3; ++k) E[k] = x.cfg.E[k];
+        return LBM_OK;
+    }
+    GUARD(x);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(E, x.scratch + SCRATCH_INS_OFF + INS_E, 3 * sizeof(double), cudaMemcpyDeviceToHost, st),
+       "copy field");
+    CK(cudaStreamSynchronize(st), "synchronize");
     return LBM_OK;
 }
 
@@ -837,6 +892,68 @@ cudaError_t launch_reduce_rows(const double* partials, int nb, int W, double* ou
     return cudaGetLastError();
 }
 
+// insulating walls, stage one: block b sums the rows [b*chunk, (b+1)*chunk)
+// of the step threads' velocity sums in a fixed order
+__global__ void k_ins_rows(const double* __restrict__ rows, long long n, long long chunk, double* __restrict__ out)
+{
+    __shared__ double sm[3 * 32];
+    double v[3] = {0.0, 0.0, 0.0};
+    const long long b0 = (long long)blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+    for (long long r = b0 + threadIdx.x; r < b1; r += blockDim.x)
+        for (int k = 0; k < 3; ++k) v[k] += rows[r * 3 + k];
+    for (int k = 0; k < 3; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) sm[k * 32 + wid] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+        for (int k = 0; k < 3; ++k) {
+            double s = (lane < nw) ? sm[k * 32 + lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) out[blockIdx.x * 3 + k] = s;
+        }
+    }
+}
+
+// the field of insulating walls (Eq. 36): E = -<v> x B with <v> = c sum(W) / n_fluid,
+// and its force coefficient dt sigma_e (E x B) / c in each precision
+__global__ void k_ins_field(double* blk, double n_fluid, double c, double dt, double sigma, double B0, double B1,
+                            double B2, double scale)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double* vs = blk + INS_VSUM;
+    const double v[3] = {c * vs[0] / n_fluid, c * vs[1] / n_fluid, c * vs[2] / n_fluid};
+    const double B[3] = {B0, B1, B2};
+    double E[3];
+    E[0] = -(v[1] * B[2] - v[2] * B[1]);
+    E[1] = -(v[2] * B[0] - v[0] * B[2]);
+    E[2] = -(v[0] * B[1] - v[1] * B[0]);
+    const double ExB[3] = {E[1] * B[2] - E[2] * B[1], E[2] * B[0] - E[0] * B[2], E[0] * B[1] - E[1] * B[0]};
+    float* af = reinterpret_cast<float*>(blk + INS_AEB_F);
+    float* as = reinterpret_cast<float*>(blk + INS_AEB_S);
+    for (int k = 0; k < 3; ++k) {
+        const double aeb = dt * sigma * ExB[k] / c;
+        blk[INS_E + k] = E[k];
+        blk[INS_AEB_D + k] = aeb;
+        af[k] = (float)aeb;
+        as[k] = (float)(aeb * scale);
+    }
+}
+
+// the configured field (after create, init, import or load)
+__global__ void k_ins_reset(double* blk, double E0, double E1, double E2, double a0, double a1, double a2,
+                            float f0, float f1, float f2, float s0, float s1, float s2)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    blk[INS_E] = E0; blk[INS_E + 1] = E1; blk[INS_E + 2] = E2;
+    blk[INS_AEB_D] = a0; blk[INS_AEB_D + 1] = a1; blk[INS_AEB_D + 2] = a2;
+    float* af = reinterpret_cast<float*>(blk + INS_AEB_F);
+    float* as = reinterpret_cast<float*>(blk + INS_AEB_S);
+    af[0] = f0; af[1] = f1; af[2] = f2;
+    as[0] = s0; as[1] = s1; as[2] = s2;
+}
+
 __global__ void k_zero(double* p, long long n)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -846,6 +963,34 @@ __global__ void k_zero(double* p, long long n)
 cudaError_t launch_zero(double* p, long long n, cudaStream_t st)
 {
     k_zero<<<64, 256, 0, st>>>(p, n);
+    return cudaGetLastError();
+}
+
+// after a step: sum the step threads' velocity rows in a fixed order (at
+// most INS_RED_ROWS blocks, then one row pass) and set the field
+cudaError_t ins_update(const Ctx& x, cudaStream_t st)
+{
+    double* blk = x.scratch + SCRATCH_INS_OFF;
+    const long long n = x.ins_threads;
+    const long long chunk = (n + INS_RED_ROWS - 1) / INS_RED_ROWS;
+    const int nb = (int)((n + chunk - 1) / chunk);
+    k_ins_rows<<<nb, 256, 0, st>>>(x.scratch + SCRATCH_INS_ROWS, n, chunk, x.scratch + SCRATCH_INS_RED);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_reduce_rows(x.scratch + SCRATCH_INS_RED, nb, 3, blk + INS_VSUM, 1.0, 0, st);
+    if (e != cudaSuccess) return e;
+    const double scale = (x.cfg.storage == LBM_STORE_F16S) ? 4096.0 : 1.0;
+    k_ins_field<<<1, 32, 0, st>>>(blk, (double)(x.n_fluid > 0 ? x.n_fluid : 1), x.kpd.c, x.kpd.dt, x.cfg.sigma_e,
+                                  x.cfg.B[0], x.cfg.B[1], x.cfg.B[2], scale);
+    return cudaGetLastError();
+}
+
+// the configured field and its force coefficients (fill_params computed them)
+cudaError_t ins_reset(const Ctx& x, cudaStream_t st)
+{
+    k_ins_reset<<<1, 32, 0, st>>>(x.scratch + SCRATCH_INS_OFF, x.cfg.E[0], x.cfg.E[1], x.cfg.E[2], x.kpd.AEB[0],
+                                  x.kpd.AEB[1], x.kpd.AEB[2], x.kpf.AEB[0], x.kpf.AEB[1], x.kpf.AEB[2], x.kps.AEB[0],
+                                  x.kps.AEB[1], x.kps.AEB[2]);
     return cudaGetLastError();
 }
 

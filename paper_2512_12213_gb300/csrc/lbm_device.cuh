@@ -255,6 +255,11 @@ template <typename R> struct KP {
     // u^eq = u + ueq_c, u^F = uf_u u + uf_c, C = Cf, E_a . A = pe[a]
     R ueq_c[3], uf_u, uf_c[3], Cf;
     R pe[19];
+    // insulating walls: the force coefficient dt sigma_e (E x B) / c of the
+    // current field, kept on the device (replaces AEB), and the per-thread
+    // rows of the step kernel's flow-velocity sums; null otherwise
+    const R* aeb_dev;
+    double* ins_rows;
     // units for outputs
     R c, dt, svol;    // c, dt, dx^D / dt
 };
@@ -320,7 +325,8 @@ __device__ __forceinline__ void macro_from_moments(const Mom<R>& mo, const KP<R>
         R wv[3], Ag[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            Ag[k] = (k < D) ? p.AG[k] + p.AEB[k] * ir : R(0);
+            const R aeb = p.aeb_dev ? p.aeb_dev[k] : p.AEB[k];
+            Ag[k] = (k < D) ? p.AG[k] + aeb * ir : R(0);
             wv[k] = m.u[k] + R(0.5) * Ag[k];
         }
         const R kk = R(0.5) * p.kappa * ir;

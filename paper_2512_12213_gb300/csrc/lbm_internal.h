@@ -56,6 +56,14 @@ constexpr size_t SCRATCH_ADJ_OFF = (size_t)MAX_PARTIAL_ROWS * PARTIAL_WIDTH;
 constexpr size_t SCRATCH_OUT_OFF = SCRATCH_ADJ_OFF + (size_t)ADJ_BLOCKS * 6;
 constexpr size_t SCRATCH_FLAG_OFF = SCRATCH_OUT_OFF + 8;   // device error flags (unsigned)
 constexpr size_t SCRATCH_DOUBLES = SCRATCH_FLAG_OFF + 8;
+// insulating walls only, after the above: the field block (E, the sum of v,
+// the force coefficient in FP64, FP32 and FP32 storage units), the stage-one
+// rows of the velocity sum, then one row of 3 doubles per step thread
+constexpr size_t SCRATCH_INS_OFF = SCRATCH_DOUBLES;
+constexpr int INS_E = 0, INS_VSUM = 3, INS_AEB_D = 6, INS_AEB_F = 9, INS_AEB_S = 11;   // doubles into the block
+constexpr int INS_RED_ROWS = 1024;
+constexpr size_t SCRATCH_INS_RED = SCRATCH_INS_OFF + 16;
+constexpr size_t SCRATCH_INS_ROWS = SCRATCH_INS_RED + (size_t)INS_RED_ROWS * 3;
 
 struct Ctx;
 
@@ -82,6 +90,10 @@ const Dispatch& dispatch_bf16();
 cudaError_t launch_reduce_rows(const double* partials, int nb, int W, double* out, double weight, int accumulate,
                                cudaStream_t st);
 cudaError_t launch_zero(double* p, long long n, cudaStream_t st);
+// insulating walls: set the field from the last step's mean flow velocity /
+// reset it to the configured field
+cudaError_t ins_update(const Ctx& x, cudaStream_t st);
+cudaError_t ins_reset(const Ctx& x, cudaStream_t st);
 
 struct Ctx {
     lbm_config cfg;
@@ -116,6 +128,10 @@ struct Ctx {
     size_t tile_smem;
     mutable int tile_blocks;
     unsigned* errflag;
+    // insulating walls: step threads (rows of the velocity sum) and fluid nodes
+    bool insulating;
+    long long ins_threads;
+    long long n_fluid;
 };
 
 }  // namespace lbm

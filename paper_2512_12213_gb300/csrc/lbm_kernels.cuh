@@ -352,6 +352,24 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
     // two nodes at a time in packed FP32x2 arithmetic (FP32 compute without
     // the Lorentz force, Maxwell term or LES)
     constexpr bool PAIR2 = !EXT && sizeof(R) == 4;
+    // insulating walls: this thread's sum of the flow velocity v over the
+    // fluid nodes it relaxes, one row per thread for a fixed-order reduction
+    R vs[3] = {R(0), R(0), R(0)};
+    auto add_v = [&](const NodeM<R>& m) {
+        if constexpr (EXT) {
+            vs[0] += m.v[0];
+            vs[1] += m.v[1];
+            vs[2] += m.v[2];
+        }
+    };
+    auto put_v = [&]() {
+        if constexpr (EXT) {
+            if (p.ins_rows) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) p.ins_rows[tid * 3 + k] = (double)vs[k];
+            }
+        }
+    };
 
     const long long base = row * g.nxp + x0;
     if (!special) {
@@ -399,11 +417,13 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                     NodeM<R> m;
                     node_macro<R, Q, EXT>(d0, p, m);
                     node_relax<R, Q, EXT>(d0, p, m);
+                    add_v(m);
                 }
                 {
                     NodeM<R> m;
                     node_macro<R, Q, EXT>(d1, p, m);
                     node_relax<R, Q, EXT>(d1, p, m);
+                    add_v(m);
                 }
                 if constexpr (SR) {
                     NodeRng rp((uint32_t)(base + 2 * i), seed);     // the pair's first node
@@ -433,6 +453,7 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                     NodeM<R> m;
                     node_macro<R, Q, EXT>(d, p, m);
                     node_relax<R, Q, EXT>(d, p, m);
+                    add_v(m);
 #pragma unroll
                     for (int a = 0; a < Q; ++a) {
 #pragma unroll
@@ -476,6 +497,7 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                 *reinterpret_cast<typename RawVec<sizeof(T) * V>::type*>(dst + (long long)a * g.sq + base) = o.raw;
             }
         }
+        put_v();
         return;
     }
     // chunk with a solid neighbour or padding: node by node
@@ -492,6 +514,7 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
         NodeM<R> m;
         node_macro<R, Q, EXT>(d, p, m);
         node_relax<R, Q, EXT>(d, p, m);
+        add_v(m);
         if constexpr (SR) {
             NodeRng rng((uint32_t)(base + k), seed);
 #pragma unroll
@@ -501,6 +524,7 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
             for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + base + k] = S::from_raw(d[a]);
         }
     }
+    put_v();
 }
 
 // ------------------------------------------ inverse propagation (import/init)

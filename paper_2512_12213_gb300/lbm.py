@@ -55,6 +55,7 @@ class LbmConfig(ctypes.Structure):
         ("face_wall", ctypes.c_int32 * 6),
         ("rounding", ctypes.c_int32),
         ("seed", ctypes.c_uint32),
+        ("insulating", ctypes.c_int32),
     ]
 
 
@@ -80,6 +81,7 @@ _SIGS = {
     "lbm_save_state": [_vp, _vp, _vp],
     "lbm_load_state": [_vp, _vp, ctypes.c_int64, _vp],
     "lbm_time": [_vp, _P(ctypes.c_int64)],
+    "lbm_electric_field": [_vp, _P(ctypes.c_double), _vp],
     "lbm_device_status": [_vp, _P(ctypes.c_uint32), _i, _vp],
     "lbm_stress": [_vp, _i, _vp, _vp, _vp, _vp, _vp],
     "lbm_wall_force": [_vp, _i, ctypes.c_uint, _d, _vp, _i, _vp],
@@ -118,7 +120,8 @@ def _check(status, ctx=None):
 def make_config(lattice=9, nx=4, ny=4, nz=1, periodic=(1, 1, 1), dx=1.0, dt=1.0, tau=0.8, rho0=1.0,
                 force_model="e", g=(0.0, 0.0, 0.0), lorentz=0, B=(0.0, 0.0, 0.0), E=(0.0, 0.0, 0.0),
                 sigma_e=0.0, mu=1.0, maxwell=0, les=0, cs=0.1, storage="f64", wall_u=(),
-                face_wall=(1, 1, 1, 1, 1, 1), rounding="nearest", seed=0, **_ignored) -> LbmConfig:
+                face_wall=(1, 1, 1, 1, 1, 1), rounding="nearest", seed=0, insulating=0,
+                **_ignored) -> LbmConfig:
     c = LbmConfig()
     c.lattice, c.nx, c.ny, c.nz = int(lattice), int(nx), int(ny), int(nz)
     for k in range(3):
@@ -137,6 +140,7 @@ def make_config(lattice=9, nx=4, ny=4, nz=1, periodic=(1, 1, 1), dx=1.0, dt=1.0,
         c.face_wall[k] = int(face_wall[k])
     c.rounding = ROUND[rounding] if isinstance(rounding, str) else int(rounding)
     c.seed = int(seed) & 0xFFFFFFFF
+    c.insulating = int(insulating)
     return c
 
 
@@ -223,6 +227,13 @@ def lbm_time(ctx):
     t = ctypes.c_int64()
     _check(load().lbm_time(ctx, ctypes.byref(t)), ctx)
     return t.value
+
+
+def lbm_electric_field(ctx, stream):
+    """The field the next step uses (insulating walls: set by the last step)."""
+    E = (ctypes.c_double * 3)()
+    _check(load().lbm_electric_field(ctx, E, stream), ctx)
+    return np.array(list(E))
 
 
 def lbm_device_status(ctx, clear, stream):
@@ -355,6 +366,9 @@ class Sim:
 
     def device_status(self, clear=True):
         return lbm_device_status(self.ctx, clear, self.stream)
+
+    def electric_field(self):
+        return lbm_electric_field(self.ctx, self.stream)
 
     # diagnostics
     def stress(self, variant):

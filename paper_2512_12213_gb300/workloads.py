@@ -37,6 +37,23 @@ def hartmann(nx=256, ny=128, tau=0.8, Ha=10.0, Uw=0.05, B0=0.05, model="e", maxw
     return cfg, inputs.empty_mask(nx, ny)
 
 
+def hartmann_insulating(nx=256, ny=128, tau=0.8, Ha=10.0, B0=0.05, model="e", storage="f64"):
+    """D2Q9 channel of half-width H = ny/2 between stationary insulating walls
+    in a transverse imposed field B = (0, B0, 0): the field E = -<v> x B
+    keeps the net current zero (Eq. 36); the body force makes the centre-line
+    velocity 0.05."""
+    H = ny / 2
+    nu = (tau - 0.5) / 3
+    K = nu * Ha ** 2 / H ** 2
+    m = Ha / H
+    # u(y) = (g/K) mH coth(mH) (1 - cosh(m y)/cosh(m H))
+    g = 0.05 * K / (m * H / math.tanh(m * H) * (1 - 1 / math.cosh(m * H)))
+    cfg = dict(lattice=9, nx=nx, ny=ny, nz=1, periodic=(1, 0, 1), tau=tau, force_model=model, g=(g, 0.0, 0.0),
+               lorentz=1, B=(0.0, B0, 0.0), sigma_e=K / B0 ** 2, insulating=1, mu=1.0, storage=storage,
+               wall_u=((0, 0, 0),), face_wall=(1, 1, 1, 1, 1, 1))
+    return cfg, inputs.empty_mask(nx, ny)
+
+
 # body forces for the sphere case, from a Stokes estimate with a finite-Re
 # drag factor (the measured Reynolds number is reported by the benchmark)
 SPHERE_RE = {20: dict(tau=0.68, g=4.5e-7), 100: dict(tau=0.536, g=1.9e-7)}

@@ -50,7 +50,8 @@ def test_buffer_sizes(lib):
 
 @pytest.mark.parametrize("field,value,msg", [
     ("lattice", 7, "lattice"), ("nx", 0, "nx"), ("tau", 0.5, "tau"), ("force_model", 5, "force_model"),
-    ("storage", 4, "storage"), ("dx", 0.0, "dx"), ("nz", 2, "D2Q9"),
+    ("storage", 4, "storage"), ("dx", 0.0, "dx"), ("nz", 2, "D2Q9"), ("insulating", 1, "Lorentz"),
+    ("insulating", 2, "insulating"),
 ])
 def test_invalid_configs_rejected(lib, field, value, msg):
     cfg, mask = workloads.poiseuille(nx=8, ny=6)
@@ -109,3 +110,16 @@ def test_stochastic_rounding_only_for_16_bit(lib):
     with pytest.raises(lbm.LbmError, match="16-bit"):
         lbm.lbm_buffer_sizes(lbm.make_config(**dict(cfg, rounding="stochastic")), mask)
     lbm.lbm_buffer_sizes(lbm.make_config(**dict(cfg, storage="f16s", rounding="stochastic")), mask)
+
+
+def test_insulating_walls_scratch(lib):
+    """Insulating walls add a field block and one row of 3 doubles per step
+    thread (FP64: 2 nodes per thread, else 4) to the scratch buffer."""
+    cfg, mask = workloads.hartmann_insulating(nx=100, ny=40)
+    plain = lbm.lbm_buffer_sizes(lbm.make_config(**dict(cfg, insulating=0)), mask)
+    ins = lbm.lbm_buffer_sizes(lbm.make_config(**cfg), mask)
+    threads = (128 // 2) * 40
+    assert ins[lbm.BUF_SCRATCH] >= plain[lbm.BUF_SCRATCH] + 3 * 8 * threads
+    assert ins[lbm.BUF_POP_A] == plain[lbm.BUF_POP_A]
+    ins32 = lbm.lbm_buffer_sizes(lbm.make_config(**dict(cfg, storage="f32")), mask)
+    assert ins[lbm.BUF_SCRATCH] - ins32[lbm.BUF_SCRATCH] >= 3 * 8 * (threads // 2) - 256

@@ -1,0 +1,135 @@
+"""Insulating walls (Sec. 6, Eq. 36) on the GPU: the field E = -<v> x B is
+kept on the device and set after every step from that step's mean flow
+velocity.  Checked against the FP64 oracle, which carries the field as
+explicit state (populations and field, step by step), against the closed
+form of the insulating Hartmann flow, and against the zero total Lorentz
+force at steady state."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2512_12213_gb300 import inputs, lbm, workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 2e-6, "f16s": 1e-4, "bf16s": 1e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2512_12213_gb300 import build
+    build.build()
+    lbm.load()
+    assert torch.cuda.is_available()
+
+
+def _rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _case(name, storage, model="e"):
+    if name == "channel_2d":          # ragged D2Q9 channel with a cylinder, in-plane field
+        nx, ny = 70, 37
+        mask = inputs.cylinder_mask(nx, ny, (30.5, 17.2), 5.1, wall=2)
+        cfg = dict(lattice=9, nx=nx, ny=ny, nz=1, periodic=(1, 0, 1), dx=0.5, dt=0.2, tau=0.71, force_model=model,
+                   g=(4e-3, 0, 0), lorentz=1, B=(0.02, 0.11, 0.0), E=(0.0, 0.0, 1e-3), sigma_e=0.6, mu=1.0,
+                   insulating=1, storage=storage, wall_u=((0, 0, 0), (0, 0, 0)), face_wall=(1, 1, 1, 1, 1, 1))
+    elif name == "duct_3d":           # D3Q19 duct, oblique field, Maxwell equilibrium too
+        nx, ny, nz = 41, 14, 11
+        mask = inputs.random_solids(nx, ny, nz, 0.03, n_walls=1, seed=31)
+        cfg = dict(lattice=19, nx=nx, ny=ny, nz=nz, periodic=(1, 0, 0), tau=0.66, force_model=model,
+                   g=(8e-5, 1e-5, 0), lorentz=1, B=(0.03, 0.08, 0.05), E=(2e-4, 0, -1e-4), sigma_e=0.9, mu=1.1,
+                   maxwell=1, insulating=1, storage=storage, wall_u=((0, 0, 0), (0.01, 0, 0)),
+                   face_wall=(1, 1, 1, 2, 1, 1))
+    elif name == "periodic_3d":       # fully periodic D3Q19 with a sphere (16-bit vector path)
+        nx, ny, nz = 64, 20, 18
+        mask = inputs.sphere_mask(nx, ny, nz, (20.3, 9.6, 8.8), 4.2, wall=1)
+        cfg = dict(lattice=19, nx=nx, ny=ny, nz=nz, periodic=(1, 1, 1), tau=0.7, force_model=model,
+                   g=(1e-4, 0, 0), lorentz=1, B=(0.0, 0.1, 0.02), sigma_e=0.5, insulating=1, storage=storage,
+                   wall_u=((0, 0, 0),))
+    return cfg, mask
+
+
+def _start(orc, cfg, mask):
+    ocfg = orc.make_cfg(**workloads.oracle_kwargs(cfg))
+    nz, ny, nx = mask.shape
+    D = 2 if cfg["lattice"] == 9 else 3
+    rho, u = inputs.smooth_fields(nx, ny, nz, dims=D, u_amplitude=0.03, seed=3)
+    c = cfg.get("dx", 1.0) / cfg.get("dt", 1.0)
+    f0 = orc.init(ocfg, mask, rho, u * c, inputs.noise(cfg["lattice"], nx, ny, nz, 1e-3, seed=4))
+    return ocfg, f0
+
+
+@pytest.mark.parametrize("name,storage,model", [
+    ("channel_2d", "f64", "e"), ("channel_2d", "f64", "c"), ("duct_3d", "f64", "d"), ("periodic_3d", "f64", "e"),
+    ("channel_2d", "f32", "e"), ("duct_3d", "f32", "b"), ("periodic_3d", "f16s", "e"), ("channel_2d", "bf16s", "a")])
+def test_populations_and_field_against_oracle(orc, name, storage, model):
+    cfg, mask = _case(name, storage, model)
+    ocfg, f0 = _start(orc, cfg, mask)
+    sim = lbm.Sim(cfg, mask)
+    sim.import_f(f0)
+    # after import the next step uses the configured field
+    assert np.allclose(sim.electric_field(), cfg.get("E", (0, 0, 0)), rtol=0, atol=0)
+    steps = 20
+    sim.step(steps)
+    f_ref, E_ref = orc.run_e(ocfg, mask, f0, steps)
+    assert _rel(sim.export_f().cpu().numpy(), f_ref) < TOL[storage]
+    E = sim.electric_field()
+    assert _rel(E, E_ref) < (1e-11 if storage == "f64" else 50 * TOL[storage])
+    # the field moved away from the configured one
+    assert _rel(E, cfg.get("E", (0, 0, 0))) > 1e-3
+
+
+def test_field_reset_and_no_replay(orc):
+    cfg, mask = _case("channel_2d", "f64")
+    sim = lbm.Sim(cfg, mask)
+    sim.rest()
+    sim.step(5)
+    assert _rel(sim.electric_field(), cfg["E"]) > 1e-6
+    sim.rest()
+    assert np.array_equal(sim.electric_field(), np.array(cfg["E"]))
+    buf = torch.empty(sim.sizes[lbm.BUF_POP_A], dtype=torch.uint8, device=sim.device)
+    out = torch.empty_like(buf)
+    lbm.lbm_save_state(sim.ctx, buf, sim.stream)
+    with pytest.raises(lbm.LbmError, match="field is state"):
+        lbm.lbm_step_from(sim.ctx, buf, out, 0, sim.stream)
+    sim.step(3)
+    lbm.lbm_load_state(sim.ctx, buf, 0, sim.stream)
+    assert np.array_equal(sim.electric_field(), np.array(cfg["E"]))
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_insulating_hartmann_256x128(storage):
+    """Ha 10 between stationary insulating walls, H = 64: the cosh profile of
+    nu u'' + g - K (u - <u>) = 0 within the halfway-bounce-back error, the
+    zero-current field E_z = -B0 <v_x>, zero total Lorentz force (sum rho a =
+    sum rho g, Eq. 36) and walls that carry the body force of g alone."""
+    cfg, mask = workloads.hartmann_insulating(storage=storage)
+    sim = lbm.Sim(cfg, mask)
+    sim.rest()
+    sim.step(60000)
+    H, Ha, tau = 64, 10.0, cfg["tau"]
+    nu = (tau - 0.5) / 3
+    K = nu * Ha ** 2 / H ** 2
+    m = Ha / H
+    g = cfg["g"][0]
+    y = np.arange(128) - H + 0.5
+    u = (g / K) * m * H / np.tanh(m * H) * (1 - np.cosh(m * y) / np.cosh(m * H))
+    _, _, _, v = sim.stress(lbm.S2)
+    vx = v[0, 0, :, 17].cpu().numpy()
+    assert _rel(vx, u) < 1e-3
+    vmean = v[0, 0].cpu().numpy().mean()
+    E = sim.electric_field()
+    assert abs(E[2] / (-cfg["B"][1] * vmean) - 1) < (1e-9 if storage == "f64" else 1e-5)
+    mass, _, body = sim.balance()
+    tol = 1e-9 if storage == "f64" else 1e-4
+    assert abs(body[0] / (g * mass) - 1) < tol
+    F = sim.wall_force(1)          # both walls carry wall id 1
+    if storage == "f64":
+        assert abs(F[0] / (g * mass) - 1) < 1e-8
+    else:
+        # a rounded fixed point conserves momentum per step only up to the
+        # rounding of every stored deviation, N Q 2^-24 max|d|
+        w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+        d = sim.export_f().cpu().numpy()[:, 0] - w[:, None, None]
+        assert abs(F[0] - g * mass) < 256 * 128 * 9 * 2.0 ** -24 * np.abs(d).max()
