@@ -122,6 +122,20 @@ static long link_dest(const orc_cfg* c, const lat_t* L, const unsigned char* wid
     return d;
 }
 
+/* index of the node one link away along a (periodic axes wrap), or -1 when
+ * the link leaves the box through a closed face */
+static long neighbour(const orc_cfg* c, const lat_t* L, int x, int y, int z, int a)
+{
+    int p[3] = {x + L->e[a][0], y + L->e[a][1], z + L->e[a][2]};
+    const int n[3] = {c->nx, c->ny, c->nz};
+    for (int k = 0; k < 3; ++k) {
+        if (p[k] >= 0 && p[k] < n[k]) continue;
+        if (!c->periodic[k]) return -1;
+        p[k] = (p[k] + n[k]) % n[k];
+    }
+    return ((long)p[2] * c->ny + p[1]) * c->nx + p[0];
+}
+
 static const double* wall_velocity(const orc_cfg* c, int wall)
 {
     static const double zero[3] = {0, 0, 0};
@@ -254,8 +268,27 @@ static void step_work(const orc_cfg* c, const lat_t* L, const unsigned char* wid
                 for (int a = 0; a < Q; ++a) {
                     int wall = 0;
                     long d = link_dest(c, L, wid, x, y, z, a, &wall);
-                    if (d >= 0) fnew[a * N + d] = frel[a * N + n];
-                    else fnew[L->opp[a] * N + n] = frel[a * N + n] - ladd(c, L, a, wall);
+                    if (d >= 0) {
+                        fnew[a * N + d] = frel[a * N + n];
+                        continue;
+                    }
+                    const int b = L->opp[a];
+                    const double out = frel[a * N + n] - ladd(c, L, a, wall);
+                    const long s = c->phi ? neighbour(c, L, x, y, z, a) : -1;
+                    if (s < 0 || wid[s] == 0) {            /* box face, or no wall distance */
+                        fnew[b * N + n] = out;
+                        continue;
+                    }
+                    const double q = (double)c->phi[n] / ((double)c->phi[n] - (double)c->phi[s]);
+                    if (q >= 0.5) {
+                        fnew[b * N + n] = out / (2.0 * q) + (1.0 - 1.0 / (2.0 * q)) * frel[b * N + n];
+                    } else {
+                        int w2 = 0;
+                        const long ff = link_dest(c, L, wid, x, y, z, b, &w2);
+                        fnew[b * N + n] = (ff < 0) ? out
+                                                   : 2.0 * q * frel[a * N + n] + (1.0 - 2.0 * q) * frel[a * N + ff] -
+                                                         ladd(c, L, a, wall);
+                    }
                 }
             }
     memcpy(f, fnew, sizeof(double) * N * Q);
@@ -514,6 +547,7 @@ int orc_adjoint_drag(const orc_cfg* c, const unsigned char* wid, const double* f
 {
     lat_t L;
     if (get_lat(c->q, &L)) return -1;
+    if (c->phi) return -2;        /* the transpose below is that of halfway bounce-back */
     const long N = nnodes(c);
     const int Q = L.q;
     const double cc = c->dx / c->dt, s = cell_volume(c, &L) / c->dt, h = 1e-30;

@@ -61,6 +61,13 @@ typedef struct orc_cfg {
     int n_walls;           /* wall ids 1..n_walls */
     double wall_u[ORC_MAX_WALLS][3];   /* velocity of wall k at index k-1 */
     int face_wall[6];
+    const float* phi;      /* NULL: halfway bounce-back on every solid link.  Else the
+                              signed wall distance per node (N floats, > 0 in fluid,
+                              < 0 in solid, in lattice units): a solid link from x_f
+                              to x_s crosses the wall at x_f + q e with
+                              q = phi_f / (phi_f - phi_s), and the incoming population
+                              is interpolated (see orc_step).  Closed box faces stay
+                              halfway. */
     int insulating;        /* 1 (with lorentz): insulating walls, no net current.  The
                               field E of step t is -<v> x B with <v> the mean flow
                               velocity over fluid nodes of step t-1 (the first step
@@ -90,7 +97,15 @@ void orc_init(const orc_cfg* c, const unsigned char* wall_id, const double* rho,
               const double* u, const double* xi, double* f);
 
 /* one step of Eq. (2): f (in: f(t), out: f(t+dt)); frel (N*Q) receives
- * f^rel(t) if not NULL */
+ * f^rel(t) if not NULL.  A population f^rel_a(x_f) leaving a fluid node into
+ * a solid node returns as f_b(x_f, t+dt), b = opp(a), by halfway bounce-back
+ * f_b = f^rel_a(x_f) - L (L the moving-wall term) or, with cfg->phi, by linear
+ * interpolation at the wall point x_f + q e_a:
+ *   q <  1/2: f_b = 2q f^rel_a(x_f) + (1 - 2q) f^rel_a(x_f + e_b) - L
+ *   q >= 1/2: f_b = (f^rel_a(x_f) - L)/(2q) + (1 - 1/(2q)) f^rel_b(x_f)
+ * (halfway when q < 1/2 and x_f + e_b is not a fluid node).  The momentum
+ * exchange of Eq. (25) with these values refers to the imaginary point
+ * x_f + e_a/2 (discussion after Eq. 25). */
 void orc_step(const orc_cfg* c, const unsigned char* wall_id, double* f, double* frel);
 
 /* run n steps in place (with cfg->insulating, E starts at cfg->E and is
@@ -128,7 +143,8 @@ void orc_balance(const orc_cfg* c, const unsigned char* wall_id, const double* f
 /* time-averaged drag J = (1/T) sum_{t=0}^{T-1} d . F_wall(t) (uncorrected
  * momentum exchange on wall `wall`) from the canonical initial state f0, and
  * its gradient with respect to theta = (g[0..2], u_w[0..2] of `wall`), by the
- * discrete adjoint with complex-step collision Jacobians.  grad[6]. */
+ * discrete adjoint with complex-step collision Jacobians.  grad[6].  Returns
+ * -2 with cfg->phi (interpolated walls have no transpose here). */
 int orc_adjoint_drag(const orc_cfg* c, const unsigned char* wall_id, const double* f0, int T,
                      int wall, const double* d, double* J, double* grad);
 

@@ -20,7 +20,14 @@ identities (no GPU).
 * insulating walls (Eq. 36): with E = -<v> x B the Hartmann profile
   converges at second order to nu u'' + g - K (u - <u>) = 0, u(+-H) = 0, and at
   steady state the total Lorentz force vanishes, so the walls carry exactly
-  the body force of g (Eq. 34 with a zero Lorentz term).
+  the body force of g (Eq. 34 with a zero Lorentz term);
+* walls off the half-grid (discussion after Eq. 25, end of Sec. 6), linear
+  interpolated bounce-back from a signed wall distance: q = 1/2 is halfway
+  bounce-back exactly; Poiseuille between walls at arbitrary positions
+  converges at second order to the parabola of the true walls (halfway
+  bounce-back on the same nodes only at first order); the exact per-step
+  momentum balance holds with the interpolated values (momentum exchange at
+  the imaginary points).
 """
 import numpy as np
 import pytest
@@ -343,3 +350,75 @@ def test_insulating_field_differs_from_conducting(orc):
     vi = orc.node_macro(r["cfg"], r["f"][:, 0, 16, 0])["v"][0]
     vc = orc.node_macro(cfg, fc[:, 0, 16, 0])["v"][0]
     assert vc < 0.5 * vi
+
+
+def _offgrid_channel(orc, H, q1, q2, tau=0.8, model="e", nx=2, interpolate=True):
+    """Channel with solid rows y = 0 and y = ny-1 and walls at y = 1 - q1 and
+    y = ny - 2 + q2 (q the distance of the first fluid row to the wall)."""
+    ny = 2 * H + 2
+    yw_lo, yw_hi = 1 - q1, ny - 2 + q2
+    y = np.arange(ny, dtype=float)
+    phi = np.repeat(np.minimum(y - yw_lo, yw_hi - y)[None, :, None], nx, axis=2).astype(np.float32)
+    mask = (phi < 0).astype(np.uint8)
+    nu = (tau - 0.5) / 3
+    L = yw_hi - yw_lo
+    g = 8 * nu * 0.02 / L ** 2
+    cfg = orc.make_cfg(q=9, nx=nx, ny=ny, nz=1, periodic=(1, 1, 1), tau=tau, force_model=model, g=(g, 0, 0),
+                       wall_u=((0, 0, 0),), phi=phi if interpolate else None)
+    f = _rest(orc, cfg, mask)
+    f = orc.run(cfg, mask, f, int(20 * L * L / nu / 3))
+    v = np.array([orc.node_macro(cfg, f[:, 0, j, 0])["v"][0] for j in range(1, ny - 1)])
+    yy = np.arange(1, ny - 1)
+    exact = g / (2 * nu) * (yy - yw_lo) * (yw_hi - yy)
+    return np.abs(v - exact).max() / exact.max()
+
+
+@pytest.mark.parametrize("q1,q2", [(0.3, 0.8), (0.15, 0.65)])
+def test_interpolated_walls_second_order(orc, q1, q2):
+    e = [_offgrid_channel(orc, H, q1, q2) for H in (4, 8, 16)]
+    assert e[-1] < 2e-3
+    assert 3.3 < e[0] / e[1] < 4.6 and 3.3 < e[1] / e[2] < 4.6
+    # the same nodes with halfway bounce-back see the walls half a node off
+    h = [_offgrid_channel(orc, H, q1, q2, interpolate=False) for H in (4, 8, 16)]
+    assert h[-1] > 10 * e[-1] and h[0] / h[1] < 2.2 and h[1] / h[2] < 2.2
+
+
+def test_interpolated_walls_halfway_limit(orc):
+    """phi = +-1/2 on every solid link gives q = 1/2: the interpolation is the
+    halfway rule, bit for bit, with moving walls."""
+    nx, ny, nz = 11, 9, 8
+    mask = inputs.sphere_mask(nx, ny, nz, (5.2, 4.1, 3.9), 2.6, wall=1)
+    mask[:, 0, :] = 2
+    phi = np.where(mask > 0, -0.5, 0.5).astype(np.float32)
+    kw = dict(q=19, nx=nx, ny=ny, nz=nz, periodic=(1, 1, 0), tau=0.7, force_model="d", g=(1e-3, 0, 2e-4),
+              wall_u=((0.01, -0.02, 0.0), (0.03, 0, 0.01)), face_wall=(1, 1, 1, 1, 2, 1))
+    a, b = orc.make_cfg(**kw), orc.make_cfg(**kw, phi=phi)
+    rho, u = inputs.smooth_fields(nx, ny, nz, dims=3, seed=2)
+    f0 = orc.init(a, mask, rho, u * 0.5, inputs.noise(19, nx, ny, nz, 1e-2, seed=3))
+    assert np.array_equal(orc.run(a, mask, f0, 6), orc.run(b, mask, f0, 6))
+
+
+@pytest.mark.parametrize("model", ["e", "c"])
+def test_interpolated_walls_exact_momentum_balance(orc, model):
+    """F_wall = sum rho a - [M(t+dt) - M(t)]/dt every step with the
+    interpolated incoming populations: the momentum exchange of Eq. (25) at
+    the imaginary points closes the balance exactly."""
+    nx, ny, nz = 14, 12, 10
+    c0 = np.array([6.3, 5.8, 4.6])
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    phi = (np.sqrt((x - c0[0]) ** 2 + (y - c0[1]) ** 2 + (z - c0[2]) ** 2) - 3.4).astype(np.float32)
+    mask = (phi < 0).astype(np.uint8)
+    cfg = orc.make_cfg(q=19, nx=nx, ny=ny, nz=nz, periodic=(1, 1, 1), dx=0.5, dt=0.2, tau=0.74,
+                       force_model=model, g=(3e-2, -1e-2, 5e-3), wall_u=((0.02, 0.01, -0.01),), phi=phi)
+    c = cfg.dx / cfg.dt
+    rho, u = inputs.smooth_fields(nx, ny, nz, dims=3, seed=7)
+    f = orc.init(cfg, mask, rho, u * 0.5 * c, inputs.noise(19, nx, ny, nz, 1e-2, seed=8))
+    for _ in range(4):
+        _, M0, rhoa = orc.balance(cfg, mask, f)
+        fn, fr = orc.step(cfg, mask, f)
+        _, M1, _ = orc.balance(cfg, mask, fn)
+        F = orc.wall_force(cfg, mask, fr, fn, -1, 0)
+        ref = rhoa - (M1 - M0) / cfg.dt
+        scale = np.abs(M0).max() / cfg.dt + np.abs(F).max()
+        assert np.allclose(F, ref, rtol=0, atol=2e-14 * scale), (F, ref)
+        f = fn
