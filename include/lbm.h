@@ -120,7 +120,8 @@ enum {
     LBM_BUF_LINKS = 3,        /* boundary-link list      (required if any link exists) */
     LBM_BUF_SCRATCH = 4,      /* FP64 reduction partials (required) */
     LBM_BUF_STAGE = 5,        /* canonical staging for host import/export (optional) */
-    LBM_NUM_BUFFERS = 6
+    LBM_BUF_PHI = 6,          /* signed wall distance per node, float (required if curved) */
+    LBM_NUM_BUFFERS = 7
 };
 
 #define LBM_MAX_WALLS 16
@@ -148,7 +149,24 @@ typedef struct lbm_config {
     int32_t rounding;                /* LBM_ROUND_NEAREST, or LBM_ROUND_STOCHASTIC (16-bit storage only) */
     uint32_t seed;                   /* stream of the stochastic rounding */
     int32_t insulating;              /* 1 (needs lorentz): insulating walls, see below */
+    int32_t curved;                  /* 1: walls off the half-grid from a signed distance, see below */
 } lbm_config;
+
+/* Walls off the half-grid (discussion after Eq. 25, end of Sec. 6).  With
+ * curved = 1 the context holds a signed wall distance phi per node (buffer
+ * LBM_BUF_PHI; lattice units, > 0 at fluid nodes, < 0 at solid nodes; set
+ * with lbm_set_wall_distance, +-1/2 until then).  A link from fluid node x_f
+ * along a into a solid node x_s crosses the wall at x_f + q e_a with
+ * q = phi_f / (phi_f - phi_s), and the population b = opp(a) entering x_f is
+ * interpolated from the stored post-collision values (L the moving-wall term
+ * of halfway bounce-back):
+ *   q <  1/2: f_b(x_f) = 2q f^rel_a(x_f) + (1 - 2q) f^rel_a(x_f + e_b) + L
+ *   q >= 1/2: f_b(x_f) = (f^rel_a(x_f) + L)/(2q) + (1 - 1/(2q)) f^rel_b(x_f)
+ * (halfway bounce-back when q < 1/2 and x_f + e_b is not a fluid node; closed
+ * box faces are always halfway).  q = 1/2 is halfway bounce-back.  The wall
+ * force (Eq. 25) uses these values; it then refers to the imaginary points
+ * x_f + e_a/2, and at steady state equals the body force on the fluid nodes'
+ * volume units.  The adjoint step does not support curved walls. */
 
 /* Insulating walls (Sec. 6, Eq. 36).  No current leaves the fluid, so the
  * electric field is the one that makes the net current sigma_e sum(E + v x B)
@@ -232,6 +250,13 @@ lbm_status lbm_step_from(lbm_ctx* ctx, const void* src, void* dst, int64_t t, vo
  * sets T to `t` and marks the previous state as unavailable. */
 lbm_status lbm_save_state(lbm_ctx* ctx, void* dst, void* stream);
 lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, int64_t t, void* stream);
+
+/* Signed wall distance of a curved-wall context (see above): phi_host holds
+ * nx*ny*nz floats in the canonical node order, host memory, > 0 exactly at the
+ * fluid nodes and < 0 exactly at the solid nodes of the geometry the context
+ * was created with (else LBM_ERR_ARG); NULL restores +-1/2 (halfway).  Takes
+ * effect for the next step and every later call; synchronises the stream. */
+lbm_status lbm_set_wall_distance(lbm_ctx* ctx, const float* phi_host, void* stream);
 
 /* Current time T. */
 lbm_status lbm_time(const lbm_ctx* ctx, int64_t* t);

@@ -78,6 +78,7 @@ bool validate(const lbm_config* c, const uint8_t* wid, std::string& err)
         return fail("stochastic rounding applies to 16-bit storage only");
     if (c->insulating != 0 && c->insulating != 1) return fail("insulating must be 0 or 1");
     if (c->insulating && !c->lorentz) return fail("insulating walls need the Lorentz force (lorentz = 1)");
+    if (c->curved != 0 && c->curved != 1) return fail("curved must be 0 or 1");
     if (!wid) return fail("wall_id is NULL");
     const long long N = nodes_of(c);
     for (long long n = 0; n < N; ++n)
@@ -195,6 +196,7 @@ void sizes_of(const lbm_config* c, long long n_links, size_t s[LBM_NUM_BUFFERS])
     if (c->insulating)
         s[LBM_BUF_SCRATCH] = round256((SCRATCH_INS_ROWS + 3 * (size_t)step_threads_of(c)) * sizeof(double));
     s[LBM_BUF_STAGE] = round256((size_t)(c->lattice + 4) * N * sizeof(double));
+    s[LBM_BUF_PHI] = c->curved ? round256((size_t)sq * sizeof(float)) : 0;
 }
 
 template <typename R> void cast_kp(const KP<double>& s, KP<R>& d)
@@ -351,13 +353,28 @@ void choose_tile(Ctx& x)
     // LBM_STEP_KERNEL=tile selects the shared-memory staged step where it fits;
     // the register-tiled step is the default
     const char* sel = getenv("LBM_STEP_KERNEL");
-    const bool want_tile = sel && strcmp(sel, "tile") == 0 && x.cfg.rounding == LBM_ROUND_NEAREST && !x.insulating;
+    const bool want_tile = sel && strcmp(sel, "tile") == 0 && x.cfg.rounding == LBM_ROUND_NEAREST && !x.insulating && !x.cfg.curved;
     const bool fits = want_tile && smem_for(R, ns) <= (size_t)x.smem_optin;
     x.tile_R = fits ? R : 0;
     x.tile_stages = fits ? ns : 0;
     x.tile_smem = fits ? smem_for(R, ns) : 0;
     x.tile_ntiles = fits ? ((x.cfg.ny + R - 1) / R) * x.cfg.nz : 0;
     x.tile_blocks = 0;
+}
+
+// signed wall distance in the padded layout: the given canonical values, or
+// +-1/2 (halfway bounce-back) when phi is null; padding gets 0
+std::vector<float> padded_distance(const Ctx& x, const float* phi)
+{
+    std::vector<float> out((size_t)x.geo.sq, 0.0f);
+    for (int z = 0; z < x.cfg.nz; ++z)
+        for (int y = 0; y < x.cfg.ny; ++y)
+            for (int xx = 0; xx < x.cfg.nx; ++xx) {
+                const size_t n = ((size_t)z * x.cfg.ny + y) * x.cfg.nx + xx;
+                const size_t pn = ((size_t)z * x.cfg.ny + y) * x.geo.nxp + xx;
+                out[pn] = phi ? phi[n] : (x.host_wid[n] ? -0.5f : 0.5f);
+            }
+    return out;
 }
 
 struct DeviceGuard {
@@ -505,7 +522,7 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
     size_t need[LBM_NUM_BUFFERS];
     sizes_of(&x.cfg, x.n_links, need);
     for (int b = 0; b < LBM_NUM_BUFFERS; ++b) {
-        const bool optional = (b == LBM_BUF_STAGE) || (b == LBM_BUF_LINKS && need[b] == 0);
+        const bool optional = (b == LBM_BUF_STAGE) || ((b == LBM_BUF_LINKS || b == LBM_BUF_PHI) && need[b] == 0);
         if (!buffers[b]) {
             if (optional) continue;
             g_cfg_err = "required buffer " + std::to_string(b) + " is NULL";
@@ -533,6 +550,8 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
     bind_insulating(x);
     x.stage = buffers[LBM_BUF_STAGE];
     x.stage_bytes = x.stage ? sizes[LBM_BUF_STAGE] : 0;
+    x.geo.phi = x.cfg.curved ? (const float*)buffers[LBM_BUF_PHI] : nullptr;
+    if (x.cfg.curved) x.host_wid.assign(host_wall_id, host_wall_id + nodes_of(cfg));
     x.t = 0;
     x.prev_valid = false;
     if (cudaGetDevice(&x.device) != cudaSuccess) {
@@ -554,6 +573,11 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
         e = cudaMemcpyAsync(x.links, links.data(), links.size() * sizeof(Link), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = launch_zero(x.scratch, (long long)SCRATCH_DOUBLES, st);
     if (e == cudaSuccess && x.insulating) e = ins_reset(x, st);
+    std::vector<float> phi0;
+    if (e == cudaSuccess && x.cfg.curved) {
+        phi0 = padded_distance(x, nullptr);
+        e = cudaMemcpyAsync((void*)x.geo.phi, phi0.data(), phi0.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+    }
     // solid and padding entries of both population buffers start defined
     if (e == cudaSuccess) e = cudaMemsetAsync(x.pop[0], 0, need[LBM_BUF_POP_A], st);
     if (e == cudaSuccess) e = cudaMemsetAsync(x.pop[1], 0, need[LBM_BUF_POP_B], st);
@@ -752,6 +776,33 @@ lbm_status lbm_time(const lbm_ctx* ctx, int64_t* t)
     return LBM_OK;
 }
 
+lbm_status lbm_set_wall_distance(lbm_ctx* ctx, const float* phi_host, void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (!x.cfg.curved) return arg_fail(x, "lbm_set_wall_distance needs a context created with curved = 1");
+    if (phi_host) {
+        const long long N = nodes(x);
+        for (long long n = 0; n < N; ++n) {
+            const float v = phi_host[n];
+            const bool ok = x.host_wid[n] ? (v < 0.0f) : (v > 0.0f);
+            if (!ok || !std::isfinite(v)) {
+                char buf[200];
+                snprintf(buf, sizeof buf,
+                         "wall distance %g at node %lld: it must be > 0 at fluid nodes and < 0 at solid nodes", (double)v,
+                         n);
+                return arg_fail(x, buf);
+            }
+        }
+    }
+    GUARD(x);
+    const std::vector<float> ph = padded_distance(x, phi_host);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync((void*)x.geo.phi, ph.data(), ph.size() * sizeof(float), cudaMemcpyHostToDevice, st), "copy phi");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    return LBM_OK;
+}
+
 lbm_status lbm_electric_field(lbm_ctx* ctx, double* E, void* stream)
 {
     if (!ctx) return LBM_ERR_ARG;
@@ -842,8 +893,8 @@ lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* state_prev, const void* ph
 {
     if (!ctx) return LBM_ERR_ARG;
     Ctx& x = ctx->c;
-    if (x.cfg.lorentz || x.cfg.les) {
-        x.err = "the adjoint supports a uniform body force without LES";
+    if (x.cfg.lorentz || x.cfg.les || x.cfg.curved) {
+        x.err = "the adjoint supports a uniform body force without LES, on halfway walls";
         return LBM_ERR_UNSUPPORTED;
     }
     if (!state_prev || !phi_out || !dir || phi_out == phi_next) return arg_fail(x, "bad adjoint buffers");

@@ -220,6 +220,7 @@ struct Geo {
     long long sq;           // elements between direction planes (= nxp*ny*nz)
     int periodic[3];
     int face_wall[6];
+    const float* phi;       // signed wall distance per node (padded layout), or null: halfway walls
 };
 
 // node classes (one byte per node, padded layout)
@@ -626,9 +627,53 @@ __device__ __forceinline__ bool pull_source(const Geo& g, const uint8_t* __restr
     return true;
 }
 
+// index of the node (x+ex, y+ey, z+ez), periodic axes wrapped; -1 through a
+// closed face of the box
+__device__ __forceinline__ long long link_target(const Geo& g, int x, int y, int z, int ex, int ey, int ez)
+{
+    int xs = 0, ys = 0, zs = 0, wall = 0;
+    if (!axis_step(x + ex, g.nx, g.periodic[0], 0, 0, xs, wall)) return -1;
+    if (!axis_step(y + ey, g.ny, g.periodic[1], 0, 0, ys, wall)) return -1;
+    if (!axis_step(z + ez, g.nz, g.periodic[2], 0, 0, zs, wall)) return -1;
+    return ((long long)zs * g.ny + ys) * g.nxp + xs;
+}
+
+// The population f_b(x, T) entering fluid node x (padded index own) through a
+// link a = opp(b) that leaves x into a solid node or through a closed face
+// (wall id `wall`), from the stored post-collision state P (deviations; RAW:
+// storage units).  Halfway bounce-back P_a(x) + L with Ladd's term
+// L = w_b E_b . LW; with a wall distance (g.phi) and a solid node x + E_a,
+// the linear interpolation at the wall point x + q E_a,
+// q = phi(x) / (phi(x) - phi(x + E_a)):
+//   q <  1/2: 2q P_a(x) + (1 - 2q) P_a(x - E_a) + L   (halfway if x - E_a is no fluid node)
+//   q >= 1/2: (P_a(x) + L)/(2q) + (1 - 1/(2q)) P_b(x)
+// The weights sum to 1, so the rule holds for the shifted deviations too.
+template <int Q, class S, bool RAW>
+__device__ __forceinline__ typename S::R bounced(const typename S::T* __restrict__ P, const uint8_t* __restrict__ cls,
+                                                 const Geo& g, const KP<typename S::R>& p, int x, int y, int z,
+                                                 long long own, int b, int wall)
+{
+    using R = typename S::R;
+    auto cv = [](typename S::T v) { return RAW ? S::to_raw(v) : S::to_r(v); };
+    const int a = OPP<Q>(b);
+    const R L = R(WD<Q>(b)) * (R(EX<Q>(b)) * p.LW[wall][0] + R(EY<Q>(b)) * p.LW[wall][1] + R(EZ<Q>(b)) * p.LW[wall][2]);
+    const R Pa = cv(P[(long long)a * g.sq + own]);
+    const R out = Pa + L;
+    if (!g.phi) return out;
+    const long long s = link_target(g, x, y, z, EX<Q>(a), EY<Q>(a), EZ<Q>(a));
+    if (s < 0 || !nc_solid(cls[s])) return out;            // a closed box face
+    const R pf = R(g.phi[own]), ps = R(g.phi[s]);
+    const R q = pf / (pf - ps);
+    if (q >= R(0.5)) return out / (R(2) * q) + (R(1) - R(1) / (R(2) * q)) * cv(P[(long long)b * g.sq + own]);
+    long long ff;
+    int w2;
+    if (!pull_source(g, cls, x, y, z, EX<Q>(a), EY<Q>(a), EZ<Q>(a), ff, w2)) return out;
+    return R(2) * q * Pa + (R(1) - R(2) * q) * cv(P[(long long)a * g.sq + ff]) + L;
+}
+
 // canonical post-propagation deviations at node (x,y,z) from a stored
-// post-collision state: d_b(x) = P_b(x - E_b), or P_opp(b)(x) + w_b E_b.LW
-// through a wall (halfway bounce-back with Ladd's moving-wall term)
+// post-collision state: d_b(x) = P_b(x - E_b), or the bounced population
+// through a wall (halfway or interpolated bounce-back, see bounced)
 template <int Q, class S, bool RAW = false>
 __device__ __forceinline__ void gather_node(const typename S::T* __restrict__ P, const uint8_t* __restrict__ cls,
                                             const Geo& g, const KP<typename S::R>& p, int x, int y, int z,
@@ -646,9 +691,7 @@ __device__ __forceinline__ void gather_node(const typename S::T* __restrict__ P,
         } else if (pull_source(g, cls, x, y, z, EX<Q>(b), EY<Q>(b), EZ<Q>(b), src, wall)) {
             d[b] = cv(P[(long long)b * g.sq + src]);
         } else {
-            const R w = R(WD<Q>(b));
-            const R el = R(EX<Q>(b)) * p.LW[wall][0] + R(EY<Q>(b)) * p.LW[wall][1] + R(EZ<Q>(b)) * p.LW[wall][2];
-            d[b] = cv(P[(long long)OPP<Q>(b) * g.sq + own]) + w * el;
+            d[b] = bounced<Q, S, RAW>(P, cls, g, p, x, y, z, own, b, wall);
         }
     }
 }

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -128,6 +129,8 @@ struct Ctx {
     size_t tile_smem;
     mutable int tile_blocks;
     unsigned* errflag;
+    // curved walls: the wall ids of the geometry (host), to check distances
+    std::vector<uint8_t> host_wid;
     // insulating walls: step threads (rows of the velocity sum) and fluid nodes
     bool insulating;
     long long ins_threads;

@@ -559,6 +559,58 @@ __device__ __forceinline__ R src_value(const SrcFields& s, const KP<R>& p, int a
     return R(fe - WD<Q>(a) * (double)p.rho0);
 }
 
+// canonical index of a fluid node given by its padded index
+__device__ __forceinline__ long long canon_of(const Geo& g, long long padded)
+{
+    const int xs = (int)(padded % g.nxp);
+    return (padded / g.nxp) * g.nx + xs;
+}
+
+// The stored value P_a(x) of a link a that leaves fluid node x (padded own,
+// canonical nd) into a wall, such that the bounced population of opp(a) at x
+// (see bounced) is the given f_opp(a)(x): the inverse of the halfway or
+// interpolated rule.  Every case is explicit except both opposite links of
+// x hitting solids with q >= 1/2, a 2 x 2 solve.
+template <int Q, typename R, class Src>
+__device__ R unbounced(const Src& s, const KP<R>& p, const Geo& g, const uint8_t* __restrict__ cls, int x, int y, int z,
+                       long long own, long long nd, int a, int wall)
+{
+    const int b = OPP<Q>(a);
+    const R Lb = R(WD<Q>(b)) * (R(EX<Q>(b)) * p.LW[wall][0] + R(EY<Q>(b)) * p.LW[wall][1] + R(EZ<Q>(b)) * p.LW[wall][2]);
+    const R fb = src_value<Q, R>(s, p, b, nd);
+    const R half = fb - Lb;
+    if (!g.phi) return half;
+    const long long sa = link_target(g, x, y, z, EX<Q>(a), EY<Q>(a), EZ<Q>(a));
+    if (sa < 0 || !nc_solid(cls[sa])) return half;               // a closed box face
+    const R qa = R(g.phi[own]) / (R(g.phi[own]) - R(g.phi[sa]));
+    long long nb;
+    int wb;
+    const bool b_fluid = pull_source(g, cls, x, y, z, EX<Q>(a), EY<Q>(a), EZ<Q>(a), nb, wb);   // x + E_b = x - E_a
+    if (qa < R(0.5)) {
+        if (!b_fluid) return half;
+        const R fa = src_value<Q, R>(s, p, a, nd);                // = P_a(x - E_a)
+        return (fb - Lb - (R(1) - R(2) * qa) * fa) / (R(2) * qa);
+    }
+    R Pb;
+    if (b_fluid) {
+        Pb = src_value<Q, R>(s, p, b, canon_of(g, nb));           // node x + E_b pulls b from x
+        return R(2) * qa * fb - (R(2) * qa - R(1)) * Pb - Lb;
+    }
+    // the link b of x hits a wall too (wall id wb)
+    const R La = R(WD<Q>(a)) * (R(EX<Q>(a)) * p.LW[wb][0] + R(EY<Q>(a)) * p.LW[wb][1] + R(EZ<Q>(a)) * p.LW[wb][2]);
+    const R fa = src_value<Q, R>(s, p, a, nd);
+    const long long sb = link_target(g, x, y, z, EX<Q>(b), EY<Q>(b), EZ<Q>(b));
+    const R qb = (sb >= 0 && nc_solid(cls[sb])) ? R(g.phi[own]) / (R(g.phi[own]) - R(g.phi[sb])) : R(0.5);
+    if (qb < R(0.5) || !(sb >= 0 && nc_solid(cls[sb]))) {
+        // b bounces halfway (its second node x + E_a is the solid, or a face)
+        Pb = fa - La;
+        return R(2) * qa * fb - (R(2) * qa - R(1)) * Pb - Lb;
+    }
+    const R A1 = R(2) * qa * fb - Lb, k1 = R(2) * qa - R(1);
+    const R A2 = R(2) * qb * fa - La, k2 = R(2) * qb - R(1);
+    return (A1 - k1 * A2) / (R(1) - k1 * k2);
+}
+
 template <int Q, class S, class Src>
 __global__ void __launch_bounds__(NODE_THREADS)
 k_inverse_stream(typename S::T* __restrict__ P, const uint8_t* __restrict__ cls, const Geo g,
@@ -591,8 +643,7 @@ k_inverse_stream(typename S::T* __restrict__ P, const uint8_t* __restrict__ cls,
                 const long long ns = rs * g.nx + xs;
                 val = src_value<Q, R>(s, p, a, ns);
             } else {
-                const R el = R(EX<Q>(a)) * p.LW[wall][0] + R(EY<Q>(a)) * p.LW[wall][1] + R(EZ<Q>(a)) * p.LW[wall][2];
-                val = src_value<Q, R>(s, p, OPP<Q>(a), nd) + R(WD<Q>(a)) * el;
+                val = unbounced<Q, R>(s, p, g, cls, x, y, z, n, nd, a, wall);
             }
             P[(long long)a * g.sq + n] = S::from_r(val);
         }
@@ -626,12 +677,14 @@ k_export(const typename S::T* __restrict__ P, const uint8_t* __restrict__ cls, c
 
 // ------------------------------------------------------------- wall force
 // One thread per boundary link (x_f, a') of one wall: fbar_a' = P_a'(x_f)
-// = f^rel(x_f, T-1), fbar_a = f_opp(a')(x_f, T) = fbar_a' - w E_a'.LW.
+// = f^rel(x_f, T-1), fbar_a = f_opp(a')(x_f, T), the bounced population
+// (halfway: fbar_a' - w E_a'.LW; interpolated with a wall distance).
 // Per link (dx^D/dt) [e_a' (fbar_a' + fbar_a) + corrections], in FP64.
 template <int Q, class S>
 __global__ void __launch_bounds__(RED_THREADS)
-k_links(const typename S::T* __restrict__ P, const Link* __restrict__ links, long long begin, long long end,
-        const Geo g, const KP<typename S::R> p, unsigned flags, double* __restrict__ partials)
+k_links(const typename S::T* __restrict__ P, const uint8_t* __restrict__ cls, const Link* __restrict__ links,
+        long long begin, long long end, const Geo g, const KP<typename S::R> p, unsigned flags,
+        double* __restrict__ partials)
 {
     __shared__ double sm[3 * 32];
     double acc[3] = {0.0, 0.0, 0.0};
@@ -650,8 +703,14 @@ k_links(const typename S::T* __restrict__ P, const Link* __restrict__ links, lon
                 w = WD<Q>(b);
             }
         fo = (double)S::to_r(P[(long long)a * g.sq + L.node]) + w * rho0;
-        const double el = e[0] * (double)p.LW[L.wall][0] + e[1] * (double)p.LW[L.wall][1] + e[2] * (double)p.LW[L.wall][2];
-        const double fi = fo - w * el;        // bounced population f_opp(a')(x_f, T)
+        // bounced population f_opp(a')(x_f, T)
+        const int xn = (int)(L.node % g.nxp);
+        const long long rn = L.node / g.nxp;
+        const int yn = (int)(rn % g.ny), zn = (int)(rn / g.ny);
+        double fi = 0.0;
+#pragma unroll
+        for (int b = 1; b < Q; ++b)
+            if (OPP<Q>(b) == a) fi = (double)bounced<Q, S, false>(P, cls, g, p, xn, yn, zn, L.node, b, L.wall) + w * rho0;
         double mxa = 0.0;
         if ((flags & 2u) && p.maxwell)
 #pragma unroll
@@ -945,7 +1004,7 @@ cudaError_t launch_links(const Ctx& c, const void* P, long long begin, long long
     using T = typename S::T;
     const int blocks = grid_for(end - begin, RED_THREADS, MAX_PARTIAL_ROWS);
     *nblocks = blocks;
-    k_links<Q, S><<<blocks, RED_THREADS, 0, st>>>((const T*)P, c.links, begin, end, c.geo, kp_of<S>(c), flags,
+    k_links<Q, S><<<blocks, RED_THREADS, 0, st>>>((const T*)P, c.cls, c.links, begin, end, c.geo, kp_of<S>(c), flags,
                                                   partials);
     return cudaGetLastError();
 }

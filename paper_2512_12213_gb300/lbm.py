@@ -25,7 +25,7 @@ ROUND = {"nearest": 0, "stochastic": 1}
 S1, S2, S3, S4 = 1, 2, 3, 4
 MOVING_CORR, MAXWELL_REMOVE, ACCUMULATE = 1, 2, 4
 OUT_DEVICE, OUT_HOST, OUT_HOST_ASYNC = 0, 1, 2
-BUF_POP_A, BUF_POP_B, BUF_NODE, BUF_LINKS, BUF_SCRATCH, BUF_STAGE, NUM_BUFFERS = range(7)
+BUF_POP_A, BUF_POP_B, BUF_NODE, BUF_LINKS, BUF_SCRATCH, BUF_STAGE, BUF_PHI, NUM_BUFFERS = range(8)
 MAX_WALLS = 16
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_UNSUPPORTED", 5: "ERR_NAN",
           6: "ERR_STATE"}
@@ -56,6 +56,7 @@ class LbmConfig(ctypes.Structure):
         ("rounding", ctypes.c_int32),
         ("seed", ctypes.c_uint32),
         ("insulating", ctypes.c_int32),
+        ("curved", ctypes.c_int32),
     ]
 
 
@@ -82,6 +83,7 @@ _SIGS = {
     "lbm_load_state": [_vp, _vp, ctypes.c_int64, _vp],
     "lbm_time": [_vp, _P(ctypes.c_int64)],
     "lbm_electric_field": [_vp, _P(ctypes.c_double), _vp],
+    "lbm_set_wall_distance": [_vp, _P(ctypes.c_float), _vp],
     "lbm_device_status": [_vp, _P(ctypes.c_uint32), _i, _vp],
     "lbm_stress": [_vp, _i, _vp, _vp, _vp, _vp, _vp],
     "lbm_wall_force": [_vp, _i, ctypes.c_uint, _d, _vp, _i, _vp],
@@ -120,7 +122,7 @@ def _check(status, ctx=None):
 def make_config(lattice=9, nx=4, ny=4, nz=1, periodic=(1, 1, 1), dx=1.0, dt=1.0, tau=0.8, rho0=1.0,
                 force_model="e", g=(0.0, 0.0, 0.0), lorentz=0, B=(0.0, 0.0, 0.0), E=(0.0, 0.0, 0.0),
                 sigma_e=0.0, mu=1.0, maxwell=0, les=0, cs=0.1, storage="f64", wall_u=(),
-                face_wall=(1, 1, 1, 1, 1, 1), rounding="nearest", seed=0, insulating=0,
+                face_wall=(1, 1, 1, 1, 1, 1), rounding="nearest", seed=0, insulating=0, curved=0,
                 **_ignored) -> LbmConfig:
     c = LbmConfig()
     c.lattice, c.nx, c.ny, c.nz = int(lattice), int(nx), int(ny), int(nz)
@@ -141,6 +143,7 @@ def make_config(lattice=9, nx=4, ny=4, nz=1, periodic=(1, 1, 1), dx=1.0, dt=1.0,
     c.rounding = ROUND[rounding] if isinstance(rounding, str) else int(rounding)
     c.seed = int(seed) & 0xFFFFFFFF
     c.insulating = int(insulating)
+    c.curved = int(curved)
     return c
 
 
@@ -227,6 +230,16 @@ def lbm_time(ctx):
     t = ctypes.c_int64()
     _check(load().lbm_time(ctx, ctypes.byref(t)), ctx)
     return t.value
+
+
+def lbm_set_wall_distance(ctx, phi, stream):
+    """Signed wall distance of a curved-wall context (canonical node order,
+    float32 host array), or None for halfway bounce-back everywhere."""
+    if phi is None:
+        _check(load().lbm_set_wall_distance(ctx, None, stream), ctx)
+        return
+    a = np.ascontiguousarray(phi, dtype=np.float32)
+    _check(load().lbm_set_wall_distance(ctx, a.ctypes.data_as(_P(ctypes.c_float)), stream), ctx)
 
 
 def lbm_electric_field(ctx, stream):
@@ -369,6 +382,9 @@ class Sim:
 
     def electric_field(self):
         return lbm_electric_field(self.ctx, self.stream)
+
+    def set_wall_distance(self, phi):
+        lbm_set_wall_distance(self.ctx, phi, self.stream)
 
     # diagnostics
     def stress(self, variant):

@@ -123,3 +123,15 @@ def test_insulating_walls_scratch(lib):
     assert ins[lbm.BUF_POP_A] == plain[lbm.BUF_POP_A]
     ins32 = lbm.lbm_buffer_sizes(lbm.make_config(**dict(cfg, storage="f32")), mask)
     assert ins[lbm.BUF_SCRATCH] - ins32[lbm.BUF_SCRATCH] >= 3 * 8 * (threads // 2) - 256
+
+
+def test_curved_walls_buffer(lib):
+    """Curved walls need a float per padded node for the wall distance."""
+    cfg, mask = workloads.poiseuille(nx=100, ny=12)
+    plain = lbm.lbm_buffer_sizes(lbm.make_config(**cfg), mask)
+    cur = lbm.lbm_buffer_sizes(lbm.make_config(**dict(cfg, curved=1)), mask)
+    assert plain[lbm.BUF_PHI] == 0
+    assert cur[lbm.BUF_PHI] >= 128 * 12 * 4 and cur[lbm.BUF_PHI] % 256 == 0
+    c = lbm.make_config(**dict(cfg, curved=2))
+    with pytest.raises(lbm.LbmError, match="curved"):
+        lbm.lbm_buffer_sizes(c, mask)
