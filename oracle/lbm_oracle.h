@@ -72,6 +72,11 @@ typedef struct orc_cfg {
                               field E of step t is -<v> x B with <v> the mean flow
                               velocity over fluid nodes of step t-1 (the first step
                               uses E as given); see orc_step_e / orc_run_e */
+    int stokes;            /* 1: the linear equilibrium rho w (1 + 3 e.u^eq/c^2) (+ Maxwell
+                              term), whose second moment is c^2 rho delta/3 (Stokes
+                              equation, the note after Eq. 11) */
+    double darcy;          /* >= 0: resistance of a porous medium, a += -darcy v at the
+                              flow velocity v (Brinkman equation with stokes = 1) */
 } orc_cfg;
 
 /* lattice tables: e (unit-speed integers, Q*3), w (Q), opposite index (Q) */

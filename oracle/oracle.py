@@ -57,6 +57,8 @@ class OrcCfg(ctypes.Structure):
         ("face_wall", ctypes.c_int * 6),
         ("phi", ctypes.c_void_p),
         ("insulating", ctypes.c_int),
+        ("stokes", ctypes.c_int),
+        ("darcy", ctypes.c_double),
     ]
 
 
@@ -100,7 +102,7 @@ def lib():
 def make_cfg(q=9, nx=4, ny=4, nz=1, periodic=(1, 1, 1), dx=1.0, dt=1.0, tau=0.8, rho0=1.0,
              force_model="e", g=(0.0, 0.0, 0.0), lorentz=0, B=(0.0, 0.0, 0.0), E=(0.0, 0.0, 0.0),
              sigma_e=0.0, mu=1.0, maxwell=0, les=0, cs=0.1, wall_u=(), face_wall=(1, 1, 1, 1, 1, 1),
-             insulating=0, phi=None, **_ignored) -> OrcCfg:
+             insulating=0, phi=None, stokes=0, darcy=0.0, **_ignored) -> OrcCfg:
     """Build an oracle configuration.  ``wall_u`` lists the velocity of walls
     1..n; ``force_model`` is one of 'a'..'e' (Sec. 2)."""
     c = OrcCfg()
@@ -121,6 +123,7 @@ def make_cfg(q=9, nx=4, ny=4, nz=1, periodic=(1, 1, 1), dx=1.0, dt=1.0, tau=0.8,
     for k in range(6):
         c.face_wall[k] = int(face_wall[k])
     c.insulating = int(insulating)
+    c.stokes, c.darcy = int(stokes), float(darcy)
     if phi is not None:
         # signed wall distance per node (float32, the library's precision too)
         c._phi = np.ascontiguousarray(phi, dtype=np.float32)
