@@ -150,7 +150,18 @@ typedef struct lbm_config {
     uint32_t seed;                   /* stream of the stochastic rounding */
     int32_t insulating;              /* 1 (needs lorentz): insulating walls, see below */
     int32_t curved;                  /* 1: walls off the half-grid from a signed distance, see below */
+    int32_t stokes;                  /* 1: linear equilibrium rho w (1 + 3 e.u^eq/c^2), see below */
+    double darcy;                    /* >= 0: porous resistance, a += -darcy v (Brinkman), see below */
 } lbm_config;
+
+/* Stokes and Brinkman flow (the note after Eq. 11).  stokes = 1 replaces the
+ * equilibrium of Eq. (1) by its linear part (plus the Maxwell term), whose
+ * second moment c^2 rho delta/3 carries no rho u u: the recovered equation is
+ * the Stokes equation.  darcy > 0 adds the resistance of a porous medium,
+ * a += -darcy v at the flow velocity v (solved exactly with v = u + dt a/2,
+ * together with the Lorentz force), which with stokes = 1 gives the Brinkman
+ * equation.  Stress variant S1 (the artefact term of the full equilibrium) is
+ * refused with stokes = 1, the adjoint with stokes = 1 or darcy > 0. */
 
 /* Walls off the half-grid (discussion after Eq. 25, end of Sec. 6).  With
  * curved = 1 the context holds a signed wall distance phi per node (buffer

@@ -79,6 +79,8 @@ bool validate(const lbm_config* c, const uint8_t* wid, std::string& err)
     if (c->insulating != 0 && c->insulating != 1) return fail("insulating must be 0 or 1");
     if (c->insulating && !c->lorentz) return fail("insulating walls need the Lorentz force (lorentz = 1)");
     if (c->curved != 0 && c->curved != 1) return fail("curved must be 0 or 1");
+    if (c->stokes != 0 && c->stokes != 1) return fail("stokes must be 0 or 1");
+    if (!(c->darcy >= 0.0) || !std::isfinite(c->darcy)) return fail("darcy must be finite and >= 0");
     if (!wid) return fail("wall_id is NULL");
     const long long N = nodes_of(c);
     for (long long n = 0; n < N; ++n)
@@ -210,6 +212,7 @@ template <typename R> void cast_kp(const KP<double>& s, KP<R>& d)
     for (int a = 0; a < 19; ++a) d.mx[a] = (R)s.mx[a];
     for (int k = 0; k < 6; ++k) d.Lh[k] = (R)s.Lh[k];
     d.les = s.les; d.lesc = (R)s.lesc; d.face_ladd = s.face_ladd;
+    d.stokes = s.stokes; d.darcy_h = (R)s.darcy_h;
     for (int w = 0; w <= MAXW; ++w)
         for (int k = 0; k < 3; ++k) d.LW[w][k] = (R)s.LW[w][k];
     d.c = (R)s.c; d.dt = (R)s.dt; d.svol = (R)s.svol;
@@ -300,6 +303,8 @@ void fill_params(Ctx& x)
     }
     p.les = c->les;
     p.lesc = 18.0 * c->cs * c->cs;
+    p.stokes = c->stokes;
+    p.darcy_h = 0.5 * c->dt * c->darcy;
     p.face_ladd = 0;
     for (int k = 0; k < D; ++k)
         if (!c->periodic[k])
@@ -353,7 +358,7 @@ void choose_tile(Ctx& x)
     // LBM_STEP_KERNEL=tile selects the shared-memory staged step where it fits;
     // the register-tiled step is the default
     const char* sel = getenv("LBM_STEP_KERNEL");
-    const bool want_tile = sel && strcmp(sel, "tile") == 0 && x.cfg.rounding == LBM_ROUND_NEAREST && !x.insulating && !x.cfg.curved;
+    const bool want_tile = sel && strcmp(sel, "tile") == 0 && x.cfg.rounding == LBM_ROUND_NEAREST && !x.insulating && !x.cfg.curved && !x.cfg.stokes && !(x.cfg.darcy > 0.0);
     const bool fits = want_tile && smem_for(R, ns) <= (size_t)x.smem_optin;
     x.tile_R = fits ? R : 0;
     x.tile_stages = fits ? ns : 0;
@@ -481,7 +486,7 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
     Ctx& x = h->c;
     x.cfg = *cfg;
     if (x.cfg.lattice == LBM_D2Q9) x.cfg.periodic[2] = 1;
-    x.ext = (cfg->lorentz || cfg->maxwell || cfg->les) ? 1 : 0;
+    x.ext = (cfg->lorentz || cfg->maxwell || cfg->les || cfg->stokes || cfg->darcy > 0.0) ? 1 : 0;
     x.sr = (cfg->rounding == LBM_ROUND_STOCHASTIC) ? 1 : 0;
     x.insulating = cfg->insulating != 0;
     x.ins_threads = step_threads_of(cfg);
@@ -825,6 +830,10 @@ lbm_status lbm_stress(lbm_ctx* ctx, int variant, void* sigma, void* S, void* rho
     if (!ctx) return LBM_ERR_ARG;
     Ctx& x = ctx->c;
     if (variant < LBM_S1 || variant > LBM_S4) return arg_fail(x, "variant must be 1..4");
+    if (variant == LBM_S1 && x.cfg.stokes) {
+        x.err = "stress variant S1 carries the artefact term of the full equilibrium; not with stokes = 1";
+        return LBM_ERR_UNSUPPORTED;
+    }
     if (variant >= LBM_S3 && (x.t < 1 || !x.prev_valid)) {
         x.err = "half-step stress needs at least one step since the last init/import/load";
         return LBM_ERR_STATE;
@@ -893,8 +902,8 @@ lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* state_prev, const void* ph
 {
     if (!ctx) return LBM_ERR_ARG;
     Ctx& x = ctx->c;
-    if (x.cfg.lorentz || x.cfg.les || x.cfg.curved) {
-        x.err = "the adjoint supports a uniform body force without LES, on halfway walls";
+    if (x.cfg.lorentz || x.cfg.les || x.cfg.curved || x.cfg.stokes || x.cfg.darcy > 0.0) {
+        x.err = "the adjoint supports a uniform body force without LES, on halfway walls, with the equilibrium of Eq. (1)";
         return LBM_ERR_UNSUPPORTED;
     }
     if (!state_prev || !phi_out || !dir || phi_out == phi_next) return arg_fail(x, "bad adjoint buffers");

@@ -250,6 +250,8 @@ template <typename R> struct KP {
     R Lh[6];          // L / c^2: xx yy zz xy xz yz (zero without the Maxwell term)
     int les;
     R lesc;           // 18 Cs^2
+    int stokes;       // linear equilibrium (no rho u u)
+    R darcy_h;        // dt darcy / 2: porous resistance in the implicit v
     int face_ladd;    // some closed face of the box is a moving wall
     R LW[MAXW + 1][3];  // 6 rho0 u_w / c per wall id (Ladd term = w_a E_a . LW)
     // per-launch constants of the node-pair path (uniform body force only):
@@ -319,10 +321,11 @@ __device__ __forceinline__ void macro_from_moments(const Mom<R>& mo, const KP<R>
     m.drho = drho;
     m.u[0] = mo.j[0] * ir; m.u[1] = mo.j[1] * ir; m.u[2] = (D == 3) ? mo.j[2] * ir : R(0);
     m.A[0] = p.AG[0]; m.A[1] = p.AG[1]; m.A[2] = (D == 3) ? p.AG[2] : R(0);
-    if (EXT && p.lorentz) {
-        // v = u + A/2 with A = A_g + (kappa/rho)[(v.B)B - B^2 v] in the D
-        // simulated components: (1 + k B^2) v - k B_p (B_p . v) = w, k = kappa/(2 rho),
-        // w = u + (A_g + A_EB/rho)/2, solved with the Sherman-Morrison formula.
+    if (EXT && (p.lorentz || p.darcy_h != R(0))) {
+        // v = u + A/2 with A = A_g + (kappa/rho)[(v.B)B - B^2 v] - dt darcy v in
+        // the D simulated components: (1 + h + k B^2) v - k B_p (B_p . v) = w,
+        // k = kappa/(2 rho), h = dt darcy/2, w = u + (A_g + A_EB/rho)/2,
+        // solved with the Sherman-Morrison formula.
         R wv[3], Ag[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -332,8 +335,9 @@ __device__ __forceinline__ void macro_from_moments(const Mom<R>& mo, const KP<R>
         }
         const R kk = R(0.5) * p.kappa * ir;
         const R Bw = p.B[0] * wv[0] + p.B[1] * wv[1] + ((D == 3) ? p.B[2] * wv[2] : R(0));
-        const R den = R(1) / (R(1) + kk * p.B2);
-        const R s = kk * Bw / (R(1) + kk * (p.B2 - p.Bp2));
+        const R al = R(1) + p.darcy_h;
+        const R den = R(1) / (al + kk * p.B2);
+        const R s = kk * Bw / (al + kk * (p.B2 - p.Bp2));
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             const R vk = (wv[k] + s * p.B[k]) * den;
@@ -357,7 +361,7 @@ __device__ __forceinline__ void macro_from_moments(const Mom<R>& mo, const KP<R>
             const int i = (c < 3) ? c : (c == 5 ? 1 : 0);
             const int j = (c < 3) ? c : (c == 3 ? 1 : 2);
             if (D == 2 && (i == 2 || j == 2)) continue;
-            R Pc = mo.P[c] - rho * m.weq[i] * m.weq[j] - (p.maxwell ? p.Lh[c] : R(0));
+            R Pc = mo.P[c] - (p.stokes ? R(0) : rho * m.weq[i] * m.weq[j]) - (p.maxwell ? p.Lh[c] : R(0));
             if (i == j) Pc -= drho * third;
             PP += (i == j ? R(1) : R(2)) * Pc * Pc;
         }
@@ -462,7 +466,8 @@ __device__ __forceinline__ void node_relax(R (&d)[Q], const KP<R>& p, const Node
     constexpr int D = LatDim<Q>::D;
     const R om = m.om, om1 = R(1) - om;
     const R rho = m.rho, Crho = m.C * m.rho;
-    const R usq = R(1.5) * (m.weq[0] * m.weq[0] + m.weq[1] * m.weq[1] + ((D == 3) ? m.weq[2] * m.weq[2] : R(0)));
+    const bool sto = EXT && p.stokes;        // linear equilibrium: no u^eq u^eq terms
+    const R usq = sto ? R(0) : R(1.5) * (m.weq[0] * m.weq[0] + m.weq[1] * m.weq[1] + ((D == 3) ? m.weq[2] * m.weq[2] : R(0)));
     const R fa = m.wf[0] * m.A[0] + m.wf[1] * m.A[1] + ((D == 3) ? m.wf[2] * m.A[2] : R(0));
     const R base = om * (m.drho - rho * usq) - R(3) * Crho * fa;   // times w
     const bool mxw = EXT && p.maxwell;
@@ -470,7 +475,7 @@ __device__ __forceinline__ void node_relax(R (&d)[Q], const KP<R>& p, const Node
         constexpr R w0 = R(WD<Q>(0));
         d[0] = om1 * d[0] + w0 * base + (mxw ? om * p.mx[0] : R(0));
     }
-    const R k1 = R(4.5) * om * rho, k2 = R(9) * Crho, kl = R(3) * om * rho, kf = R(3) * Crho;
+    const R k1 = sto ? R(0) : R(4.5) * om * rho, k2 = R(9) * Crho, kl = R(3) * om * rho, kf = R(3) * Crho;
 #pragma unroll
     for (int k = 0; k < LatDim<Q>::NP; ++k) {
         const int a = PAIR<Q>(k), b = OPP<Q>(a);

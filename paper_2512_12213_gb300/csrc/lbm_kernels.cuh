@@ -553,7 +553,7 @@ __device__ __forceinline__ R src_value(const SrcFields& s, const KP<R>& p, int a
     const double W[3] = {s.u[n] / c, s.u[s.N + n] / c, (Q == 19) ? s.u[2 * s.N + n] / c : 0.0};
     const double eu = EX<Q>(a) * W[0] + EY<Q>(a) * W[1] + EZ<Q>(a) * W[2];
     const double ww = W[0] * W[0] + W[1] * W[1] + W[2] * W[2];
-    double fe = rho * WD<Q>(a) * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * ww);
+    double fe = p.stokes ? rho * WD<Q>(a) * (1.0 + 3.0 * eu) : rho * WD<Q>(a) * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * ww);
     if (p.maxwell) fe += (double)p.mx[a];
     if (s.xi) fe *= 1.0 + s.xi[(long long)a * s.N + n];
     return R(fe - WD<Q>(a) * (double)p.rho0);
@@ -816,7 +816,7 @@ k_stress(const typename S::T* __restrict__ cur, const typename S::T* __restrict_
                         if (ee) P2 += R(ee) * d[a];
                     }
                     // cheap form of Sec. 3: sum e e f - (p delta + rho u^eq u^eq + L)
-                    R Pi = P2 - m.rho * m.weq[i] * m.weq[j] - (p.maxwell ? p.Lh[lc] : R(0));
+                    R Pi = P2 - (p.stokes ? R(0) : m.rho * m.weq[i] * m.weq[j]) - (p.maxwell ? p.Lh[lc] : R(0));
                     if (i == j) Pi -= m.drho / R(3);
                     if (variant == 1) {
                         // E_ij = tau dt rho (u^eq a + a u^eq) - tau Theta_ij, in units of c^2
@@ -858,7 +858,7 @@ k_stress(const typename S::T* __restrict__ cur, const typename S::T* __restrict_
                         if (ee) P2 += R(ee) * db[a];
                     }
                     // sum e e (fbar - f^eq(rhobar, ubar)), in units of c^2
-                    R Pi = P2 - rb * ub[i] * ub[j] - (p.maxwell ? p.Lh[lc] : R(0));
+                    R Pi = P2 - (p.stokes ? R(0) : rb * ub[i] * ub[j]) - (p.maxwell ? p.Lh[lc] : R(0));
                     if (i == j) Pi -= drb / R(3);
                     R s = -c2 * Pi;
                     if (variant == 4 && p.model != MODEL_A)

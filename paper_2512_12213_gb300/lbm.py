@@ -57,6 +57,8 @@ class LbmConfig(ctypes.Structure):
         ("seed", ctypes.c_uint32),
         ("insulating", ctypes.c_int32),
         ("curved", ctypes.c_int32),
+        ("stokes", ctypes.c_int32),
+        ("darcy", ctypes.c_double),
     ]
 
 
@@ -123,7 +125,7 @@ def make_config(lattice=9, nx=4, ny=4, nz=1, periodic=(1, 1, 1), dx=1.0, dt=1.0,
                 force_model="e", g=(0.0, 0.0, 0.0), lorentz=0, B=(0.0, 0.0, 0.0), E=(0.0, 0.0, 0.0),
                 sigma_e=0.0, mu=1.0, maxwell=0, les=0, cs=0.1, storage="f64", wall_u=(),
                 face_wall=(1, 1, 1, 1, 1, 1), rounding="nearest", seed=0, insulating=0, curved=0,
-                **_ignored) -> LbmConfig:
+                stokes=0, darcy=0.0, **_ignored) -> LbmConfig:
     c = LbmConfig()
     c.lattice, c.nx, c.ny, c.nz = int(lattice), int(nx), int(ny), int(nz)
     for k in range(3):
@@ -144,6 +146,7 @@ def make_config(lattice=9, nx=4, ny=4, nz=1, periodic=(1, 1, 1), dx=1.0, dt=1.0,
     c.seed = int(seed) & 0xFFFFFFFF
     c.insulating = int(insulating)
     c.curved = int(curved)
+    c.stokes, c.darcy = int(stokes), float(darcy)
     return c
 
 
