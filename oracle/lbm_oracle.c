@@ -143,6 +143,17 @@ static const double* wall_velocity(const orc_cfg* c, int wall)
     return c->wall_u[wall - 1];
 }
 
+/* the configuration at node n: with a local field (induced runs) B is that
+ * node's field */
+static const orc_cfg* node_cfg(const orc_cfg* c, long n, orc_cfg* tmp)
+{
+    if (!c->Bfield) return c;
+    *tmp = *c;
+    const long N = (long)c->nx * c->ny * c->nz;
+    for (int k = 0; k < 3; ++k) tmp->B[k] = c->Bfield[k * N + n];
+    return tmp;
+}
+
 /* Ladd's moving-wall term for a population leaving along a into a wall */
 static double ladd(const orc_cfg* c, const lat_t* L, int a, int wall)
 {
@@ -230,35 +241,12 @@ void orc_init(const orc_cfg* c, const unsigned char* wid, const double* rho,
     }
 }
 
-/* one step with caller work arrays frel (N*Q) and fnew (N*Q); vmean (if not
- * NULL) receives the mean flow velocity v over the fluid nodes */
-static void step_work(const orc_cfg* c, const lat_t* L, const unsigned char* wid,
-                      double* f, double* frel, double* fnew, double* vmean)
+/* propagation of f^rel to x + dt e_a, halfway or interpolated bounce-back at
+ * solids (see orc_step) */
+static void propagate(const orc_cfg* c, const lat_t* L, const unsigned char* wid, const double* frel, double* fnew)
 {
     const long N = nnodes(c);
     const int Q = L->q;
-    double vs[3] = {0.0, 0.0, 0.0};
-    long nf = 0;
-    /* relaxation with the force term at every fluid node, Eq. (2) */
-    for (long n = 0; n < N; ++n) {
-        if (wid[n] != 0) {
-            for (int a = 0; a < Q; ++a) frel[a * N + n] = 0.0;
-            continue;
-        }
-        double fl[19], out[19];
-        for (int a = 0; a < Q; ++a) fl[a] = f[a * N + n];
-        collide_r(c, L, fl, c->g, out);
-        for (int a = 0; a < Q; ++a) frel[a * N + n] = out[a];
-        if (vmean) {
-            macro_t_r m;
-            macro_r(c, L, fl, c->g, &m);
-            for (int k = 0; k < 3; ++k) vs[k] += m.v[k];
-            ++nf;
-        }
-    }
-    if (vmean)
-        for (int k = 0; k < 3; ++k) vmean[k] = nf ? vs[k] / (double)nf : 0.0;
-    /* propagation to x + dt e_a, halfway bounce-back at solids */
     memset(fnew, 0, sizeof(double) * N * Q);
     for (int z = 0; z < c->nz; ++z)
         for (int y = 0; y < c->ny; ++y)
@@ -291,6 +279,37 @@ static void step_work(const orc_cfg* c, const lat_t* L, const unsigned char* wid
                     }
                 }
             }
+}
+
+/* one step with caller work arrays frel (N*Q) and fnew (N*Q); vmean (if not
+ * NULL) receives the mean flow velocity v over the fluid nodes */
+static void step_work(const orc_cfg* c, const lat_t* L, const unsigned char* wid,
+                      double* f, double* frel, double* fnew, double* vmean)
+{
+    const long N = nnodes(c);
+    const int Q = L->q;
+    double vs[3] = {0.0, 0.0, 0.0};
+    long nf = 0;
+    /* relaxation with the force term at every fluid node, Eq. (2) */
+    for (long n = 0; n < N; ++n) {
+        if (wid[n] != 0) {
+            for (int a = 0; a < Q; ++a) frel[a * N + n] = 0.0;
+            continue;
+        }
+        double fl[19], out[19];
+        for (int a = 0; a < Q; ++a) fl[a] = f[a * N + n];
+        collide_r(c, L, fl, c->g, out);
+        for (int a = 0; a < Q; ++a) frel[a * N + n] = out[a];
+        if (vmean) {
+            macro_t_r m;
+            macro_r(c, L, fl, c->g, &m);
+            for (int k = 0; k < 3; ++k) vs[k] += m.v[k];
+            ++nf;
+        }
+    }
+    if (vmean)
+        for (int k = 0; k < 3; ++k) vmean[k] = nf ? vs[k] / (double)nf : 0.0;
+    propagate(c, L, wid, frel, fnew);
     memcpy(f, fnew, sizeof(double) * N * Q);
 }
 
@@ -351,6 +370,143 @@ void orc_run(const orc_cfg* c, const unsigned char* wid, double* f, int nsteps)
     orc_run_e(c, wid, f, nsteps, E);
 }
 
+/* ---- induced field ---- */
+
+typedef struct {
+    int q;
+    int e[7][3];
+    double w[7], theta;
+    int opp[7];
+} mlat_t;
+
+static void get_mlat(int fq, mlat_t* M)
+{
+    static const int e7[7][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+    static const int e5[5][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0}};
+    M->q = (fq == 9) ? 5 : 7;
+    M->theta = (fq == 9) ? 1.0 / 3.0 : 0.25;
+    for (int i = 0; i < M->q; ++i) {
+        for (int k = 0; k < 3; ++k) M->e[i][k] = (fq == 9) ? e5[i][k] : e7[i][k];
+        M->w[i] = (i == 0) ? ((fq == 9) ? 1.0 / 3.0 : 0.25) : ((fq == 9) ? 1.0 / 6.0 : 0.125);
+    }
+    for (int i = 0; i < M->q; ++i)
+        for (int j = 0; j < M->q; ++j)
+            if (M->e[j][0] == -M->e[i][0] && M->e[j][1] == -M->e[i][1] && M->e[j][2] == -M->e[i][2]) M->opp[i] = j;
+}
+
+int orc_mag_q(int q) { return q == 9 ? 5 : 7; }
+
+void orc_mag_init(const orc_cfg* c, const unsigned char* wid, double* g)
+{
+    mlat_t M;
+    get_mlat(c->q, &M);
+    const long N = nnodes(c);
+    for (int k = 0; k < 3; ++k)
+        for (int i = 0; i < M.q; ++i)
+            for (long n = 0; n < N; ++n) g[((long)k * M.q + i) * N + n] = wid[n] ? 0.0 : M.w[i] * c->B[k];
+}
+
+void orc_mag_field(const orc_cfg* c, const unsigned char* wid, const double* g, double* B)
+{
+    mlat_t M;
+    get_mlat(c->q, &M);
+    const long N = nnodes(c);
+    for (int k = 0; k < 3; ++k)
+        for (long n = 0; n < N; ++n) {
+            double s = 0.0;
+            if (!wid[n])
+                for (int i = 0; i < M.q; ++i) s += g[((long)k * M.q + i) * N + n];
+            B[k * N + n] = s;
+        }
+}
+
+/* node one step along the field-lattice velocity e (periodic wrap); -1 with
+ * the wall id when it is solid or outside a closed face */
+static long mlink_dest(const orc_cfg* c, const unsigned char* wid, int x, int y, int z, const int* e)
+{
+    int p[3] = {x + e[0], y + e[1], z + e[2]};
+    const int n[3] = {c->nx, c->ny, c->nz};
+    for (int k = 0; k < 3; ++k) {
+        if (p[k] >= 0 && p[k] < n[k]) continue;
+        if (!c->periodic[k]) return -1;
+        p[k] = (p[k] + n[k]) % n[k];
+    }
+    long d = ((long)p[2] * c->ny + p[1]) * c->nx + p[0];
+    return wid[d] ? -1 : d;
+}
+
+void orc_run_mhd(const orc_cfg* c, const unsigned char* wid, double* f, double* g, int nsteps, double* frel_out)
+{
+    lat_t L;
+    mlat_t M;
+    get_lat(c->q, &L);
+    get_mlat(c->q, &M);
+    const long N = nnodes(c);
+    const int Q = L.q, Qm = M.q;
+    const double cc = c->dx / c->dt;
+    const double taum = 0.5 + c->eta / (M.theta * cc * cc * c->dt);
+    double* frel = (double*)malloc(sizeof(double) * N * Q);
+    double* fnew = (double*)malloc(sizeof(double) * N * Q);
+    double* grel = (double*)malloc(sizeof(double) * 3 * Qm * N);
+    for (int s = 0; s < nsteps; ++s) {
+        memset(grel, 0, sizeof(double) * 3 * Qm * N);
+        for (long n = 0; n < N; ++n) {
+            if (wid[n] != 0) {
+                for (int a = 0; a < Q; ++a) frel[a * N + n] = 0.0;
+                continue;
+            }
+            /* the node's field, and the fluid relaxation with the Maxwell
+             * equilibrium of Eq. (10) at that field */
+            orc_cfg cn = *c;
+            for (int k = 0; k < 3; ++k) {
+                double b = 0.0;
+                for (int i = 0; i < Qm; ++i) b += g[((long)k * Qm + i) * N + n];
+                cn.B[k] = b;
+            }
+            double fl[19], out[19];
+            for (int a = 0; a < Q; ++a) fl[a] = f[a * N + n];
+            collide_r(&cn, &L, fl, c->g, out);
+            for (int a = 0; a < Q; ++a) frel[a * N + n] = out[a];
+            macro_t_r m;
+            macro_r(&cn, &L, fl, c->g, &m);
+            /* the field relaxation: Lambda_jk = v_j B_k - B_j v_k */
+            double Lam[3][3];
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k) Lam[j][k] = m.v[j] * cn.B[k] - cn.B[j] * m.v[k];
+            for (int k = 0; k < 3; ++k)
+                for (int i = 0; i < Qm; ++i) {
+                    double el = 0.0;
+                    for (int j = 0; j < 3; ++j) el += M.e[i][j] * Lam[j][k];
+                    const double geq = M.w[i] * (cn.B[k] + el / (M.theta * cc));
+                    const double gi = g[((long)k * Qm + i) * N + n];
+                    grel[((long)k * Qm + i) * N + n] = gi - (gi - geq) / taum;
+                }
+        }
+        propagate(c, &L, wid, frel, fnew);
+        memcpy(f, fnew, sizeof(double) * N * Q);
+        memset(g, 0, sizeof(double) * 3 * Qm * N);
+        for (int z = 0; z < c->nz; ++z)
+            for (int y = 0; y < c->ny; ++y)
+                for (int x = 0; x < c->nx; ++x) {
+                    const long n = ((long)z * c->ny + y) * c->nx + x;
+                    if (wid[n] != 0) continue;
+                    for (int i = 0; i < Qm; ++i) {
+                        const long d = mlink_dest(c, wid, x, y, z, M.e[i]);
+                        for (int k = 0; k < 3; ++k) {
+                            const double gr = grel[((long)k * Qm + i) * N + n];
+                            if (d >= 0) g[((long)k * Qm + i) * N + d] = gr;
+                            else g[((long)k * Qm + M.opp[i]) * N + n] =
+                                     c->mag_conducting ? gr : -gr + 2.0 * M.w[i] * c->B[k];
+                        }
+                    }
+                }
+        if (frel_out && s == nsteps - 1) memcpy(frel_out, frel, sizeof(double) * N * Q);
+    }
+    free(frel);
+    free(fnew);
+    free(grel);
+}
+
 void orc_wall_force(const orc_cfg* c, const unsigned char* wid, const double* frel,
                     const double* fnext, int wall, int flags, double* out)
 {
@@ -364,6 +520,8 @@ void orc_wall_force(const orc_cfg* c, const unsigned char* wid, const double* fr
             for (int x = 0; x < c->nx; ++x) {
                 long n = ((long)z * c->ny + y) * c->nx + x;
                 if (wid[n] != 0) continue;
+                orc_cfg tmp;
+                const orc_cfg* cn = node_cfg(c, n, &tmp);
                 for (int a = 0; a < L.q; ++a) {
                     int lw = 0;
                     if (link_dest(c, &L, wid, x, y, z, a, &lw) >= 0) continue;
@@ -377,7 +535,7 @@ void orc_wall_force(const orc_cfg* c, const unsigned char* wid, const double* fr
                         double d = ek * (fo + fi);
                         if (flags & ORC_MOVING_CORR) d += uw[k] * (fi - fo);
                         if ((flags & ORC_MAXWELL_REMOVE) && c->maxwell)
-                            d -= 2.0 * ek * maxwell_delta(c, &L, a);
+                            d -= 2.0 * ek * maxwell_delta(cn, &L, a);
                         out[k] += s * d;
                     }
                 }
@@ -394,6 +552,8 @@ long orc_count_links(const orc_cfg* c, const unsigned char* wid, int wall)
             for (int x = 0; x < c->nx; ++x) {
                 long n = ((long)z * c->ny + y) * c->nx + x;
                 if (wid[n] != 0) continue;
+                orc_cfg tmp;
+                const orc_cfg* cn = node_cfg(c, n, &tmp);
                 for (int a = 0; a < L.q; ++a) {
                     int lw = 0;
                     if (link_dest(c, &L, wid, x, y, z, a, &lw) >= 0) continue;
@@ -413,10 +573,11 @@ static void theta_of(const orc_cfg* c, const macro_t_r* m, double T[3][3])
                           : m->C * c->dt * m->rho * (m->uF[i] * m->a[j] + m->uF[j] * m->a[i]);
 }
 
-void orc_stress(const orc_cfg* c, const unsigned char* wid, const double* f,
+void orc_stress(const orc_cfg* c0, const unsigned char* wid, const double* f,
                 const double* frel, const double* fnext, int variant,
                 double* sigma, double* S, double* rho_out, double* v_out)
 {
+    const orc_cfg* c = c0;
     lat_t L;
     get_lat(c->q, &L);
     const long N = nnodes(c);
@@ -425,6 +586,8 @@ void orc_stress(const orc_cfg* c, const unsigned char* wid, const double* f,
     const int ci[6] = {0, 1, 2, 0, 0, 1}, cj[6] = {0, 1, 2, 1, 2, 2};
     const int ci2[3] = {0, 1, 0}, cj2[3] = {0, 1, 1};
     for (long n = 0; n < N; ++n) {
+        orc_cfg ncfg;
+        const orc_cfg* c = node_cfg(c0, n, &ncfg);     /* the node's field in induced runs */
         double sig[3][3] = {{0}}, rr = 0, vv[3] = {0, 0, 0}, nu;
         if (wid[n] == 0) {
             double fl[19];

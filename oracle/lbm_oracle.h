@@ -77,6 +77,15 @@ typedef struct orc_cfg {
                               equation, the note after Eq. 11) */
     double darcy;          /* >= 0: resistance of a porous medium, a += -darcy v at the
                               flow velocity v (Brinkman equation with stokes = 1) */
+    int induced;           /* 1: the field is induced, B(x, t) carried by a vector lattice
+                              Boltzmann model (see orc_run_mhd); the fluid sees it through
+                              the Maxwell equilibrium of Eq. (10) at the local B (needs
+                              maxwell = 1, lorentz = 0); B above is the external field */
+    double eta;            /* magnetic diffusivity of the induced field */
+    int mag_conducting;    /* walls for the field: 0 insulating (B = B_ext at the wall),
+                              1 perfectly conducting (no normal gradient) */
+    const double* Bfield;  /* NULL, or the local field B[3][N] that orc_stress and
+                              orc_wall_force use instead of B (induced runs) */
 } orc_cfg;
 
 /* lattice tables: e (unit-speed integers, Q*3), w (Q), opposite index (Q) */
@@ -122,6 +131,24 @@ void orc_run(const orc_cfg* c, const unsigned char* wall_id, double* f, int n);
  * (-<v> x B of the last step, Eq. 36); frel as in orc_step (last step) */
 void orc_step_e(const orc_cfg* c, const unsigned char* wall_id, double* f, double* frel, double* E);
 void orc_run_e(const orc_cfg* c, const unsigned char* wall_id, double* f, int n, double* E);
+
+/* Induced field (Sec. 4 cites Dellar's vector lattice Boltzmann model for
+ * the induction equation dB/dt + div(v B - B v) = eta lap B): components
+ * g[k][i][N] (k = x, y, z) on D2Q5 (weights 1/3, 1/6; theta = 1/3) or D3Q7
+ * (1/4, 1/8; theta = 1/4) with the axis velocities of the fluid lattice.
+ * Per step, from the fluid state f(t) and g(t): B = sum_i g_i at each fluid
+ * node; the fluid relaxes with the Maxwell equilibrium at that B; the field
+ * relaxes to g^eq_ik = W_i [B_k + e_ij (v_j B_k - B_j v_k)/(theta c)] with the
+ * node's flow velocity v and tau_m = 1/2 + eta/(theta c^2 dt); both
+ * propagate.  A field link into a wall returns anti-bounced,
+ * -g'_i + 2 W_i B_ext (insulating) or bounced, g'_i (conducting).
+ * orc_mag_init sets g = W_i B_ext at fluid nodes (0 at solids);
+ * orc_mag_field gives B[3][N] = sum_i g (0 at solids). */
+int orc_mag_q(int q);
+void orc_mag_init(const orc_cfg* c, const unsigned char* wall_id, double* g);
+void orc_mag_field(const orc_cfg* c, const unsigned char* wall_id, const double* g, double* B);
+/* n coupled steps; frel (N*Q, may be NULL) receives f^rel of the last step */
+void orc_run_mhd(const orc_cfg* c, const unsigned char* wall_id, double* f, double* g, int n, double* frel);
 
 /* momentum-exchange force of Eq. (25) on wall `wall` (or every wall if
  * wall < 0) during the step t -> t+dt, from frel = f^rel(t) and

@@ -59,6 +59,10 @@ class OrcCfg(ctypes.Structure):
         ("insulating", ctypes.c_int),
         ("stokes", ctypes.c_int),
         ("darcy", ctypes.c_double),
+        ("induced", ctypes.c_int),
+        ("eta", ctypes.c_double),
+        ("mag_conducting", ctypes.c_int),
+        ("Bfield", ctypes.c_void_p),
     ]
 
 
@@ -85,6 +89,10 @@ def lib():
             "orc_run": (None, [cp, ub, dp, ctypes.c_int]),
             "orc_step_e": (None, [cp, ub, dp, dp, dp]),
             "orc_run_e": (None, [cp, ub, dp, ctypes.c_int, dp]),
+            "orc_mag_q": (ctypes.c_int, [ctypes.c_int]),
+            "orc_mag_init": (None, [cp, ub, dp]),
+            "orc_mag_field": (None, [cp, ub, dp, dp]),
+            "orc_run_mhd": (None, [cp, ub, dp, dp, ctypes.c_int, dp]),
             "orc_wall_force": (None, [cp, ub, dp, dp, ctypes.c_int, ctypes.c_int, dp]),
             "orc_count_links": (ctypes.c_long, [cp, ub, ctypes.c_int]),
             "orc_stress": (None, [cp, ub, dp, dp, dp, ctypes.c_int, dp, dp, dp, dp]),
@@ -102,7 +110,8 @@ def lib():
 def make_cfg(q=9, nx=4, ny=4, nz=1, periodic=(1, 1, 1), dx=1.0, dt=1.0, tau=0.8, rho0=1.0,
              force_model="e", g=(0.0, 0.0, 0.0), lorentz=0, B=(0.0, 0.0, 0.0), E=(0.0, 0.0, 0.0),
              sigma_e=0.0, mu=1.0, maxwell=0, les=0, cs=0.1, wall_u=(), face_wall=(1, 1, 1, 1, 1, 1),
-             insulating=0, phi=None, stokes=0, darcy=0.0, **_ignored) -> OrcCfg:
+             insulating=0, phi=None, stokes=0, darcy=0.0, induced=0, eta=0.0, mag_conducting=0,
+             **_ignored) -> OrcCfg:
     """Build an oracle configuration.  ``wall_u`` lists the velocity of walls
     1..n; ``force_model`` is one of 'a'..'e' (Sec. 2)."""
     c = OrcCfg()
@@ -124,6 +133,7 @@ def make_cfg(q=9, nx=4, ny=4, nz=1, periodic=(1, 1, 1), dx=1.0, dt=1.0, tau=0.8,
         c.face_wall[k] = int(face_wall[k])
     c.insulating = int(insulating)
     c.stokes, c.darcy = int(stokes), float(darcy)
+    c.induced, c.eta, c.mag_conducting = int(induced), float(eta), int(mag_conducting)
     if phi is not None:
         # signed wall distance per node (float32, the library's precision too)
         c._phi = np.ascontiguousarray(phi, dtype=np.float32)
@@ -216,6 +226,39 @@ def run_e(cfg, wall_id, f, n, E=None):
     e = np.array(list(cfg.E) if E is None else E, dtype=np.float64)
     lib().orc_run_e(ctypes.byref(cfg), _ub(_u8(wall_id)), _dp(fn), int(n), _dp(e))
     return fn, e
+
+
+def mag_init(cfg, wall_id):
+    """Field distributions at rest in the external field, g[3][Qm][N]."""
+    qm = lib().orc_mag_q(cfg.q)
+    g = np.zeros((3, qm, cfg.nz, cfg.ny, cfg.nx))
+    lib().orc_mag_init(ctypes.byref(cfg), _ub(_u8(wall_id)), _dp(g))
+    return g
+
+
+def mag_field(cfg, wall_id, g):
+    B = np.zeros((3, cfg.nz, cfg.ny, cfg.nx))
+    lib().orc_mag_field(ctypes.byref(cfg), _ub(_u8(wall_id)), _dp(_f64(g)), _dp(B))
+    return B
+
+
+def run_mhd(cfg, wall_id, f, g, n):
+    """n coupled fluid / induced-field steps; returns (f, g, f^rel of the last step)."""
+    fn, gn = _f64(f).copy(), _f64(g).copy()
+    fr = np.zeros_like(fn)
+    lib().orc_run_mhd(ctypes.byref(cfg), _ub(_u8(wall_id)), _dp(fn), _dp(gn), int(n), _dp(fr))
+    return fn, gn, fr
+
+
+def with_field(cfg, B):
+    """A copy of cfg whose stress and wall force use the local field B[3][N]."""
+    c = OrcCfg.from_buffer_copy(cfg)
+    for k in ("_phi",):
+        if hasattr(cfg, k):
+            setattr(c, k, getattr(cfg, k))
+    c._B = np.ascontiguousarray(B, dtype=np.float64)
+    c.Bfield = c._B.ctypes.data
+    return c
 
 
 def step_e(cfg, wall_id, f, E=None):

@@ -513,3 +513,77 @@ def test_brinkman_channel_second_order_and_balance(orc):
     # ratio climbs towards 4 (2.8, then 3.3)
     assert errs[-1] < 3e-3
     assert 2.5 < errs[0] / errs[1] < 4.6 and 3.0 < errs[1] / errs[2] < 4.6 and errs[1] / errs[2] > errs[0] / errs[1]
+
+
+def _induced_hartmann(orc, H, conducting, tau=0.8, Ha=4.0, B0=0.05):
+    """Channel between walls at y = +-H in an external field (0, B0, 0) with
+    the field induced (Dellar's vector lattice Boltzmann model, Sec. 4) and
+    coupled through the Maxwell equilibrium of Eq. (10).  Steady equations:
+    nu u'' + (B0/mu rho) b' + g = 0 and eta b'' + B0 u' = 0, u(+-H) = 0 and
+    b(+-H) = 0 (insulating) or b'(+-H) = 0 (conducting, zero mean b)."""
+    ny, nx = 2 * H, 2
+    nu = (tau - 0.5) / 3
+    K = nu * Ha ** 2 / H ** 2                   # B0^2 / (mu rho eta), mu = rho = 1
+    eta = B0 ** 2 / K
+    m = np.sqrt(K / nu)
+    t = np.tanh(m * H) / (m * H)
+    gain = 1 / (K * t) if not conducting else 1 / K
+    g = 0.01 / (gain * (1 - 1 / np.cosh(m * H)))
+    cfg = orc.make_cfg(q=9, nx=nx, ny=ny, nz=1, periodic=(1, 0, 1), tau=tau, force_model="e", g=(g, 0, 0),
+                       B=(0, B0, 0), maxwell=1, mu=1.0, induced=1, eta=eta, mag_conducting=int(conducting),
+                       wall_u=((0, 0, 0),))
+    mask = np.zeros((1, ny, nx), np.uint8)
+    f = orc.init(cfg, mask, np.ones((1, ny, nx)), np.zeros((3, 1, ny, nx)))
+    f, gm, _ = orc.run_mhd(cfg, mask, f, orc.mag_init(cfg, mask), 80 * H * H)
+    B = orc.mag_field(cfg, mask, gm)
+    _, _, _, v = orc.stress(orc.with_field(cfg, B), mask, f, None, None, 2)
+    y = np.arange(ny) - H + 0.5
+    u = g * gain * (1 - np.cosh(m * y) / np.cosh(m * H))
+    # integral of u from -H to y
+    intu = g * gain * ((y + H) - (np.sinh(m * y) + np.sinh(m * H)) / (m * np.cosh(m * H)))
+    if conducting:
+        b = -(B0 / eta) * intu
+        b -= b.mean()
+    else:
+        b = (B0 / eta) * (u.mean() * (y + H) - intu)
+    eu = np.abs(v[0, 0, :, 0] - u).max() / u.max()
+    eb = np.abs(B[0, 0, :, 0] - b).max() / np.abs(b).max()
+    return eu, eb, B
+
+
+@pytest.mark.parametrize("conducting", [False, True])
+def test_induced_field_hartmann_second_order(orc, conducting):
+    eu, eb = [], []
+    for H in (8, 16, 32):
+        a, b, B = _induced_hartmann(orc, H, conducting)
+        eu.append(a)
+        eb.append(b)
+        # the normal component is uniform (div B = 0 across the channel)
+        assert np.abs(B[1] - 0.05).max() < 1e-13
+    assert eu[-1] < 2e-3 and eb[-1] < 6e-3
+    for e in (eu, eb):
+        assert 2.8 < e[0] / e[1] < 4.6 and 3.2 < e[1] / e[2] < 4.6
+
+
+def test_induced_field_total_conserved_by_conducting_walls(orc):
+    """Relaxation keeps sum_i g_ik = B_k at each node and bounce-back keeps
+    the population at its node: the total field is conserved every step with
+    conducting walls (not with insulating ones, which exchange with B_ext)."""
+    nx, ny, nz = 12, 9, 7
+    mask = inputs.random_solids(nx, ny, nz, 0.1, n_walls=1, seed=23)
+    for conducting in (1, 0):
+        cfg = orc.make_cfg(q=19, nx=nx, ny=ny, nz=nz, periodic=(1, 0, 1), tau=0.7, force_model="d",
+                           g=(2e-3, 0, 1e-3), B=(0.02, 0.05, -0.03), maxwell=1, mu=1.0, induced=1, eta=0.05,
+                           mag_conducting=conducting, wall_u=((0.01, 0, 0), (0, 0, 0)), face_wall=(1, 1, 2, 2, 1, 1))
+        rho, u = inputs.smooth_fields(nx, ny, nz, dims=3, seed=4)
+        f = orc.init(cfg, mask, rho, u * 0.5, inputs.noise(19, nx, ny, nz, 1e-2, seed=5))
+        g = orc.mag_init(cfg, mask)
+        B0 = orc.mag_field(cfg, mask, g).sum(axis=(1, 2, 3))
+        drift = 0.0
+        for _ in range(5):
+            f, g, _ = orc.run_mhd(cfg, mask, f, g, 1)
+            drift = max(drift, np.abs(orc.mag_field(cfg, mask, g).sum(axis=(1, 2, 3)) - B0).max())
+        if conducting:
+            assert drift < 1e-14 * nx * ny * nz
+        else:
+            assert drift > 1e-6
