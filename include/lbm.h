@@ -121,7 +121,9 @@ enum {
     LBM_BUF_SCRATCH = 4,      /* FP64 reduction partials (required) */
     LBM_BUF_STAGE = 5,        /* canonical staging for host import/export (optional) */
     LBM_BUF_PHI = 6,          /* signed wall distance per node, float (required if curved) */
-    LBM_NUM_BUFFERS = 7
+    LBM_BUF_MAG_A = 7,        /* induced-field distributions, ping (required if induced) */
+    LBM_BUF_MAG_B = 8,        /* induced-field distributions, pong (required if induced) */
+    LBM_NUM_BUFFERS = 9
 };
 
 #define LBM_MAX_WALLS 16
@@ -152,7 +154,26 @@ typedef struct lbm_config {
     int32_t curved;                  /* 1: walls off the half-grid from a signed distance, see below */
     int32_t stokes;                  /* 1: linear equilibrium rho w (1 + 3 e.u^eq/c^2), see below */
     double darcy;                    /* >= 0: porous resistance, a += -darcy v (Brinkman), see below */
+    int32_t induced;                 /* 1: induced magnetic field (needs maxwell = 1), see below */
+    double eta;                      /* magnetic diffusivity of the induced field, > 0 */
+    int32_t mag_conducting;          /* induced field at walls: 0 insulating, 1 perfectly conducting */
 } lbm_config;
+
+/* Induced magnetic field (Sec. 4 cites Dellar's vector lattice Boltzmann
+ * model for the induction equation dB/dt + div(v B - B v) = eta lap B).
+ * With induced = 1 the field B(x, t) is carried by distributions g_ik
+ * (k = x, y, z) on the axis velocities of the fluid lattice (D2Q5 weights
+ * 1/3, 1/6 with theta = 1/3; D3Q7 1/4, 1/8 with theta = 1/4), relaxed with
+ * tau_m = 1/2 + eta/(theta c^2 dt) to g^eq_ik = W_i [B_k + e_ij (v_j B_k -
+ * B_j v_k)/(theta c)] with the node's flow velocity v, and propagated; a
+ * field link into a wall or a closed face returns as -g'_i + 2 W_i B (B the
+ * configured external field: insulating walls) or g'_i (conducting walls).
+ * The fluid relaxes with the Maxwell term of Eq. (10) at the local field
+ * (maxwell = 1 is required; lorentz, les, curved and insulating must be 0);
+ * B above is the external field.  Both fields step from the same time
+ * level.  Create / init / import / load set the field distributions to rest
+ * in the external field, W_i B; lbm_step_from, the adjoint and the half-step
+ * stress variants S3 / S4 are refused.  lbm_export_field reads B(x, T). */
 
 /* Stokes and Brinkman flow (the note after Eq. 11).  stokes = 1 replaces the
  * equilibrium of Eq. (1) by its linear part (plus the Maxwell term), whose
@@ -268,6 +289,11 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, int64_t t, void* stream
  * was created with (else LBM_ERR_ARG); NULL restores +-1/2 (halfway).  Takes
  * effect for the next step and every later call; synchronises the stream. */
 lbm_status lbm_set_wall_distance(lbm_ctx* ctx, const float* phi_host, void* stream);
+
+/* The induced field B(x, T) of an induced-field context: B[3][N] doubles,
+ * canonical node order (zero at solid nodes), device or host memory
+ * (on_host != 0: synchronises; needs the STAGE buffer). */
+lbm_status lbm_export_field(lbm_ctx* ctx, double* B, int on_host, void* stream);
 
 /* Current time T. */
 lbm_status lbm_time(const lbm_ctx* ctx, int64_t* t);

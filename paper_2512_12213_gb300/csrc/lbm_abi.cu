@@ -81,6 +81,14 @@ bool validate(const lbm_config* c, const uint8_t* wid, std::string& err)
     if (c->curved != 0 && c->curved != 1) return fail("curved must be 0 or 1");
     if (c->stokes != 0 && c->stokes != 1) return fail("stokes must be 0 or 1");
     if (!(c->darcy >= 0.0) || !std::isfinite(c->darcy)) return fail("darcy must be finite and >= 0");
+    if (c->induced != 0 && c->induced != 1) return fail("induced must be 0 or 1");
+    if (c->induced) {
+        if (!c->maxwell) return fail("the induced field acts through the Maxwell equilibrium (maxwell = 1)");
+        if (c->lorentz || c->les || c->curved || c->insulating)
+            return fail("the induced field needs lorentz = les = curved = insulating = 0");
+        if (!(c->eta > 0.0) || !std::isfinite(c->eta)) return fail("eta must be finite and > 0");
+        if (c->mag_conducting != 0 && c->mag_conducting != 1) return fail("mag_conducting must be 0 or 1");
+    }
     if (!wid) return fail("wall_id is NULL");
     const long long N = nodes_of(c);
     for (long long n = 0; n < N; ++n)
@@ -199,6 +207,11 @@ void sizes_of(const lbm_config* c, long long n_links, size_t s[LBM_NUM_BUFFERS])
         s[LBM_BUF_SCRATCH] = round256((SCRATCH_INS_ROWS + 3 * (size_t)step_threads_of(c)) * sizeof(double));
     s[LBM_BUF_STAGE] = round256((size_t)(c->lattice + 4) * N * sizeof(double));
     s[LBM_BUF_PHI] = c->curved ? round256((size_t)sq * sizeof(float)) : 0;
+    // induced field: 3 components x (5 or 7) directions per padded node, compute precision
+    const size_t mag = c->induced ? round256((size_t)3 * (c->lattice == 9 ? 5 : 7) * sq *
+                                             (c->storage == LBM_STORE_F64 ? 8 : 4))
+                                  : 0;
+    s[LBM_BUF_MAG_A] = s[LBM_BUF_MAG_B] = mag;
 }
 
 template <typename R> void cast_kp(const KP<double>& s, KP<R>& d)
@@ -213,6 +226,9 @@ template <typename R> void cast_kp(const KP<double>& s, KP<R>& d)
     for (int k = 0; k < 6; ++k) d.Lh[k] = (R)s.Lh[k];
     d.les = s.les; d.lesc = (R)s.lesc; d.face_ladd = s.face_ladd;
     d.stokes = s.stokes; d.darcy_h = (R)s.darcy_h;
+    d.induced = s.induced; d.mag_cond = s.mag_cond; d.mxk = (R)s.mxk; d.om_m = (R)s.om_m;
+    for (int k = 0; k < 3; ++k) d.Bext[k] = (R)s.Bext[k];
+    d.mag = nullptr;
     for (int w = 0; w <= MAXW; ++w)
         for (int k = 0; k < 3; ++k) d.LW[w][k] = (R)s.LW[w][k];
     d.c = (R)s.c; d.dt = (R)s.dt; d.svol = (R)s.svol;
@@ -305,6 +321,15 @@ void fill_params(Ctx& x)
     p.lesc = 18.0 * c->cs * c->cs;
     p.stokes = c->stokes;
     p.darcy_h = 0.5 * c->dt * c->darcy;
+    p.induced = c->induced;
+    if (c->induced) {
+        // D2Q5 theta = 1/3, D3Q7 theta = 1/4: tau_m = 1/2 + eta / (theta c^2 dt)
+        const double theta = (c->lattice == 9) ? 1.0 / 3.0 : 0.25;
+        p.mag_cond = c->mag_conducting;
+        p.mxk = 9.0 / (2.0 * cc * cc * c->mu);
+        p.om_m = 1.0 / (0.5 + c->eta / (theta * cc * cc * c->dt));
+        for (int k = 0; k < 3; ++k) p.Bext[k] = c->B[k];
+    }
     p.face_ladd = 0;
     for (int k = 0; k < D; ++k)
         if (!c->periodic[k])
@@ -331,6 +356,7 @@ void fill_params(Ctx& x)
     q.kappa *= s;
     for (int k = 0; k < 3; ++k) q.AEB[k] *= s;
     for (int a = 0; a < 19; ++a) q.mx[a] *= s;
+    q.mxk *= s;
     for (int k = 0; k < 6; ++k) q.Lh[k] *= s;
     for (int w = 0; w <= MAXW; ++w)
         for (int k = 0; k < 3; ++k) q.LW[w][k] *= s;
@@ -486,7 +512,7 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
     Ctx& x = h->c;
     x.cfg = *cfg;
     if (x.cfg.lattice == LBM_D2Q9) x.cfg.periodic[2] = 1;
-    x.ext = (cfg->lorentz || cfg->maxwell || cfg->les || cfg->stokes || cfg->darcy > 0.0) ? 1 : 0;
+    x.ext = (cfg->lorentz || cfg->maxwell || cfg->les || cfg->stokes || cfg->darcy > 0.0 || cfg->induced) ? 1 : 0;
     x.sr = (cfg->rounding == LBM_ROUND_STOCHASTIC) ? 1 : 0;
     x.insulating = cfg->insulating != 0;
     x.ins_threads = step_threads_of(cfg);
@@ -527,7 +553,9 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
     size_t need[LBM_NUM_BUFFERS];
     sizes_of(&x.cfg, x.n_links, need);
     for (int b = 0; b < LBM_NUM_BUFFERS; ++b) {
-        const bool optional = (b == LBM_BUF_STAGE) || ((b == LBM_BUF_LINKS || b == LBM_BUF_PHI) && need[b] == 0);
+        const bool optional = (b == LBM_BUF_STAGE) || ((b == LBM_BUF_LINKS || b == LBM_BUF_PHI || b == LBM_BUF_MAG_A ||
+                                                         b == LBM_BUF_MAG_B) &&
+                                                        need[b] == 0);
         if (!buffers[b]) {
             if (optional) continue;
             g_cfg_err = "required buffer " + std::to_string(b) + " is NULL";
@@ -549,6 +577,8 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
     x.pop[0] = buffers[LBM_BUF_POP_A];
     x.pop[1] = buffers[LBM_BUF_POP_B];
     x.cur = 0;
+    x.mag[0] = x.cfg.induced ? buffers[LBM_BUF_MAG_A] : nullptr;
+    x.mag[1] = x.cfg.induced ? buffers[LBM_BUF_MAG_B] : nullptr;
     x.cls = (uint8_t*)buffers[LBM_BUF_NODE];
     x.links = (Link*)buffers[LBM_BUF_LINKS];
     x.scratch = (double*)buffers[LBM_BUF_SCRATCH];
@@ -578,6 +608,7 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
         e = cudaMemcpyAsync(x.links, links.data(), links.size() * sizeof(Link), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = launch_zero(x.scratch, (long long)SCRATCH_DOUBLES, st);
     if (e == cudaSuccess && x.insulating) e = ins_reset(x, st);
+    if (e == cudaSuccess && x.cfg.induced) e = x.ops->mag_init(x, st);
     std::vector<float> phi0;
     if (e == cudaSuccess && x.cfg.curved) {
         phi0 = padded_distance(x, nullptr);
@@ -657,6 +688,7 @@ lbm_status lbm_init_equilibrium(lbm_ctx* ctx, const double* rho, const double* u
     }
     CK(x.ops->init_fields(x, dr, du, dxi, x.pop[x.cur], st), "init kernel");
     if (x.insulating) CK(ins_reset(x, st), "insulating-wall field");
+    if (x.cfg.induced) CK(x.ops->mag_init(x, st), "induced-field reset");
     if (on_host) CK(cudaStreamSynchronize(st), "synchronize");
     x.t = 0;
     x.prev_valid = false;
@@ -679,6 +711,7 @@ lbm_status lbm_import_f(lbm_ctx* ctx, const void* src, int dtype, int on_host, v
     }
     CK(x.ops->import_f(x, dsrc, dtype, x.pop[x.cur], st), "import kernel");
     if (x.insulating) CK(ins_reset(x, st), "insulating-wall field");
+    if (x.cfg.induced) CK(x.ops->mag_init(x, st), "induced-field reset");
     if (on_host) CK(cudaStreamSynchronize(st), "synchronize");
     x.t = 0;
     x.prev_valid = false;
@@ -714,7 +747,11 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps, void* stream)
     GUARD(x);
     cudaStream_t st = (cudaStream_t)stream;
     for (int s = 0; s < nsteps; ++s) {
-        CK(x.ops->step(x, x.pop[x.cur], x.pop[1 - x.cur], step_seed(x, x.t), st), "step kernel");
+        if (x.cfg.induced)
+            CK(x.ops->mhd_step(x, x.pop[x.cur], x.pop[1 - x.cur], x.mag[x.cur], x.mag[1 - x.cur], step_seed(x, x.t), st),
+               "coupled step kernel");
+        else
+            CK(x.ops->step(x, x.pop[x.cur], x.pop[1 - x.cur], step_seed(x, x.t), st), "step kernel");
         if (x.insulating) CK(ins_update(x, st), "insulating-wall field");
         x.cur = 1 - x.cur;
         x.t += 1;
@@ -730,8 +767,9 @@ lbm_status lbm_step_from(lbm_ctx* ctx, const void* src, void* dst, int64_t t, vo
     if (!src || !dst || src == dst) return arg_fail(x, "src and dst must be distinct non-NULL buffers");
     if (((uintptr_t)src) % 256 || ((uintptr_t)dst) % 256) return arg_fail(x, "buffers must be 256-byte aligned");
     if (t < 0) return arg_fail(x, "t must be >= 0");
-    if (x.insulating) {
-        x.err = "lbm_step_from: with insulating walls the field is state a population checkpoint does not hold";
+    if (x.insulating || x.cfg.induced) {
+        x.err = "lbm_step_from: with insulating walls or an induced field the field is state a population checkpoint "
+                "does not hold";
         return LBM_ERR_UNSUPPORTED;
     }
     GUARD(x);
@@ -757,6 +795,7 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, int64_t t, void* stream
     GUARD(x);
     CK(cudaMemcpyAsync(x.pop[x.cur], src, pop_bytes(x), cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "load");
     if (x.insulating) CK(ins_reset(x, (cudaStream_t)stream), "insulating-wall field");
+    if (x.cfg.induced) CK(x.ops->mag_init(x, (cudaStream_t)stream), "induced-field reset");
     x.t = t;
     x.prev_valid = false;
     return LBM_OK;
@@ -825,6 +864,28 @@ lbm_status lbm_electric_field(lbm_ctx* ctx, double* E, void* stream)
     return LBM_OK;
 }
 
+lbm_status lbm_export_field(lbm_ctx* ctx, double* B, int on_host, void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (!B) return arg_fail(x, "B is NULL");
+    if (!x.cfg.induced) return arg_fail(x, "lbm_export_field needs a context created with induced = 1");
+    GUARD(x);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = 3 * (size_t)nodes(x) * sizeof(double);
+    double* dB = B;
+    if (on_host) {
+        if (!x.stage || x.stage_bytes < bytes) return arg_fail(x, "host output needs the STAGE buffer");
+        dB = (double*)x.stage;
+    }
+    CK(x.ops->mag_field(x, dB, st), "field kernel");
+    if (on_host) {
+        CK(cudaMemcpyAsync(B, x.stage, bytes, cudaMemcpyDeviceToHost, st), "copy B");
+        CK(cudaStreamSynchronize(st), "synchronize");
+    }
+    return LBM_OK;
+}
+
 lbm_status lbm_stress(lbm_ctx* ctx, int variant, void* sigma, void* S, void* rho, void* v, void* stream)
 {
     if (!ctx) return LBM_ERR_ARG;
@@ -832,6 +893,10 @@ lbm_status lbm_stress(lbm_ctx* ctx, int variant, void* sigma, void* S, void* rho
     if (variant < LBM_S1 || variant > LBM_S4) return arg_fail(x, "variant must be 1..4");
     if (variant == LBM_S1 && x.cfg.stokes) {
         x.err = "stress variant S1 carries the artefact term of the full equilibrium; not with stokes = 1";
+        return LBM_ERR_UNSUPPORTED;
+    }
+    if (variant >= LBM_S3 && x.cfg.induced) {
+        x.err = "the half-step stress variants S3 / S4 are not defined with an induced field";
         return LBM_ERR_UNSUPPORTED;
     }
     if (variant >= LBM_S3 && (x.t < 1 || !x.prev_valid)) {
@@ -902,7 +967,7 @@ lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* state_prev, const void* ph
 {
     if (!ctx) return LBM_ERR_ARG;
     Ctx& x = ctx->c;
-    if (x.cfg.lorentz || x.cfg.les || x.cfg.curved || x.cfg.stokes || x.cfg.darcy > 0.0) {
+    if (x.cfg.lorentz || x.cfg.les || x.cfg.curved || x.cfg.stokes || x.cfg.darcy > 0.0 || x.cfg.induced) {
         x.err = "the adjoint supports a uniform body force without LES, on halfway walls, with the equilibrium of Eq. (1)";
         return LBM_ERR_UNSUPPORTED;
     }

@@ -252,6 +252,14 @@ template <typename R> struct KP {
     R lesc;           // 18 Cs^2
     int stokes;       // linear equilibrium (no rho u u)
     R darcy_h;        // dt darcy / 2: porous resistance in the implicit v
+    // induced field: the Maxwell term at the node's field, mxk w_a m_a(B) with
+    // mxk = 9/(2 c^2 mu) (storage units where the step runs in them); the
+    // field lattice's 1/tau_m, wall rule and external field; the current
+    // field distributions (physical units, compute precision), set per launch
+    int induced, mag_cond;
+    R mxk, om_m;
+    R Bext[3];
+    const R* mag;     // set by the launcher of each kernel that reads the field
     int face_ladd;    // some closed face of the box is a moving wall
     R LW[MAXW + 1][3];  // 6 rho0 u_w / c per wall id (Ladd term = w_a E_a . LW)
     // per-launch constants of the node-pair path (uniform body force only):
@@ -267,8 +275,21 @@ template <typename R> struct KP {
     R c, dt, svol;    // c, dt, dx^D / dt
 };
 
+// Maxwell term of Eq. (10) for direction a at the field B, in units with
+// k = 9 / (2 c^2 mu): k w_a (B^2 |E_a|^2 / 2 - (E_a.B)^2 [- B^2/6 in 3-D])
+template <int Q, typename R>
+__device__ __forceinline__ R maxwell_at(R k, const R (&B)[3], int a)
+{
+    const R B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const R eb = R(EX<Q>(a)) * B[0] + R(EY<Q>(a)) * B[1] + R(EZ<Q>(a)) * B[2];
+    R t = R(0.5) * B2 * R(SPEED2<Q>(a)) - eb * eb;
+    if (Q == 19) t -= B2 / R(6);
+    return k * R(WD<Q>(a)) * t;
+}
+
 // ---------------------------------------------------- per-node quantities
 template <typename R> struct NodeM {
+    R Bl[3];              // the node's field (induced field only)
     R rho, drho;
     R u[3], A[3], v[3];   // in units of c (A: velocity increment per step)
     R weq[3], wf[3];      // u^eq / c and u^F / c (wf = 0 for model [a])
@@ -460,7 +481,7 @@ __device__ __forceinline__ void relax_pair(int a, R& da, R& db, const Coef<R>& c
 //        + 9 w C rho (E_a.W^F)(E_a.A)   (+ om Maxwell term)
 // and the odd part Pa = om 3 w rho t + 3 w C rho (E_a.A), the coefficients
 // taken once per speed class (Eqs. 1-3).
-template <typename R, int Q, bool EXT>
+template <typename R, int Q, bool EXT, bool MAGF = false>
 __device__ __forceinline__ void node_relax(R (&d)[Q], const KP<R>& p, const NodeM<R>& m)
 {
     constexpr int D = LatDim<Q>::D;
@@ -471,9 +492,15 @@ __device__ __forceinline__ void node_relax(R (&d)[Q], const KP<R>& p, const Node
     const R fa = m.wf[0] * m.A[0] + m.wf[1] * m.A[1] + ((D == 3) ? m.wf[2] * m.A[2] : R(0));
     const R base = om * (m.drho - rho * usq) - R(3) * Crho * fa;   // times w
     const bool mxw = EXT && p.maxwell;
+    // Maxwell term of Eq. (10): the configured table, or (MAGF) at the node's
+    // induced field
+    auto mx_of = [&](int a) -> R {
+        if constexpr (MAGF) return maxwell_at<Q, R>(p.mxk, m.Bl, a);
+        else return p.mx[a];
+    };
     {
         constexpr R w0 = R(WD<Q>(0));
-        d[0] = om1 * d[0] + w0 * base + (mxw ? om * p.mx[0] : R(0));
+        d[0] = om1 * d[0] + w0 * base + (mxw ? om * mx_of(0) : R(0));
     }
     const R k1 = sto ? R(0) : R(4.5) * om * rho, k2 = R(9) * Crho, kl = R(3) * om * rho, kf = R(3) * Crho;
 #pragma unroll
@@ -485,7 +512,7 @@ __device__ __forceinline__ void node_relax(R (&d)[Q], const KP<R>& p, const Node
         const R ea = R(ex) * m.A[0] + R(ey) * m.A[1] + ((D == 3) ? R(ez) * m.A[2] : R(0));
         const R ef = R(ex) * m.wf[0] + R(ey) * m.wf[1] + ((D == 3) ? R(ez) * m.wf[2] : R(0));
         R ps = w * (base + k1 * t * t + k2 * ef * ea);
-        if (mxw) ps += om * p.mx[a];
+        if (mxw) ps += om * mx_of(a);
         const R pa = w * (kl * t + kf * ea);
         const R da = d[a], db = d[b];
         d[a] = om1 * da + (ps + pa);
@@ -698,6 +725,60 @@ __device__ __forceinline__ void gather_node(const typename S::T* __restrict__ P,
         } else {
             d[b] = bounced<Q, S, RAW>(P, cls, g, p, x, y, z, own, b, wall);
         }
+    }
+}
+
+// ----------------------------------------------------- induced field
+// Field distributions on the axis velocities of the fluid lattice: the
+// first QM fluid directions (rest, +-x, +-y [, +-z]) with weights W0, W1.
+template <int Q> struct MagLat {
+    static constexpr int QM = (Q == 9) ? 5 : 7;
+    static constexpr double W0 = (Q == 9) ? 1.0 / 3.0 : 0.25;
+    static constexpr double W1 = (Q == 9) ? 1.0 / 6.0 : 0.125;
+    static constexpr double TH = (Q == 9) ? 1.0 / 3.0 : 0.25;       // sum W e e = TH I
+};
+
+// the canonical field distributions g(x, T) at node (x, y, z) (padded index
+// own) from the stored post-collision ones G: G_i(x - e_i) through a fluid
+// link, else -G_opp(i)(x) + 2 W_i B_ext (insulating) or G_opp(i)(x)
+// (conducting)
+template <int Q, typename R>
+__device__ __forceinline__ void mag_gather(const R* __restrict__ G, const uint8_t* __restrict__ cls, const Geo& g,
+                                           const KP<R>& p, int x, int y, int z, long long own,
+                                           R (&gm)[3][MagLat<Q>::QM])
+{
+    constexpr int QM = MagLat<Q>::QM;
+#pragma unroll
+    for (int i = 0; i < QM; ++i) {
+        const R W = R(i == 0 ? MagLat<Q>::W0 : MagLat<Q>::W1);
+        long long src;
+        int wall;
+        const bool fluid = (i == 0) || pull_source(g, cls, x, y, z, EX<Q>(i), EY<Q>(i), EZ<Q>(i), src, wall);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (i == 0) gm[k][0] = G[(long long)(k * QM) * g.sq + own];
+            else if (fluid) gm[k][i] = G[(long long)(k * QM + i) * g.sq + src];
+            else {
+                const R v = G[(long long)(k * QM + OPP<Q>(i)) * g.sq + own];
+                gm[k][i] = p.mag_cond ? v : R(2) * W * p.Bext[k] - v;
+            }
+        }
+    }
+}
+
+// the node's field B(x, T) = sum_i g_i(x, T)
+template <int Q, typename R>
+__device__ __forceinline__ void mag_field_at(const R* __restrict__ G, const uint8_t* __restrict__ cls, const Geo& g,
+                                             const KP<R>& p, int x, int y, int z, long long own, R (&B)[3])
+{
+    R gm[3][MagLat<Q>::QM];
+    mag_gather<Q, R>(G, cls, g, p, x, y, z, own, gm);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        R s = R(0);
+#pragma unroll
+        for (int i = 0; i < MagLat<Q>::QM; ++i) s += gm[k][i];
+        B[k] = s;
     }
 }
 

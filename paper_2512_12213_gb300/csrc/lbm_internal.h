@@ -79,6 +79,12 @@ struct Dispatch {
     cudaError_t (*balance)(const Ctx&, const void* P, double* partials, int* nblocks, cudaStream_t);
     cudaError_t (*stress)(const Ctx&, const void* cur, const void* prev, int variant, void* sig, void* S,
                           void* rho, void* v, cudaStream_t);
+    // induced field: the coupled step, both field buffers at rest in the
+    // external field, B(x, T) in canonical order
+    cudaError_t (*mhd_step)(const Ctx&, const void* src, void* dst, const void* G, void* Gn, uint32_t seed,
+                            cudaStream_t);
+    cudaError_t (*mag_init)(const Ctx&, cudaStream_t);
+    cudaError_t (*mag_field)(const Ctx&, double* B, cudaStream_t);
     cudaError_t (*adjoint)(const Ctx&, const void* Pprev, const void* phin, void* phio, int wall,
                            const double* dir, double seedw, double* partials, cudaStream_t);
 };
@@ -109,7 +115,8 @@ struct Ctx {
     size_t elem;             // bytes per stored population
     size_t relem;            // bytes per compute value
     void* pop[2];
-    int cur;                 // index of the buffer holding f^rel(T-1)
+    int cur;                 // index of the buffer holding f^rel(T-1) (and, induced, G(T-1))
+    void* mag[2];            // induced field: post-collision field distributions, null otherwise
     uint8_t* cls;
     Link* links;
     long long wall_begin[LBM_MAX_WALLS + 2];   // link ranges per wall id (sorted)

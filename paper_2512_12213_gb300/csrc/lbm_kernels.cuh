@@ -712,10 +712,20 @@ k_links(const typename S::T* __restrict__ P, const uint8_t* __restrict__ cls, co
         for (int b = 1; b < Q; ++b)
             if (OPP<Q>(b) == a) fi = (double)bounced<Q, S, false>(P, cls, g, p, xn, yn, zn, L.node, b, L.wall) + w * rho0;
         double mxa = 0.0;
-        if ((flags & 2u) && p.maxwell)
+        if ((flags & 2u) && p.maxwell) {
+            if (p.induced) {
+                // the field of the collision that produced f^rel(x_f, T-1)
+                typename S::R B[3];
+                mag_field_at<Q>(p.mag, cls, g, p, xn, yn, zn, (long long)L.node, B);
 #pragma unroll
-            for (int b = 1; b < Q; ++b)
-                if (b == a) mxa = (double)p.mx[b];
+                for (int b = 1; b < Q; ++b)
+                    if (b == a) mxa = (double)maxwell_at<Q>(p.mxk, B, b);
+            } else {
+#pragma unroll
+                for (int b = 1; b < Q; ++b)
+                    if (b == a) mxa = (double)p.mx[b];
+            }
+        }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const double ek = c * e[k];
@@ -799,6 +809,21 @@ k_stress(const typename S::T* __restrict__ cur, const typename S::T* __restrict_
             // component index -> (i, j)
             constexpr int ci3[6] = {0, 1, 2, 0, 0, 1}, cj3[6] = {0, 1, 2, 1, 2, 2};
             constexpr int ci2[3] = {0, 1, 0}, cj2[3] = {0, 1, 1};
+            // L / c^2 of the Maxwell term: configured, or at the node's induced field B(x, T)
+            R Lh[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) Lh[k] = p.Lh[k];
+            if (EXT && p.induced) {
+                R B[3];
+                mag_field_at<Q>(p.mag, cls, g, p, x, y, z, own, B);
+                const R kl = R(2) / R(9) * p.mxk, h = R(0.5) * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+                Lh[0] = kl * (h - B[0] * B[0]);
+                Lh[1] = kl * (h - B[1] * B[1]);
+                Lh[2] = kl * (h - B[2] * B[2]);
+                Lh[3] = -kl * B[0] * B[1];
+                Lh[4] = -kl * B[0] * B[2];
+                Lh[5] = -kl * B[1] * B[2];
+            }
             if (variant <= 2) {
                 gather_node<Q, S>(cur, cls, g, p, x, y, z, d);
                 node_macro<R, Q, EXT>(d, p, m);
@@ -816,7 +841,7 @@ k_stress(const typename S::T* __restrict__ cur, const typename S::T* __restrict_
                         if (ee) P2 += R(ee) * d[a];
                     }
                     // cheap form of Sec. 3: sum e e f - (p delta + rho u^eq u^eq + L)
-                    R Pi = P2 - (p.stokes ? R(0) : m.rho * m.weq[i] * m.weq[j]) - (p.maxwell ? p.Lh[lc] : R(0));
+                    R Pi = P2 - (p.stokes ? R(0) : m.rho * m.weq[i] * m.weq[j]) - (p.maxwell ? Lh[lc] : R(0));
                     if (i == j) Pi -= m.drho / R(3);
                     if (variant == 1) {
                         // E_ij = tau dt rho (u^eq a + a u^eq) - tau Theta_ij, in units of c^2
@@ -858,7 +883,7 @@ k_stress(const typename S::T* __restrict__ cur, const typename S::T* __restrict_
                         if (ee) P2 += R(ee) * db[a];
                     }
                     // sum e e (fbar - f^eq(rhobar, ubar)), in units of c^2
-                    R Pi = P2 - (p.stokes ? R(0) : rb * ub[i] * ub[j]) - (p.maxwell ? p.Lh[lc] : R(0));
+                    R Pi = P2 - (p.stokes ? R(0) : rb * ub[i] * ub[j]) - (p.maxwell ? Lh[lc] : R(0));
                     if (i == j) Pi -= drb / R(3);
                     R s = -c2 * Pi;
                     if (variant == 4 && p.model != MODEL_A)
@@ -885,6 +910,110 @@ k_stress(const typename S::T* __restrict__ cur, const typename S::T* __restrict_
     }
 }
 
+// ---------------------------------------------------------- induced field
+// One coupled step per node (one thread per padded node): the field
+// distributions g(x, T) pulled from the stored post-collision ones, the
+// node's field B = sum g, the fluid populations f(x, T) (gather_node) and
+// their moments; the field relaxes toward W_i [B + e_i . (v B - B v)/theta]
+// with the node's flow velocity v, the fluid with the Maxwell term of
+// Eq. (10) at B.  Both write their post-collision values for the next pull.
+template <int Q, class S, bool SR>
+__global__ void __launch_bounds__(NODE_THREADS)
+k_mhd_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
+           const typename S::R* __restrict__ G, typename S::R* __restrict__ Gn, const uint8_t* __restrict__ cls,
+           const Geo g, const KP<typename S::R> p, uint32_t seed)
+{
+    using R = typename S::R;
+    constexpr int QM = MagLat<Q>::QM;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= g.sq) return;
+    const int x = (int)(n % g.nxp);
+    const long long row = n / g.nxp;
+    const int y = (int)(row % g.ny), z = (int)(row / g.ny);
+    const uint8_t c = cls[n];
+    if (x >= g.nx || nc_solid(c) || c == NC_PAD) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + n] = S::from_raw(R(0));
+#pragma unroll
+        for (int j = 0; j < 3 * QM; ++j) Gn[(long long)j * g.sq + n] = R(0);
+        return;
+    }
+    R gm[3][QM];
+    mag_gather<Q>(G, cls, g, p, x, y, z, n, gm);
+    NodeM<R> m;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        R b = R(0);
+#pragma unroll
+        for (int i = 0; i < QM; ++i) b += gm[k][i];
+        m.Bl[k] = b;
+    }
+    R d[Q];
+    gather_node<Q, S, true>(src, cls, g, p, x, y, z, d);
+    node_macro<R, Q, true>(d, p, m);
+    // field: e_i is +-1 along one axis, so e_i . (v B_k - B v_k) = s (v_ax B_k - B_ax v_k)
+    const R om = p.om_m, ith = R(1.0 / MagLat<Q>::TH);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int i = 0; i < QM; ++i) {
+            const int ax = (EX<Q>(i) != 0) ? 0 : ((EY<Q>(i) != 0) ? 1 : 2);
+            const int sg = EX<Q>(i) + EY<Q>(i) + EZ<Q>(i);
+            const R W = R(i == 0 ? MagLat<Q>::W0 : MagLat<Q>::W1);
+            const R el = (i == 0) ? R(0) : R(sg) * (m.v[ax] * m.Bl[k] - m.Bl[ax] * m.v[k]);
+            const R geq = W * (m.Bl[k] + ith * el);
+            Gn[(long long)(k * QM + i) * g.sq + n] = gm[k][i] + om * (geq - gm[k][i]);
+        }
+    node_relax<R, Q, true, true>(d, p, m);
+    if constexpr (SR) {
+        NodeRng rng((uint32_t)n, seed);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + n] = S::from_raw_sr(d[a], rng.bits(a));
+    } else {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + n] = S::from_raw(d[a]);
+    }
+}
+
+// field distributions at rest in the external field, W_i B, in both buffers
+template <int Q, typename R>
+__global__ void __launch_bounds__(NODE_THREADS)
+k_mag_init(R* __restrict__ G0, R* __restrict__ G1, const uint8_t* __restrict__ cls, const Geo g, const KP<R> p)
+{
+    constexpr int QM = MagLat<Q>::QM;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= g.sq) return;
+    const uint8_t c = cls[n];
+    const bool fluid = (int)(n % g.nxp) < g.nx && !nc_solid(c) && c != NC_PAD;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int i = 0; i < QM; ++i) {
+            const R v = fluid ? R(i == 0 ? MagLat<Q>::W0 : MagLat<Q>::W1) * p.Bext[k] : R(0);
+            G0[(long long)(k * QM + i) * g.sq + n] = v;
+            G1[(long long)(k * QM + i) * g.sq + n] = v;
+        }
+}
+
+// B(x, T) in canonical order, zero at solid nodes
+template <int Q, typename R>
+__global__ void __launch_bounds__(NODE_THREADS)
+k_mag_field(const R* __restrict__ G, const uint8_t* __restrict__ cls, const Geo g, const KP<R> p,
+            double* __restrict__ Bout)
+{
+    const long long N = (long long)g.nx * g.ny * g.nz;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int x = (int)(n % g.nx);
+    const long long r = n / g.nx;
+    const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+    const long long own = r * g.nxp + x;
+    R B[3] = {R(0), R(0), R(0)};
+    if (!nc_solid(cls[own])) mag_field_at<Q>(G, cls, g, p, x, y, z, own, B);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Bout[(long long)k * N + n] = (double)B[k];
+}
+
 // ================================================================ launchers
 inline int grid_for(long long n, int threads, long long cap)
 {
@@ -904,6 +1033,20 @@ template <class S> inline const KP<typename S::R>& kp_step_of(const Ctx& c)
 {
     if constexpr (sizeof(typename S::R) == 8) return c.kpd;
     else return c.kps;
+}
+
+// a copy of the parameters that reads the field distributions G
+template <typename R> inline KP<R> with_mag(const KP<R>& p, const void* G)
+{
+    KP<R> q = p;
+    q.mag = static_cast<const R*>(G);
+    return q;
+}
+// the wall force reads the field of the step that produced the stored state:
+// B(T-1), pulled from the other field buffer
+template <class S> inline KP<typename S::R> kp_links_of(const Ctx& c)
+{
+    return with_mag(kp_of<S>(c), c.cfg.induced ? c.mag[1 - c.cur] : nullptr);
 }
 
 template <int Q, class S, bool EXT, bool SR>
@@ -1004,8 +1147,8 @@ cudaError_t launch_links(const Ctx& c, const void* P, long long begin, long long
     using T = typename S::T;
     const int blocks = grid_for(end - begin, RED_THREADS, MAX_PARTIAL_ROWS);
     *nblocks = blocks;
-    k_links<Q, S><<<blocks, RED_THREADS, 0, st>>>((const T*)P, c.cls, c.links, begin, end, c.geo, kp_of<S>(c), flags,
-                                                  partials);
+    k_links<Q, S><<<blocks, RED_THREADS, 0, st>>>((const T*)P, c.cls, c.links, begin, end, c.geo, kp_links_of<S>(c),
+                                                  flags, partials);
     return cudaGetLastError();
 }
 
@@ -1033,11 +1176,50 @@ cudaError_t launch_stress(const Ctx& c, const void* cur, const void* prev, int v
     const long long N = (long long)c.geo.nx * c.geo.ny * c.geo.nz;
     const int blocks = grid_for(N, NODE_THREADS, 65535ll * 16);
     if (c.ext)
-        k_stress<Q, S, true><<<blocks, NODE_THREADS, 0, st>>>((const T*)cur, (const T*)prev, c.cls, c.geo, kp_of<S>(c),
-                                                              variant, (R*)sig, (R*)Sv, (R*)rho, (R*)v);
+        k_stress<Q, S, true><<<blocks, NODE_THREADS, 0, st>>>((const T*)cur, (const T*)prev, c.cls, c.geo,
+                                                              with_mag(kp_of<S>(c), c.mag[c.cur]), variant, (R*)sig,
+                                                              (R*)Sv, (R*)rho, (R*)v);
     else
         k_stress<Q, S, false><<<blocks, NODE_THREADS, 0, st>>>((const T*)cur, (const T*)prev, c.cls, c.geo, kp_of<S>(c),
                                                                variant, (R*)sig, (R*)Sv, (R*)rho, (R*)v);
+    return cudaGetLastError();
+}
+
+template <int Q, class S>
+cudaError_t launch_mhd_step(const Ctx& c, const void* src, void* dst, const void* G, void* Gn, uint32_t seed,
+                            cudaStream_t st)
+{
+    using T = typename S::T;
+    using R = typename S::R;
+    const int blocks = grid_for(c.geo.sq, NODE_THREADS, 1ll << 31);
+    if constexpr (sizeof(T) == 2) {
+        if (c.sr) {
+            k_mhd_step<Q, S, true><<<blocks, NODE_THREADS, 0, st>>>((const T*)src, (T*)dst, (const R*)G, (R*)Gn, c.cls,
+                                                                    c.geo, kp_step_of<S>(c), seed);
+            return cudaGetLastError();
+        }
+    }
+    k_mhd_step<Q, S, false><<<blocks, NODE_THREADS, 0, st>>>((const T*)src, (T*)dst, (const R*)G, (R*)Gn, c.cls,
+                                                                 c.geo, kp_step_of<S>(c), seed);
+    return cudaGetLastError();
+}
+
+template <int Q, class S>
+cudaError_t launch_mag_init(const Ctx& c, cudaStream_t st)
+{
+    using R = typename S::R;
+    const int blocks = grid_for(c.geo.sq, NODE_THREADS, 1ll << 31);
+    k_mag_init<Q, R><<<blocks, NODE_THREADS, 0, st>>>((R*)c.mag[0], (R*)c.mag[1], c.cls, c.geo, kp_of<S>(c));
+    return cudaGetLastError();
+}
+
+template <int Q, class S>
+cudaError_t launch_mag_field(const Ctx& c, double* B, cudaStream_t st)
+{
+    using R = typename S::R;
+    const long long N = (long long)c.geo.nx * c.geo.ny * c.geo.nz;
+    const int blocks = grid_for(N, NODE_THREADS, 1ll << 31);
+    k_mag_field<Q, R><<<blocks, NODE_THREADS, 0, st>>>((const R*)c.mag[c.cur], c.cls, c.geo, kp_of<S>(c), B);
     return cudaGetLastError();
 }
 
@@ -1074,6 +1256,16 @@ template <class S> Dispatch make_dispatch()
                   cudaStream_t st) {
         return c.cfg.lattice == 9 ? launch_stress<9, S>(c, cu, pr, var, sg, Sv, rh, v, st)
                                   : launch_stress<19, S>(c, cu, pr, var, sg, Sv, rh, v, st);
+    };
+    d.mhd_step = [](const Ctx& c, const void* s, void* t, const void* G, void* Gn, uint32_t seed, cudaStream_t st) {
+        return c.cfg.lattice == 9 ? launch_mhd_step<9, S>(c, s, t, G, Gn, seed, st)
+                                  : launch_mhd_step<19, S>(c, s, t, G, Gn, seed, st);
+    };
+    d.mag_init = [](const Ctx& c, cudaStream_t st) {
+        return c.cfg.lattice == 9 ? launch_mag_init<9, S>(c, st) : launch_mag_init<19, S>(c, st);
+    };
+    d.mag_field = [](const Ctx& c, double* B, cudaStream_t st) {
+        return c.cfg.lattice == 9 ? launch_mag_field<9, S>(c, B, st) : launch_mag_field<19, S>(c, B, st);
     };
     d.adjoint = [](const Ctx& c, const void* Pp, const void* pn, void* po, int w, const double* dir, double sw,
                    double* pa, cudaStream_t st) {

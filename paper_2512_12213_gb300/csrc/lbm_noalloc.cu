@@ -62,7 +62,7 @@ cudaError_t launch_links_rows(const lbm::Ctx& c, const void* P, long long begin,
 {
     using T = typename S::T;
     lbm::k_links<Q, S><<<rows, lbm::RED_THREADS, 0, st>>>((const T*)P, c.cls, c.links, begin, end, c.geo,
-                                                         lbm::kp_of<S>(c), flags, partials);
+                                                         lbm::kp_links_of<S>(c), flags, partials);
     return cudaGetLastError();
 }
 

@@ -25,7 +25,8 @@ ROUND = {"nearest": 0, "stochastic": 1}
 S1, S2, S3, S4 = 1, 2, 3, 4
 MOVING_CORR, MAXWELL_REMOVE, ACCUMULATE = 1, 2, 4
 OUT_DEVICE, OUT_HOST, OUT_HOST_ASYNC = 0, 1, 2
-BUF_POP_A, BUF_POP_B, BUF_NODE, BUF_LINKS, BUF_SCRATCH, BUF_STAGE, BUF_PHI, NUM_BUFFERS = range(8)
+(BUF_POP_A, BUF_POP_B, BUF_NODE, BUF_LINKS, BUF_SCRATCH, BUF_STAGE, BUF_PHI, BUF_MAG_A, BUF_MAG_B,
+ NUM_BUFFERS) = range(10)
 MAX_WALLS = 16
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_UNSUPPORTED", 5: "ERR_NAN",
           6: "ERR_STATE"}
@@ -59,6 +60,9 @@ class LbmConfig(ctypes.Structure):
         ("curved", ctypes.c_int32),
         ("stokes", ctypes.c_int32),
         ("darcy", ctypes.c_double),
+        ("induced", ctypes.c_int32),
+        ("eta", ctypes.c_double),
+        ("mag_conducting", ctypes.c_int32),
     ]
 
 
@@ -86,6 +90,7 @@ _SIGS = {
     "lbm_time": [_vp, _P(ctypes.c_int64)],
     "lbm_electric_field": [_vp, _P(ctypes.c_double), _vp],
     "lbm_set_wall_distance": [_vp, _P(ctypes.c_float), _vp],
+    "lbm_export_field": [_vp, _vp, _i, _vp],
     "lbm_device_status": [_vp, _P(ctypes.c_uint32), _i, _vp],
     "lbm_stress": [_vp, _i, _vp, _vp, _vp, _vp, _vp],
     "lbm_wall_force": [_vp, _i, ctypes.c_uint, _d, _vp, _i, _vp],
@@ -125,7 +130,7 @@ def make_config(lattice=9, nx=4, ny=4, nz=1, periodic=(1, 1, 1), dx=1.0, dt=1.0,
                 force_model="e", g=(0.0, 0.0, 0.0), lorentz=0, B=(0.0, 0.0, 0.0), E=(0.0, 0.0, 0.0),
                 sigma_e=0.0, mu=1.0, maxwell=0, les=0, cs=0.1, storage="f64", wall_u=(),
                 face_wall=(1, 1, 1, 1, 1, 1), rounding="nearest", seed=0, insulating=0, curved=0,
-                stokes=0, darcy=0.0, **_ignored) -> LbmConfig:
+                stokes=0, darcy=0.0, induced=0, eta=0.0, mag_conducting=0, **_ignored) -> LbmConfig:
     c = LbmConfig()
     c.lattice, c.nx, c.ny, c.nz = int(lattice), int(nx), int(ny), int(nz)
     for k in range(3):
@@ -147,6 +152,7 @@ def make_config(lattice=9, nx=4, ny=4, nz=1, periodic=(1, 1, 1), dx=1.0, dt=1.0,
     c.insulating = int(insulating)
     c.curved = int(curved)
     c.stokes, c.darcy = int(stokes), float(darcy)
+    c.induced, c.eta, c.mag_conducting = int(induced), float(eta), int(mag_conducting)
     return c
 
 
@@ -250,6 +256,11 @@ def lbm_electric_field(ctx, stream):
     E = (ctypes.c_double * 3)()
     _check(load().lbm_electric_field(ctx, E, stream), ctx)
     return np.array(list(E))
+
+
+def lbm_export_field(ctx, B, on_host, stream):
+    """The induced field B(x, T) into B[3][N] doubles (device tensor or host array)."""
+    _check(load().lbm_export_field(ctx, _ptr(B), int(on_host), stream), ctx)
 
 
 def lbm_device_status(ctx, clear, stream):
@@ -388,6 +399,12 @@ class Sim:
 
     def set_wall_distance(self, phi):
         lbm_set_wall_distance(self.ctx, phi, self.stream)
+
+    def export_field(self):
+        """The induced field B(x, T), (3, nz, ny, nx) float64 on the device."""
+        B = self.torch.empty((3,) + self.shape, dtype=self.torch.float64, device=self.device)
+        lbm_export_field(self.ctx, B, 0, self.stream)
+        return B
 
     # diagnostics
     def stress(self, variant):

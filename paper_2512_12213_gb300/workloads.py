@@ -54,6 +54,26 @@ def hartmann_insulating(nx=256, ny=128, tau=0.8, Ha=10.0, B0=0.05, model="e", st
     return cfg, inputs.empty_mask(nx, ny)
 
 
+def hartmann_induced(nx=2, ny=128, tau=0.8, Ha=4.0, B0=0.05, conducting=0, model="e", storage="f64"):
+    """D2Q9 channel of half-width H = ny/2 in an external field (0, B0, 0)
+    with the induced field carried by the D2Q5 field lattice and coupled
+    through the Maxwell equilibrium; insulating (conducting = 0) or
+    perfectly conducting walls.  With K = B0^2/(mu rho eta) = nu Ha^2/H^2
+    the steady flow is u = (g/K') (1 - cosh(m y)/cosh(m H)), m = Ha/H,
+    K' = K tanh(mH)/(mH) (insulating) or K (conducting); the body force makes
+    the centre-line velocity 0.01."""
+    H = ny / 2
+    nu = (tau - 0.5) / 3
+    K = nu * Ha ** 2 / H ** 2
+    m = Ha / H
+    gain = 1 / K if conducting else 1 / (K * math.tanh(m * H) / (m * H))
+    g = 0.01 / (gain * (1 - 1 / math.cosh(m * H)))
+    cfg = dict(lattice=9, nx=nx, ny=ny, nz=1, periodic=(1, 0, 1), tau=tau, force_model=model, g=(g, 0.0, 0.0),
+               B=(0.0, B0, 0.0), maxwell=1, mu=1.0, induced=1, eta=B0 ** 2 / K, mag_conducting=int(conducting),
+               storage=storage, wall_u=((0, 0, 0),), face_wall=(1, 1, 1, 1, 1, 1))
+    return cfg, inputs.empty_mask(nx, ny)
+
+
 # body forces for the sphere case, from a Stokes estimate with a finite-Re
 # drag factor (the measured Reynolds number is reported by the benchmark)
 SPHERE_RE = {20: dict(tau=0.68, g=4.5e-7), 100: dict(tau=0.536, g=1.9e-7)}

@@ -135,3 +135,28 @@ def test_curved_walls_buffer(lib):
     c = lbm.make_config(**dict(cfg, curved=2))
     with pytest.raises(lbm.LbmError, match="curved"):
         lbm.lbm_buffer_sizes(c, mask)
+
+
+def test_induced_field_buffers(lib):
+    """The induced field needs two buffers of 3 x (5 or 7) distributions per
+    padded node in compute precision (FP64, else FP32), and is refused
+    without the Maxwell equilibrium, with the low-Rm Lorentz force, LES,
+    curved or insulating walls, and for eta <= 0."""
+    cfg, mask = workloads.hartmann_induced(nx=100, ny=12)
+    plain = lbm.lbm_buffer_sizes(lbm.make_config(**dict(cfg, induced=0)), mask)
+    ind = lbm.lbm_buffer_sizes(lbm.make_config(**cfg), mask)
+    assert plain[lbm.BUF_MAG_A] == plain[lbm.BUF_MAG_B] == 0
+    assert ind[lbm.BUF_MAG_A] == ind[lbm.BUF_MAG_B] >= 3 * 5 * 128 * 12 * 8
+    assert ind[lbm.BUF_MAG_A] % 256 == 0
+    f32 = lbm.lbm_buffer_sizes(lbm.make_config(**dict(cfg, storage="f16s")), mask)
+    assert f32[lbm.BUF_MAG_A] == (3 * 5 * 128 * 12 * 4 + 255) // 256 * 256
+    c3 = dict(lattice=19, nx=10, ny=6, nz=5, periodic=(1, 1, 1), maxwell=1, induced=1, eta=0.1, wall_u=((0, 0, 0),))
+    m3 = np.zeros((5, 6, 10), np.uint8)
+    s3 = lbm.lbm_buffer_sizes(lbm.make_config(**c3), m3)
+    assert s3[lbm.BUF_MAG_A] == (3 * 7 * 64 * 6 * 5 * 8 + 255) // 256 * 256
+    for bad, msg in ((dict(maxwell=0), "maxwell"), (dict(lorentz=1, sigma_e=0.1), "lorentz"),
+                     (dict(les=1), "les"), (dict(curved=1), "curved"), (dict(eta=0.0), "eta"),
+                     (dict(eta=float("nan")), "eta"), (dict(induced=2), "induced"),
+                     (dict(mag_conducting=3), "mag_conducting")):
+        with pytest.raises(lbm.LbmError, match=msg):
+            lbm.lbm_buffer_sizes(lbm.make_config(**dict(cfg, **bad)), mask)
