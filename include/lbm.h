@@ -165,7 +165,8 @@ typedef struct lbm_config {
  * (k = x, y, z) on the axis velocities of the fluid lattice (D2Q5 weights
  * 1/3, 1/6 with theta = 1/3; D3Q7 1/4, 1/8 with theta = 1/4), relaxed with
  * tau_m = 1/2 + eta/(theta c^2 dt) to g^eq_ik = W_i [B_k + e_ij (v_j B_k -
- * B_j v_k)/(theta c)] with the node's flow velocity v, and propagated; a
+ * B_j v_k)/(theta c)] (e_i the integer lattice vectors) with the node's flow
+ * velocity v, and propagated; a
  * field link into a wall or a closed face returns as -g'_i + 2 W_i B (B the
  * configured external field: insulating walls) or g'_i (conducting walls).
  * The fluid relaxes with the Maxwell term of Eq. (10) at the local field
@@ -173,7 +174,10 @@ typedef struct lbm_config {
  * B above is the external field.  Both fields step from the same time
  * level.  Create / init / import / load set the field distributions to rest
  * in the external field, W_i B; lbm_step_from, the adjoint and the half-step
- * stress variants S3 / S4 are refused.  lbm_export_field reads B(x, T). */
+ * stress variants S3 / S4 are refused.  S1 / S2 take the Maxwell stress at
+ * the node's field B(x, T); LBM_MAXWELL_REMOVE of the wall force takes it at
+ * B(x_f, T-1), the field of the collision that produced f^rel(x_f, T-1).
+ * lbm_export_field reads B(x, T). */
 
 /* Stokes and Brinkman flow (the note after Eq. 11).  stokes = 1 replaces the
  * equilibrium of Eq. (1) by its linear part (plus the Maxwell term), whose

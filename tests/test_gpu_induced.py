@@ -1,0 +1,208 @@
+"""Induced magnetic field on the GPU (Sec. 4: the field carried by a vector
+lattice Boltzmann model and coupled to the flow through the Maxwell
+equilibrium of Eq. 10): parity with the FP64 oracle for the fluid
+populations and the field, for the stress and the wall force at the local
+field, the induced Hartmann flow at H = 64 against its closed form, and the
+total field that conducting walls conserve."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2512_12213_gb300 import inputs, lbm, workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 2e-6, "f16s": 1e-4, "bf16s": 1e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2512_12213_gb300 import build
+    build.build()
+    lbm.load()
+    assert torch.cuda.is_available()
+
+
+def _rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _case(name, storage, model="e", rounding="nearest"):
+    if name == "channel_2d":          # ragged D2Q9 channel with a cylinder, insulating field walls
+        nx, ny = 70, 37
+        mask = inputs.cylinder_mask(nx, ny, (30.5, 17.2), 5.1, wall=2)
+        cfg = dict(lattice=9, nx=nx, ny=ny, nz=1, periodic=(1, 0, 1), dx=0.5, dt=0.2, tau=0.71, force_model=model,
+                   g=(4e-3, 1e-3, 0), B=(0.2, 0.5, 0.0), maxwell=1, mu=1.3, induced=1, eta=0.08,
+                   mag_conducting=0, storage=storage, wall_u=((0.05, 0, 0), (0, 0, 0)), face_wall=(1, 1, 1, 1, 1, 1))
+    elif name == "duct_3d":           # D3Q19 duct with scattered solids, conducting walls, oblique field
+        nx, ny, nz = 41, 14, 11
+        mask = inputs.random_solids(nx, ny, nz, 0.04, n_walls=1, seed=31)
+        cfg = dict(lattice=19, nx=nx, ny=ny, nz=nz, periodic=(1, 0, 0), tau=0.66, force_model=model,
+                   g=(8e-5, 1e-5, 0), B=(0.03, 0.08, 0.05), maxwell=1, mu=1.1, induced=1, eta=0.02,
+                   mag_conducting=1, storage=storage, wall_u=((0, 0, 0), (0.01, 0, 0)),
+                   face_wall=(1, 1, 1, 2, 1, 1))
+    elif name == "periodic_3d":       # fully periodic D3Q19 with a sphere, Stokes + Darcy too
+        nx, ny, nz = 64, 20, 18
+        mask = inputs.sphere_mask(nx, ny, nz, (20.3, 9.6, 8.8), 4.2, wall=1)
+        cfg = dict(lattice=19, nx=nx, ny=ny, nz=nz, periodic=(1, 1, 1), tau=0.7, force_model=model,
+                   g=(1e-4, 0, 0), B=(0.0, 0.1, 0.02), maxwell=1, mu=0.9, induced=1, eta=0.15, stokes=1,
+                   darcy=0.01, storage=storage, wall_u=((0, 0, 0),))
+    cfg["rounding"] = rounding
+    return cfg, mask
+
+
+def _start(orc, cfg, mask, seed=3):
+    ocfg = orc.make_cfg(**workloads.oracle_kwargs(cfg))
+    nz, ny, nx = mask.shape
+    D = 2 if cfg["lattice"] == 9 else 3
+    rho, u = inputs.smooth_fields(nx, ny, nz, dims=D, u_amplitude=0.03, seed=seed)
+    c = cfg.get("dx", 1.0) / cfg.get("dt", 1.0)
+    f0 = orc.init(ocfg, mask, rho, u * c, inputs.noise(cfg["lattice"], nx, ny, nz, 1e-3, seed=seed + 1))
+    return ocfg, f0
+
+
+@pytest.mark.parametrize("name,storage,model,rounding", [
+    ("channel_2d", "f64", "e", "nearest"), ("channel_2d", "f64", "b", "nearest"), ("duct_3d", "f64", "d", "nearest"),
+    ("periodic_3d", "f64", "e", "nearest"), ("channel_2d", "f32", "e", "nearest"), ("duct_3d", "f32", "c", "nearest"),
+    ("periodic_3d", "f16s", "e", "nearest"), ("duct_3d", "f16s", "e", "stochastic"),
+    ("channel_2d", "bf16s", "a", "nearest"), ("periodic_3d", "bf16s", "e", "stochastic")])
+def test_populations_and_field_against_oracle(orc, name, storage, model, rounding):
+    cfg, mask = _case(name, storage, model, rounding)
+    ocfg, f0 = _start(orc, cfg, mask)
+    sim = lbm.Sim(cfg, mask)
+    sim.import_f(f0)
+    g0 = orc.mag_init(ocfg, mask)
+    B0 = orc.mag_field(ocfg, mask, g0)
+    # after import the field is at rest in the external field
+    assert _rel(sim.export_field().cpu().numpy(), B0) < 1e-15
+    steps = 20
+    sim.step(steps)
+    f_ref, g_ref, _ = orc.run_mhd(ocfg, mask, f0, g0, steps)
+    B_ref = orc.mag_field(ocfg, mask, g_ref)
+    assert _rel(sim.export_f().cpu().numpy(), f_ref) < TOL[storage]
+    B = sim.export_field().cpu().numpy()
+    assert _rel(B, B_ref) < TOL[storage]
+    # the field moved: the induced part is well above the tolerance
+    assert _rel(B_ref, B0) > 1e-4
+
+
+@pytest.mark.parametrize("name", ["channel_2d", "duct_3d"])
+def test_stress_and_wall_force_against_oracle(orc, name):
+    """S1 / S2 at f(T) with the Maxwell stress of the node's field B(T); the
+    wall force with the Maxwell term removed at the field B(T-1) of the
+    collision that produced f^rel(T-1)."""
+    cfg, mask = _case(name, "f64")
+    ocfg, f0 = _start(orc, cfg, mask)
+    sim = lbm.Sim(cfg, mask)
+    sim.import_f(f0)
+    steps = 12
+    sim.step(steps)
+    f1, g1, _ = orc.run_mhd(ocfg, mask, f0, orc.mag_init(ocfg, mask), steps - 1)
+    B_prev = orc.mag_field(ocfg, mask, g1)
+    fn, gn, frel = orc.run_mhd(ocfg, mask, f1, g1, 1)
+    B_now = orc.mag_field(ocfg, mask, gn)
+    for variant in (1, 2):
+        sg, Sg, rg, vg = [t.cpu().numpy() for t in sim.stress(variant)]
+        so, So, ro, vo = orc.stress(orc.with_field(ocfg, B_now), mask, fn, None, None, variant)
+        assert _rel(sg, so) < 1e-10, variant
+        assert _rel(Sg, So) < 1e-10, variant
+        assert _rel(vg, vo) < 1e-11, variant
+    # the Maxwell stress of the local field differs from that of B_ext
+    so_ext, _, _, _ = orc.stress(ocfg, mask, fn, None, None, 2)
+    assert _rel(so_ext, so) > 1e-6
+    for wall in (1, 2):
+        for flags in (0, lbm.MAXWELL_REMOVE, lbm.MOVING_CORR | lbm.MAXWELL_REMOVE):
+            F = sim.wall_force(wall, flags)
+            Fo = orc.wall_force(orc.with_field(ocfg, B_prev), mask, frel, fn, wall, flags)
+            assert np.abs(F - Fo).max() < 1e-11 * max(np.abs(Fo).max(), 1e-30), (wall, flags)
+            out = np.zeros(3)
+            lbm.lbm_wall_force_noalloc(sim.ctx, wall, flags, 1.0, out, 1, sim.stream)
+            assert np.abs(out - Fo).max() < 1e-11 * max(np.abs(Fo).max(), 1e-30), (wall, flags)
+    with pytest.raises(lbm.LbmError, match="S3"):
+        sim.stress(3)
+
+
+def test_reset_and_refusals(orc):
+    cfg, mask = _case("channel_2d", "f64")
+    sim = lbm.Sim(cfg, mask)
+    sim.rest()
+    ocfg = orc.make_cfg(**workloads.oracle_kwargs(cfg))
+    B0 = orc.mag_field(ocfg, mask, orc.mag_init(ocfg, mask))
+    assert np.array_equal(sim.export_field().cpu().numpy(), B0)
+    buf = torch.empty(sim.sizes[lbm.BUF_POP_A], dtype=torch.uint8, device=sim.device)
+    lbm.lbm_save_state(sim.ctx, buf, sim.stream)
+    sim.step(5)
+    assert _rel(sim.export_field().cpu().numpy(), B0) > 1e-8
+    sim.rest()
+    assert np.array_equal(sim.export_field().cpu().numpy(), B0)
+    sim.step(3)
+    lbm.lbm_load_state(sim.ctx, buf, 0, sim.stream)
+    assert np.array_equal(sim.export_field().cpu().numpy(), B0)
+    # host export through the staging buffer
+    Bh = np.zeros((3,) + mask.shape)
+    lbm.lbm_export_field(sim.ctx, Bh, 1, sim.stream)
+    assert np.array_equal(Bh, B0)
+    out = torch.empty_like(buf)
+    with pytest.raises(lbm.LbmError, match="field is state"):
+        lbm.lbm_step_from(sim.ctx, buf, out, 0, sim.stream)
+    ab = lbm.lbm_adjoint_buffer_bytes(sim.ctx)
+    p0 = torch.zeros(ab, dtype=torch.uint8, device=sim.device)
+    with pytest.raises(lbm.LbmError, match="adjoint"):
+        lbm.lbm_adjoint_step(sim.ctx, buf, None, p0, 1, (1.0, 0, 0), 1.0, sim.stream)
+    plain = lbm.Sim(dict(cfg, induced=0), mask)
+    with pytest.raises(lbm.LbmError, match="induced"):
+        plain.export_field()
+
+
+@pytest.mark.parametrize("conducting", [0, 1])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_induced_hartmann_2x128(conducting, storage):
+    """Ha 4, H = 64, insulating or conducting walls: the flow and the induced
+    field b = B_x against the closed forms of nu u'' + (B0/mu rho) b' + g = 0,
+    eta b'' + B0 u' = 0 (second order; the oracle shows 2e-3 / 6e-3 at
+    H = 32), and a normal component that stays B0 (div B = 0)."""
+    cfg, mask = workloads.hartmann_induced(storage=storage, conducting=conducting)
+    H, tau, B0, Ha = 64, cfg["tau"], cfg["B"][1], 4.0
+    nu = (tau - 0.5) / 3
+    K = nu * Ha ** 2 / H ** 2
+    eta = cfg["eta"]
+    m = np.sqrt(K / nu)
+    gain = 1 / K if conducting else 1 / (K * np.tanh(m * H) / (m * H))
+    g = cfg["g"][0]
+    sim = lbm.Sim(cfg, mask)
+    sim.rest()
+    sim.step(80 * H * H)
+    y = np.arange(2 * H) - H + 0.5
+    u = g * gain * (1 - np.cosh(m * y) / np.cosh(m * H))
+    intu = g * gain * ((y + H) - (np.sinh(m * y) + np.sinh(m * H)) / (m * np.cosh(m * H)))
+    if conducting:
+        b = -(B0 / eta) * intu
+        b -= b.mean()
+    else:
+        b = (B0 / eta) * (u.mean() * (y + H) - intu)
+    _, _, _, v = sim.stress(lbm.S2)
+    B = sim.export_field().cpu().numpy()
+    assert _rel(v[0, 0, :, 0].cpu().numpy(), u) < 1e-3
+    assert _rel(B[0, 0, :, 0], b) < 3e-3
+    assert np.abs(B[1] - B0).max() < (1e-13 if storage == "f64" else 1e-6)
+
+
+def test_total_field_conserved_by_conducting_walls(orc):
+    """Relaxation keeps sum_i g_i = B at each node and bounce-back keeps the
+    population at its node, so conducting walls conserve the total field
+    step by step (insulating walls exchange with the external field)."""
+    cfg, mask = _case("duct_3d", "f64")
+    for conducting in (1, 0):
+        c = dict(cfg, mag_conducting=conducting)
+        ocfg, f0 = _start(orc, c, mask, seed=7)
+        sim = lbm.Sim(c, mask)
+        sim.import_f(f0)
+        tot0 = sim.export_field().sum(dim=(1, 2, 3)).cpu().numpy()
+        drift = 0.0
+        for _ in range(5):
+            sim.step(1)
+            drift = max(drift, np.abs(sim.export_field().sum(dim=(1, 2, 3)).cpu().numpy() - tot0).max())
+        if conducting:
+            assert drift < 1e-14 * mask.size
+        else:
+            assert drift > 1e-8
