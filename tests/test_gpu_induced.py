@@ -73,8 +73,9 @@ def test_populations_and_field_against_oracle(orc, name, storage, model, roundin
     sim.import_f(f0)
     g0 = orc.mag_init(ocfg, mask)
     B0 = orc.mag_field(ocfg, mask, g0)
-    # after import the field is at rest in the external field
-    assert _rel(sim.export_field().cpu().numpy(), B0) < 1e-15
+    # after import the field is at rest in the external field (W_i B summed
+    # in the compute precision: FP64, else FP32)
+    assert _rel(sim.export_field().cpu().numpy(), B0) < (1e-15 if storage == "f64" else 3e-7)
     steps = 20
     sim.step(steps)
     f_ref, g_ref, _ = orc.run_mhd(ocfg, mask, f0, g0, steps)
