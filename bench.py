@@ -50,8 +50,9 @@ def parse():
                    help="storage of the headline run (profiling)")
     p.add_argument("--rounding", default="stochastic", choices=["nearest", "stochastic"],
                    help="rounding of 16-bit stores in the headline run")
-    p.add_argument("--workload", default="sphere", choices=["sphere", "cavity"],
-                   help="headline workload (profiling): sphere 256x128x128 or cavity 256^3 LES")
+    p.add_argument("--workload", default="sphere", choices=["sphere", "cavity"] + list(EXTENSIONS),
+                   help="headline workload (profiling): sphere 256x128x128, cavity 256^3 LES, or the "
+                        "sphere box with one extension (curved walls, insulating walls, Brinkman, induced field)")
     return p.parse_args()
 
 
@@ -146,9 +147,41 @@ class Clocks:
 
 
 # --------------------------------------------------------------- our arm
-def bytes_per_node(Q, storage):
+def bytes_per_node(Q, storage, induced=False):
+    """Algorithmic bytes of one node update: read + write every population
+    plus the node-class byte; with the induced field also read + write the
+    3 x 7 field distributions (compute precision)."""
     s = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}[storage]
-    return 2 * Q * s + 1      # read + write every population, plus the node-class byte
+    b = 2 * Q * s + 1
+    if induced:
+        b += 2 * 3 * (5 if Q == 9 else 7) * (8 if storage == "f64" else 4)
+    return b
+
+
+# the sphere box with each extension of the core step: workload builder,
+# step kernel(s) timed, and a description
+EXTENSIONS = {
+    "curved": ("sphere_curved", "k_step<19,S,EXT=0> (interpolated bounce-back in boundary chunks)",
+               "true sphere r=12.4 as the wall, linear interpolated bounce-back from the signed distance"),
+    "insulating": ("sphere_insulating", "k_step<19,S,EXT=1> + k_ins_rows + k_reduce_rows + k_ins_field",
+                   "imposed field (0, 0.02, 0), sigma_e = 1, Lorentz force, insulating walls E = -<v> x B"),
+    "brinkman": ("sphere_brinkman", "k_step<19,S,EXT=1>",
+                 "linear (Stokes) equilibrium, Darcy resistance 1e-4 (Brinkman)"),
+    "induced": ("sphere_induced", "k_mhd_step<19,S> (fluid D3Q19 + field D3Q7, one node per thread)",
+                "external field (0, 0.02, 0), induced field on D3Q7, eta = 0.05, Maxwell equilibrium at the local field"),
+}
+
+
+def make_workload(workloads, name, storage):
+    """(cfg, mask, phi or None) of a named workload."""
+    if name == "sphere":
+        c, m = workloads.sphere(storage=storage)
+        return c, m, None
+    if name == "cavity":
+        c, m = workloads.cavity(n=256, storage=storage)
+        return c, m, None
+    out = getattr(workloads, EXTENSIONS[name][0])(storage=storage)
+    return out if len(out) == 3 else (out[0], out[1], None)
 
 
 def timed_run(torch, lbm, sim, steps, warmup, wall=1, events=True):
@@ -208,20 +241,18 @@ def run_ours(args):
     out = {}
 
     # ---- headline: sphere, shifted binary16 storage
-    if args.workload == "sphere":
-        cfg, mask = workloads.sphere(storage=args.storage)
-        hwall = 1
-    else:
-        cfg, mask = workloads.cavity(n=256, storage=args.storage)
-        hwall = 2
+    cfg, mask, phi = make_workload(workloads, args.workload, args.storage)
+    hwall = 2 if args.workload == "cavity" else 1
     sr = args.storage in ("f16s", "bf16s") and args.rounding == "stochastic"
     if sr:
         cfg = dict(cfg, rounding="stochastic", seed=2024)
     sim = lbm.Sim(cfg, mask)
+    if phi is not None:
+        sim.set_wall_distance(phi)
     sim.rest()
     N = cfg["nx"] * cfg["ny"] * cfg["nz"]
     fluid = int((mask == 0).sum())
-    bpn = bytes_per_node(19, args.storage)
+    bpn = bytes_per_node(19, args.storage, induced=bool(cfg.get("induced")))
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -237,7 +268,9 @@ def run_ours(args):
     value = ws * N * args.steps / (total_ms * 1e-3) / 1e6
     achieved = N * bpn / (kern_ms * 1e-3) / 1e9
     kname = {"f64": "StoreF64", "f32": "StoreF32", "f16s": "StoreF16", "bf16s": "StoreBF16"}[args.storage]
-    roof = {"kernel": f"k_step<19,{kname},EXT={int(bool(cfg.get('les')))},SR={int(sr)}>", "bound": "hbm", "achieved": round(achieved, 1),
+    kernel = (EXTENSIONS[args.workload][1].replace(",S", "," + kname) if args.workload in EXTENSIONS
+              else f"k_step<19,{kname},EXT={int(bool(cfg.get('les')))},SR={int(sr)}>")
+    roof = {"kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1),
             "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "peak_source": peak_kind,
             "bytes_per_node": bpn, "step_kernel_ms": round(kern_ms, 5),
             "kernel_mlups": round(N / (kern_ms * 1e-3) / 1e6, 1),
@@ -273,6 +306,7 @@ def run_ours(args):
         out["storage_variants"] = variants
         out["drag_error_vs_f64"] = drag_errors(torch, lbm, workloads, args.drag_steps)
         out["cavity_les_f32"] = cavity_bench(torch, lbm, workloads, hbm, args)
+        out["extensions_f32"] = extensions_bench(torch, lbm, workloads, hbm, args)
         out["adjoint"] = adjoint_bench(torch, lbm, workloads, hbm)
         e2e = e2e_bench(torch, lbm, workloads, args)
         cpu = cpu_baseline()
@@ -285,7 +319,8 @@ def run_ours(args):
             "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.workload == "sphere" else "D3Q19 LES cavity 256^3",
+            "config": {"workload": {"sphere": WORKLOAD, "cavity": "D3Q19 LES cavity 256^3"}.get(
+                           args.workload, WORKLOAD + "; " + EXTENSIONS.get(args.workload, ("", "", ""))[2]),
                        "nodes": N, "fluid_nodes": fluid,
                        "storage": args.storage + (" (shifted x2^12, stochastic rounding)" if sr and args.storage == "f16s"
                                                   else (" (stochastic rounding)" if sr else "")),
@@ -367,6 +402,33 @@ def cavity_bench(torch, lbm, workloads, hbm, args):
     return {"workload": "D3Q19 lid-driven cavity 256^3, lid u=0.1, tau=0.55, Smagorinsky Cs=0.1, FP32",
             "mlups": round(N * steps / (t * 1e-3) / 1e6, 1), "kernel_mlups": round(N / (k * 1e-3) / 1e6, 1),
             "achieved_gbs": round(ach, 1), "frac": round(ach / hbm, 4), "steps": steps}
+
+
+def extensions_bench(torch, lbm, workloads, hbm, args):
+    """Each extension of the core step on the sphere box in FP32 storage:
+    throughput, the step's mean duration and its HBM roofline fraction
+    (algorithmic bytes: populations, class byte, and the field distributions
+    of the induced field)."""
+    res = {}
+    steps = max(args.steps // 4, 50)
+    for name, (_, kernel, desc) in EXTENSIONS.items():
+        c, m, phi = make_workload(workloads, name, "f32")
+        s = lbm.Sim(c, m)
+        if phi is not None:
+            s.set_wall_distance(phi)
+        s.rest()
+        N = c["nx"] * c["ny"] * c["nz"]
+        t, k = timed_run(torch, lbm, s, steps, args.warmup)
+        bp = bytes_per_node(19, "f32", induced=bool(c.get("induced")))
+        ach = N * bp / (k * 1e-3) / 1e9
+        res[name] = {"workload": desc, "kernel": kernel.replace(",S", ",StoreF32"), "steps": steps,
+                     "mlups": round(N * steps / (t * 1e-3) / 1e6, 1), "step_ms": round(k, 5),
+                     "kernel_mlups": round(N / (k * 1e-3) / 1e6, 1), "bytes_per_node": bp,
+                     "achieved_gbs": round(ach, 1), "frac": round(ach / hbm, 4)}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    return res
 
 
 def adjoint_case(torch, lbm, adjoint, c, m, T, hbm):

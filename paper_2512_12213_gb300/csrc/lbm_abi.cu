@@ -195,6 +195,13 @@ long long step_threads_of(const lbm_config* c)
     return (long long)(pitch_of(c->nx) / V) * c->ny * c->nz;
 }
 
+// insulating walls: one velocity-sum row per warp of the step grid (blocks of
+// 128 threads; the warps past the last chunk write zero rows)
+long long ins_rows_of(const lbm_config* c)
+{
+    return (step_threads_of(c) + 127) / 128 * 4;
+}
+
 void sizes_of(const lbm_config* c, long long n_links, size_t s[LBM_NUM_BUFFERS])
 {
     const long long sq = (long long)pitch_of(c->nx) * c->ny * c->nz;
@@ -204,7 +211,7 @@ void sizes_of(const lbm_config* c, long long n_links, size_t s[LBM_NUM_BUFFERS])
     s[LBM_BUF_LINKS] = n_links ? round256((size_t)n_links * sizeof(Link)) : 0;
     s[LBM_BUF_SCRATCH] = round256(SCRATCH_DOUBLES * sizeof(double));
     if (c->insulating)
-        s[LBM_BUF_SCRATCH] = round256((SCRATCH_INS_ROWS + 3 * (size_t)step_threads_of(c)) * sizeof(double));
+        s[LBM_BUF_SCRATCH] = round256((SCRATCH_INS_ROWS + 3 * (size_t)ins_rows_of(c)) * sizeof(double));
     s[LBM_BUF_STAGE] = round256((size_t)(c->lattice + 4) * N * sizeof(double));
     s[LBM_BUF_PHI] = c->curved ? round256((size_t)sq * sizeof(float)) : 0;
     // induced field: 3 components x (5 or 7) directions per padded node, compute precision
@@ -384,7 +391,8 @@ void choose_tile(Ctx& x)
     // LBM_STEP_KERNEL=tile selects the shared-memory staged step where it fits;
     // the register-tiled step is the default
     const char* sel = getenv("LBM_STEP_KERNEL");
-    const bool want_tile = sel && strcmp(sel, "tile") == 0 && x.cfg.rounding == LBM_ROUND_NEAREST && !x.insulating && !x.cfg.curved && !x.cfg.stokes && !(x.cfg.darcy > 0.0);
+    const bool want_tile = sel && strcmp(sel, "tile") == 0 && x.cfg.rounding == LBM_ROUND_NEAREST && !x.insulating &&
+                           !x.cfg.curved && !x.cfg.stokes && !(x.cfg.darcy > 0.0) && !x.cfg.induced;
     const bool fits = want_tile && smem_for(R, ns) <= (size_t)x.smem_optin;
     x.tile_R = fits ? R : 0;
     x.tile_stages = fits ? ns : 0;
@@ -515,7 +523,7 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
     x.ext = (cfg->lorentz || cfg->maxwell || cfg->les || cfg->stokes || cfg->darcy > 0.0 || cfg->induced) ? 1 : 0;
     x.sr = (cfg->rounding == LBM_ROUND_STOCHASTIC) ? 1 : 0;
     x.insulating = cfg->insulating != 0;
-    x.ins_threads = step_threads_of(cfg);
+    x.ins_rows = ins_rows_of(cfg);
     x.n_fluid = 0;
     for (long long n = 0; n < (long long)cfg->nx * cfg->ny * cfg->nz; ++n) x.n_fluid += host_wall_id[n] == 0;
     x.geo.nx = cfg->nx;
@@ -1017,11 +1025,19 @@ cudaError_t launch_reduce_rows(const double* partials, int nb, int W, double* ou
     return cudaGetLastError();
 }
 
-// insulating walls, stage one: block b sums the rows [b*chunk, (b+1)*chunk)
-// of the step threads' velocity sums in a fixed order
-__global__ void k_ins_rows(const double* __restrict__ rows, long long n, long long chunk, double* __restrict__ out)
+// insulating walls, after a step: block b sums the warp rows
+// [b*chunk, (b+1)*chunk) of the step kernel's velocity sums in a fixed order;
+// the last block to finish (ticket) sums the block sums in a fixed order and
+// sets the field of Eq. (36), E = -<v> x B with <v> = c sum(v) / n_fluid, and
+// its force coefficient dt sigma_e (E x B) / c in FP64, FP32 and FP32 storage
+// units, then clears the ticket for the next step
+__global__ void k_ins_update(const double* __restrict__ rows, long long n, long long chunk, double* part, double* blk,
+                             double n_fluid, double c, double dt, double sigma, double B0, double B1, double B2,
+                             double scale)
 {
     __shared__ double sm[3 * 32];
+    __shared__ int last;
+    unsigned* ticket = reinterpret_cast<unsigned*>(blk + INS_TICKET);
     double v[3] = {0.0, 0.0, 0.0};
     const long long b0 = (long long)blockIdx.x * chunk, b1 = min(n, b0 + chunk);
     for (long long r = b0 + threadIdx.x; r < b1; r += blockDim.x)
@@ -1036,24 +1052,34 @@ __global__ void k_ins_rows(const double* __restrict__ rows, long long n, long lo
         for (int k = 0; k < 3; ++k) {
             double s = (lane < nw) ? sm[k * 32 + lane] : 0.0;
             for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-            if (lane == 0) out[blockIdx.x * 3 + k] = s;
+            if (lane == 0) part[blockIdx.x * 3 + k] = s;
+        }
+        if (lane == 0) {
+            __threadfence();
+            last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1 : 0;
         }
     }
-}
-
-// the field of insulating walls (Eq. 36): E = -<v> x B with <v> = c sum(W) / n_fluid,
-// and its force coefficient dt sigma_e (E x B) / c in each precision
-__global__ void k_ins_field(double* blk, double n_fluid, double c, double dt, double sigma, double B0, double B1,
-                            double B2, double scale)
-{
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const double* vs = blk + INS_VSUM;
-    const double v[3] = {c * vs[0] / n_fluid, c * vs[1] / n_fluid, c * vs[2] / n_fluid};
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // warp k sums column k of the block sums: lane l takes rows l, l+32, ...,
+    // then a fixed shuffle tree
+    if (wid < 3) {
+        double s = 0.0;
+        for (int r = lane; r < (int)gridDim.x; r += 32) s += __ldcg(part + r * 3 + wid);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) sm[wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double* vs = blk + INS_VSUM;
+    for (int k = 0; k < 3; ++k) vs[k] = sm[k];
+    const double vm[3] = {c * vs[0] / n_fluid, c * vs[1] / n_fluid, c * vs[2] / n_fluid};
     const double B[3] = {B0, B1, B2};
     double E[3];
-    E[0] = -(v[1] * B[2] - v[2] * B[1]);
-    E[1] = -(v[2] * B[0] - v[0] * B[2]);
-    E[2] = -(v[0] * B[1] - v[1] * B[0]);
+    E[0] = -(vm[1] * B[2] - vm[2] * B[1]);
+    E[1] = -(vm[2] * B[0] - vm[0] * B[2]);
+    E[2] = -(vm[0] * B[1] - vm[1] * B[0]);
     const double ExB[3] = {E[1] * B[2] - E[2] * B[1], E[2] * B[0] - E[0] * B[2], E[0] * B[1] - E[1] * B[0]};
     float* af = reinterpret_cast<float*>(blk + INS_AEB_F);
     float* as = reinterpret_cast<float*>(blk + INS_AEB_S);
@@ -1064,6 +1090,7 @@ __global__ void k_ins_field(double* blk, double n_fluid, double c, double dt, do
         af[k] = (float)aeb;
         as[k] = (float)(aeb * scale);
     }
+    *ticket = 0u;
 }
 
 // the configured field (after create, init, import or load)
@@ -1077,6 +1104,7 @@ __global__ void k_ins_reset(double* blk, double E0, double E1, double E2, double
     float* as = reinterpret_cast<float*>(blk + INS_AEB_S);
     af[0] = f0; af[1] = f1; af[2] = f2;
     as[0] = s0; as[1] = s1; as[2] = s2;
+    *reinterpret_cast<unsigned*>(blk + INS_TICKET) = 0u;
 }
 
 __global__ void k_zero(double* p, long long n)
@@ -1091,22 +1119,16 @@ cudaError_t launch_zero(double* p, long long n, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// after a step: sum the step threads' velocity rows in a fixed order (at
-// most INS_RED_ROWS blocks, then one row pass) and set the field
+// after a step: sum the warps' velocity rows in a fixed order and set the field
 cudaError_t ins_update(const Ctx& x, cudaStream_t st)
 {
-    double* blk = x.scratch + SCRATCH_INS_OFF;
-    const long long n = x.ins_threads;
-    const long long chunk = (n + INS_RED_ROWS - 1) / INS_RED_ROWS;
+    const long long n = x.ins_rows;
+    const long long chunk = std::max<long long>((n + INS_RED_ROWS - 1) / INS_RED_ROWS, 256);
     const int nb = (int)((n + chunk - 1) / chunk);
-    k_ins_rows<<<nb, 256, 0, st>>>(x.scratch + SCRATCH_INS_ROWS, n, chunk, x.scratch + SCRATCH_INS_RED);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = launch_reduce_rows(x.scratch + SCRATCH_INS_RED, nb, 3, blk + INS_VSUM, 1.0, 0, st);
-    if (e != cudaSuccess) return e;
     const double scale = (x.cfg.storage == LBM_STORE_F16S) ? 4096.0 : 1.0;
-    k_ins_field<<<1, 32, 0, st>>>(blk, (double)(x.n_fluid > 0 ? x.n_fluid : 1), x.kpd.c, x.kpd.dt, x.cfg.sigma_e,
-                                  x.cfg.B[0], x.cfg.B[1], x.cfg.B[2], scale);
+    k_ins_update<<<nb, 256, 0, st>>>(x.scratch + SCRATCH_INS_ROWS, n, chunk, x.scratch + SCRATCH_INS_RED,
+                                     x.scratch + SCRATCH_INS_OFF, (double)(x.n_fluid > 0 ? x.n_fluid : 1), x.kpd.c,
+                                     x.kpd.dt, x.cfg.sigma_e, x.cfg.B[0], x.cfg.B[1], x.cfg.B[2], scale);
     return cudaGetLastError();
 }
 

@@ -58,10 +58,12 @@ constexpr size_t SCRATCH_OUT_OFF = SCRATCH_ADJ_OFF + (size_t)ADJ_BLOCKS * 6;
 constexpr size_t SCRATCH_FLAG_OFF = SCRATCH_OUT_OFF + 8;   // device error flags (unsigned)
 constexpr size_t SCRATCH_DOUBLES = SCRATCH_FLAG_OFF + 8;
 // insulating walls only, after the above: the field block (E, the sum of v,
-// the force coefficient in FP64, FP32 and FP32 storage units), the stage-one
-// rows of the velocity sum, then one row of 3 doubles per step thread
+// the force coefficient in FP64, FP32 and FP32 storage units, the ticket of
+// the last-block reduction), the stage-one rows of the velocity sum, then one
+// row of 3 doubles per warp of the step grid
 constexpr size_t SCRATCH_INS_OFF = SCRATCH_DOUBLES;
 constexpr int INS_E = 0, INS_VSUM = 3, INS_AEB_D = 6, INS_AEB_F = 9, INS_AEB_S = 11;   // doubles into the block
+constexpr int INS_TICKET = 14;                                                         // unsigned in a double slot
 constexpr int INS_RED_ROWS = 1024;
 constexpr size_t SCRATCH_INS_RED = SCRATCH_INS_OFF + 16;
 constexpr size_t SCRATCH_INS_ROWS = SCRATCH_INS_RED + (size_t)INS_RED_ROWS * 3;
@@ -138,9 +140,9 @@ struct Ctx {
     unsigned* errflag;
     // curved walls: the wall ids of the geometry (host), to check distances
     std::vector<uint8_t> host_wid;
-    // insulating walls: step threads (rows of the velocity sum) and fluid nodes
+    // insulating walls: rows of the velocity sum (warps of the step grid) and fluid nodes
     bool insulating;
-    long long ins_threads;
+    long long ins_rows;
     long long n_fluid;
 };
 

@@ -14,6 +14,11 @@ namespace lbm {
 
 constexpr int STEP_THREADS = 128;
 constexpr int NODE_THREADS = 256;
+// blocks of NODE_THREADS per SM for the coupled field step: FP32 compute 3
+// (85 registers, no spill), FP64 2
+template <class S> struct MhdOcc {
+    static constexpr int value = sizeof(typename S::R) == 8 ? 2 : 3;
+};
 constexpr int RED_THREADS = 256;
 
 // ------------------------------------------------------------ warp helpers
@@ -315,45 +320,10 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
             }
         }
     }
-    if (!active) return;
-
-    // Ladd terms of moving face walls, added after unpacking (face chunks only)
-    const bool ladd = FACES && face_chunk && p.face_ladd;
-    auto add_ladd = [&](R (&d)[Q], int k) {
-#pragma unroll
-        for (int a = 1; a < Q; ++a) {
-            int wall = 0;
-            bool hit = row_out<Q>(fi, a, wall);
-            if (fi.closed_x) {
-                if (EX<Q>(a) == 1 && x0 + k == 0) { hit = true; wall = fi.wx_lo; }
-                if (EX<Q>(a) == -1 && x0 + k == g.nx - 1) { hit = true; wall = fi.wx_hi; }
-            }
-            if (hit) d[a] += ladd_of<Q, R>(p, a, wall);
-        }
-    };
-
-    // the same for two consecutive nodes k, k+1 held as pairs
-    auto add_ladd2 = [&](F2 (&d)[Q], int k) {
-#pragma unroll
-        for (int a = 1; a < Q; ++a) {
-            int wall = 0;
-            const bool hit = row_out<Q>(fi, a, wall);
-            int w0 = wall, w1 = wall;
-            bool h0 = hit, h1 = hit;
-            if (fi.closed_x) {
-                if (EX<Q>(a) == 1 && x0 + k == 0) { h0 = true; w0 = fi.wx_lo; }
-                if (EX<Q>(a) == -1 && x0 + k == g.nx - 1) { h0 = true; w0 = fi.wx_hi; }
-                if (EX<Q>(a) == -1 && x0 + k + 1 == g.nx - 1) { h1 = true; w1 = fi.wx_hi; }
-            }
-            if (h0) d[a].v.x += ladd_of<Q, R>(p, a, w0);
-            if (h1) d[a].v.y += ladd_of<Q, R>(p, a, w1);
-        }
-    };
-    // two nodes at a time in packed FP32x2 arithmetic (FP32 compute without
-    // the Lorentz force, Maxwell term or LES)
-    constexpr bool PAIR2 = !EXT && sizeof(R) == 4;
     // insulating walls: this thread's sum of the flow velocity v over the
-    // fluid nodes it relaxes, one row per thread for a fixed-order reduction
+    // fluid nodes it relaxes, summed over the warp by a fixed shuffle tree in
+    // FP64 (every thread of the block reaches it, inactive ones with zero),
+    // one row per warp for the fixed-order reduction of the field
     R vs[3] = {R(0), R(0), R(0)};
     auto add_v = [&](const NodeM<R>& m) {
         if constexpr (EXT) {
@@ -365,163 +335,206 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
     auto put_v = [&]() {
         if constexpr (EXT) {
             if (p.ins_rows) {
+                double t[3] = {(double)vs[0], (double)vs[1], (double)vs[2]};
 #pragma unroll
-                for (int k = 0; k < 3; ++k) p.ins_rows[tid * 3 + k] = (double)vs[k];
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) t[k] += __shfl_down_sync(0xffffffffu, t[k], o);
+                if (lane == 0)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) p.ins_rows[(tid >> 5) * 3 + k] = t[k];
             }
         }
     };
+    if (active) {
 
-    const long long base = row * g.nxp + x0;
-    if (!special) {
-        if constexpr (PACKED && PAIR2) {
+        // Ladd terms of moving face walls, added after unpacking (face chunks only)
+        const bool ladd = FACES && face_chunk && p.face_ladd;
+        auto add_ladd = [&](R (&d)[Q], int k) {
 #pragma unroll
-            for (int i = 0; i < V / 2; ++i) {
-                F2 dd[Q];
-#pragma unroll
-                for (int a = 0; a < Q; ++a) dd[a] = F2{S::unpack2(w[a][i])};
-                if (ladd) add_ladd2(dd, 2 * i);
-                pair_collide<Q>(dd, p);
-                if constexpr (SR) {
-                    NodeRng rp((uint32_t)(base + 2 * i), seed);     // the pair's first node
-#pragma unroll
-                    for (int a = 0; a < Q; ++a) w[a][i] = S::pack2_sr(dd[a].v.x, dd[a].v.y, rp.word());
-                } else {
-#pragma unroll
-                    for (int a = 0; a < Q; ++a) w[a][i] = S::pack2(dd[a].v.x, dd[a].v.y);
+            for (int a = 1; a < Q; ++a) {
+                int wall = 0;
+                bool hit = row_out<Q>(fi, a, wall);
+                if (fi.closed_x) {
+                    if (EX<Q>(a) == 1 && x0 + k == 0) { hit = true; wall = fi.wx_lo; }
+                    if (EX<Q>(a) == -1 && x0 + k == g.nx - 1) { hit = true; wall = fi.wx_hi; }
                 }
+                if (hit) d[a] += ladd_of<Q, R>(p, a, wall);
             }
+        };
+
+        // the same for two consecutive nodes k, k+1 held as pairs
+        auto add_ladd2 = [&](F2 (&d)[Q], int k) {
 #pragma unroll
-            for (int a = 0; a < Q; ++a) {
-                VecN<T, V> o;
-#pragma unroll
-                for (int i = 0; i < V / 2; ++i) o.u[i] = w[a][i];
-                *reinterpret_cast<typename RawVec<sizeof(T) * V>::type*>(dst + (long long)a * g.sq + base) = o.raw;
+            for (int a = 1; a < Q; ++a) {
+                int wall = 0;
+                const bool hit = row_out<Q>(fi, a, wall);
+                int w0 = wall, w1 = wall;
+                bool h0 = hit, h1 = hit;
+                if (fi.closed_x) {
+                    if (EX<Q>(a) == 1 && x0 + k == 0) { h0 = true; w0 = fi.wx_lo; }
+                    if (EX<Q>(a) == -1 && x0 + k == g.nx - 1) { h0 = true; w0 = fi.wx_hi; }
+                    if (EX<Q>(a) == -1 && x0 + k + 1 == g.nx - 1) { h1 = true; w1 = fi.wx_hi; }
+                }
+                if (h0) d[a].v.x += ladd_of<Q, R>(p, a, w0);
+                if (h1) d[a].v.y += ladd_of<Q, R>(p, a, w1);
             }
-        } else if constexpr (PACKED) {
-            // two nodes per packed word: unpack both, relax them, pack both
-            // with one conversion
-#pragma unroll
-            for (int i = 0; i < V / 2; ++i) {
-                R d0[Q], d1[Q];
-#pragma unroll
-                for (int a = 0; a < Q; ++a) {
-                    const float2 v = S::unpack2(w[a][i]);
-                    d0[a] = v.x;
-                    d1[a] = v.y;
-                }
-                if (ladd) {
-                    add_ladd(d0, 2 * i);
-                    add_ladd(d1, 2 * i + 1);
-                }
-                {
-                    NodeM<R> m;
-                    node_macro<R, Q, EXT>(d0, p, m);
-                    node_relax<R, Q, EXT>(d0, p, m);
-                    add_v(m);
-                }
-                {
-                    NodeM<R> m;
-                    node_macro<R, Q, EXT>(d1, p, m);
-                    node_relax<R, Q, EXT>(d1, p, m);
-                    add_v(m);
-                }
-                if constexpr (SR) {
-                    NodeRng rp((uint32_t)(base + 2 * i), seed);     // the pair's first node
-#pragma unroll
-                    for (int a = 0; a < Q; ++a) w[a][i] = S::pack2_sr(d0[a], d1[a], rp.word());
-                } else {
-#pragma unroll
-                    for (int a = 0; a < Q; ++a) w[a][i] = S::pack2(d0[a], d1[a]);
-                }
-            }
-#pragma unroll
-            for (int a = 0; a < Q; ++a) {
-                VecN<T, V> o;
-#pragma unroll
-                for (int i = 0; i < V / 2; ++i) o.u[i] = w[a][i];
-                *reinterpret_cast<typename RawVec<sizeof(T) * V>::type*>(dst + (long long)a * g.sq + base) = o.raw;
-            }
-        } else {
-            if constexpr (EXT) {
-                // larger node code (Lorentz / Maxwell / LES): the same rolled queue
-#pragma unroll 1
-                for (int k = 0; k < V; ++k) {
-                    R d[Q];
-#pragma unroll
-                    for (int a = 0; a < Q; ++a) d[a] = S::to_raw(f[a][0]);
-                    if (ladd) add_ladd(d, k);
-                    NodeM<R> m;
-                    node_macro<R, Q, EXT>(d, p, m);
-                    node_relax<R, Q, EXT>(d, p, m);
-                    add_v(m);
-#pragma unroll
-                    for (int a = 0; a < Q; ++a) {
-#pragma unroll
-                        for (int j = 0; j < V - 1; ++j) f[a][j] = f[a][j + 1];
-                        f[a][V - 1] = S::from_raw(d[a]);
-                    }
-                }
-            } else if constexpr (PAIR2) {
+        };
+        // two nodes at a time in packed FP32x2 arithmetic (FP32 compute without
+        // the Lorentz force, Maxwell term or LES)
+        constexpr bool PAIR2 = !EXT && sizeof(R) == 4;
+
+        const long long base = row * g.nxp + x0;
+        if (!special) {
+            if constexpr (PACKED && PAIR2) {
 #pragma unroll
                 for (int i = 0; i < V / 2; ++i) {
                     F2 dd[Q];
 #pragma unroll
-                    for (int a = 0; a < Q; ++a) dd[a] = F2{make_float2(S::to_raw(f[a][2 * i]), S::to_raw(f[a][2 * i + 1]))};
+                    for (int a = 0; a < Q; ++a) dd[a] = F2{S::unpack2(w[a][i])};
                     if (ladd) add_ladd2(dd, 2 * i);
                     pair_collide<Q>(dd, p);
+                    if constexpr (SR) {
+                        NodeRng rp((uint32_t)(base + 2 * i), seed);     // the pair's first node
 #pragma unroll
-                    for (int a = 0; a < Q; ++a) {
-                        f[a][2 * i] = S::from_raw(dd[a].v.x);
-                        f[a][2 * i + 1] = S::from_raw(dd[a].v.y);
+                        for (int a = 0; a < Q; ++a) w[a][i] = S::pack2_sr(dd[a].v.x, dd[a].v.y, rp.word());
+                    } else {
+#pragma unroll
+                        for (int a = 0; a < Q; ++a) w[a][i] = S::pack2(dd[a].v.x, dd[a].v.y);
                     }
                 }
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    VecN<T, V> o;
+#pragma unroll
+                    for (int i = 0; i < V / 2; ++i) o.u[i] = w[a][i];
+                    *reinterpret_cast<typename RawVec<sizeof(T) * V>::type*>(dst + (long long)a * g.sq + base) = o.raw;
+                }
+            } else if constexpr (PACKED) {
+                // two nodes per packed word: unpack both, relax them, pack both
+                // with one conversion
+#pragma unroll
+                for (int i = 0; i < V / 2; ++i) {
+                    R d0[Q], d1[Q];
+#pragma unroll
+                    for (int a = 0; a < Q; ++a) {
+                        const float2 v = S::unpack2(w[a][i]);
+                        d0[a] = v.x;
+                        d1[a] = v.y;
+                    }
+                    if (ladd) {
+                        add_ladd(d0, 2 * i);
+                        add_ladd(d1, 2 * i + 1);
+                    }
+                    {
+                        NodeM<R> m;
+                        node_macro<R, Q, EXT>(d0, p, m);
+                        node_relax<R, Q, EXT>(d0, p, m);
+                        add_v(m);
+                    }
+                    {
+                        NodeM<R> m;
+                        node_macro<R, Q, EXT>(d1, p, m);
+                        node_relax<R, Q, EXT>(d1, p, m);
+                        add_v(m);
+                    }
+                    if constexpr (SR) {
+                        NodeRng rp((uint32_t)(base + 2 * i), seed);     // the pair's first node
+#pragma unroll
+                        for (int a = 0; a < Q; ++a) w[a][i] = S::pack2_sr(d0[a], d1[a], rp.word());
+                    } else {
+#pragma unroll
+                        for (int a = 0; a < Q; ++a) w[a][i] = S::pack2(d0[a], d1[a]);
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    VecN<T, V> o;
+#pragma unroll
+                    for (int i = 0; i < V / 2; ++i) o.u[i] = w[a][i];
+                    *reinterpret_cast<typename RawVec<sizeof(T) * V>::type*>(dst + (long long)a * g.sq + base) = o.raw;
+                }
             } else {
+                if constexpr (EXT) {
+                    // larger node code (Lorentz / Maxwell / LES): the same rolled queue
+#pragma unroll 1
+                    for (int k = 0; k < V; ++k) {
+                        R d[Q];
 #pragma unroll
-                for (int k = 0; k < V; ++k) {
-                    R d[Q];
+                        for (int a = 0; a < Q; ++a) d[a] = S::to_raw(f[a][0]);
+                        if (ladd) add_ladd(d, k);
+                        NodeM<R> m;
+                        node_macro<R, Q, EXT>(d, p, m);
+                        node_relax<R, Q, EXT>(d, p, m);
+                        add_v(m);
 #pragma unroll
-                    for (int a = 0; a < Q; ++a) d[a] = S::to_raw(f[a][k]);
-                    if (ladd) add_ladd(d, k);
-                    NodeM<R> m;
-                    node_macro<R, Q, EXT>(d, p, m);
-                    node_relax<R, Q, EXT>(d, p, m);
+                        for (int a = 0; a < Q; ++a) {
 #pragma unroll
-                    for (int a = 0; a < Q; ++a) f[a][k] = S::from_raw(d[a]);
+                            for (int j = 0; j < V - 1; ++j) f[a][j] = f[a][j + 1];
+                            f[a][V - 1] = S::from_raw(d[a]);
+                        }
+                    }
+                } else if constexpr (PAIR2) {
+#pragma unroll
+                    for (int i = 0; i < V / 2; ++i) {
+                        F2 dd[Q];
+#pragma unroll
+                        for (int a = 0; a < Q; ++a) dd[a] = F2{make_float2(S::to_raw(f[a][2 * i]), S::to_raw(f[a][2 * i + 1]))};
+                        if (ladd) add_ladd2(dd, 2 * i);
+                        pair_collide<Q>(dd, p);
+#pragma unroll
+                        for (int a = 0; a < Q; ++a) {
+                            f[a][2 * i] = S::from_raw(dd[a].v.x);
+                            f[a][2 * i + 1] = S::from_raw(dd[a].v.y);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < V; ++k) {
+                        R d[Q];
+#pragma unroll
+                        for (int a = 0; a < Q; ++a) d[a] = S::to_raw(f[a][k]);
+                        if (ladd) add_ladd(d, k);
+                        NodeM<R> m;
+                        node_macro<R, Q, EXT>(d, p, m);
+                        node_relax<R, Q, EXT>(d, p, m);
+#pragma unroll
+                        for (int a = 0; a < Q; ++a) f[a][k] = S::from_raw(d[a]);
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    VecN<T, V> o;
+#pragma unroll
+                    for (int k = 0; k < V; ++k) o.e[k] = f[a][k];
+                    *reinterpret_cast<typename RawVec<sizeof(T) * V>::type*>(dst + (long long)a * g.sq + base) = o.raw;
                 }
             }
-#pragma unroll
-            for (int a = 0; a < Q; ++a) {
-                VecN<T, V> o;
-#pragma unroll
-                for (int k = 0; k < V; ++k) o.e[k] = f[a][k];
-                *reinterpret_cast<typename RawVec<sizeof(T) * V>::type*>(dst + (long long)a * g.sq + base) = o.raw;
-            }
-        }
-        put_v();
-        return;
-    }
-    // chunk with a solid neighbour or padding: node by node
-    for (int k = 0; k < V; ++k) {
-        const int x = x0 + k;
-        const uint8_t c = cls[base + k];
-        if (x >= g.nx || nc_solid(c) || c == NC_PAD) {
-#pragma unroll
-            for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + base + k] = S::from_raw(R(0));
-            continue;
-        }
-        R d[Q];
-        gather_node<Q, S, true>(src, cls, g, p, x, y, z, d);
-        NodeM<R> m;
-        node_macro<R, Q, EXT>(d, p, m);
-        node_relax<R, Q, EXT>(d, p, m);
-        add_v(m);
-        if constexpr (SR) {
-            NodeRng rng((uint32_t)(base + k), seed);
-#pragma unroll
-            for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + base + k] = S::from_raw_sr(d[a], rng.bits(a));
         } else {
+            // chunk with a solid neighbour or padding: node by node
+            for (int k = 0; k < V; ++k) {
+                const int x = x0 + k;
+                const uint8_t c = cls[base + k];
+                if (x >= g.nx || nc_solid(c) || c == NC_PAD) {
 #pragma unroll
-            for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + base + k] = S::from_raw(d[a]);
+                    for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + base + k] = S::from_raw(R(0));
+                    continue;
+                }
+                R d[Q];
+                gather_node<Q, S, true>(src, cls, g, p, x, y, z, d);
+                NodeM<R> m;
+                node_macro<R, Q, EXT>(d, p, m);
+                node_relax<R, Q, EXT>(d, p, m);
+                add_v(m);
+                if constexpr (SR) {
+                    NodeRng rng((uint32_t)(base + k), seed);
+#pragma unroll
+                    for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + base + k] = S::from_raw_sr(d[a], rng.bits(a));
+                } else {
+#pragma unroll
+                    for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + base + k] = S::from_raw(d[a]);
+                }
+            }
         }
     }
     put_v();
@@ -918,7 +931,7 @@ k_stress(const typename S::T* __restrict__ cur, const typename S::T* __restrict_
 // with the node's flow velocity v, the fluid with the Maxwell term of
 // Eq. (10) at B.  Both write their post-collision values for the next pull.
 template <int Q, class S, bool SR>
-__global__ void __launch_bounds__(NODE_THREADS)
+__global__ void __launch_bounds__(NODE_THREADS, MhdOcc<S>::value)
 k_mhd_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
            const typename S::R* __restrict__ G, typename S::R* __restrict__ Gn, const uint8_t* __restrict__ cls,
            const Geo g, const KP<typename S::R> p, uint32_t seed)
@@ -939,7 +952,28 @@ k_mhd_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ ds
         return;
     }
     R gm[3][QM];
-    mag_gather<Q>(G, cls, g, p, x, y, z, n, gm);
+    R d[Q];
+    if (c == NC_BULK) {
+        // every pull source is a fluid node (periodic wrap allowed): plain
+        // indexed loads, no class bytes
+        int ro[3][3];
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dz = -1; dz <= 1; ++dz)
+                ro[dy + 1][dz + 1] = (wrapi(z - dz, g.nz) * g.ny + wrapi(y - dy, g.ny)) * g.nxp;
+        const int xm = wrapi(x - 1, g.nx), xp = wrapi(x + 1, g.nx);
+        auto at = [&](int a) { return ro[EY<Q>(a) + 1][EZ<Q>(a) + 1] + (EX<Q>(a) == 0 ? x : (EX<Q>(a) == 1 ? xm : xp)); };
+#pragma unroll
+        for (int a = 0; a < Q; ++a) d[a] = S::to_raw(src[(long long)a * g.sq + at(a)]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int i = 0; i < QM; ++i) gm[k][i] = G[(long long)(k * QM + i) * g.sq + at(i)];
+    } else {
+        mag_gather<Q>(G, cls, g, p, x, y, z, n, gm);
+        gather_node<Q, S, true>(src, cls, g, p, x, y, z, d);
+    }
     NodeM<R> m;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -948,8 +982,6 @@ k_mhd_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ ds
         for (int i = 0; i < QM; ++i) b += gm[k][i];
         m.Bl[k] = b;
     }
-    R d[Q];
-    gather_node<Q, S, true>(src, cls, g, p, x, y, z, d);
     node_macro<R, Q, true>(d, p, m);
     // field: e_i is +-1 along one axis, so e_i . (v B_k - B v_k) = s (v_ax B_k - B_ax v_k)
     const R om = p.om_m, ith = R(1.0 / MagLat<Q>::TH);

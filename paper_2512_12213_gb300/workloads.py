@@ -11,6 +11,8 @@ from __future__ import annotations
 
 import math
 
+import numpy as np
+
 from . import inputs
 
 
@@ -86,6 +88,40 @@ def sphere(nx=256, ny=128, nz=128, radius=12, Re=20, model="e", storage="f16s", 
     cfg = dict(lattice=19, nx=nx, ny=ny, nz=nz, periodic=(1, 1, 1), tau=p["tau"], force_model=model,
                g=(p["g"], 0.0, 0.0), storage=storage, wall_u=((0, 0, 0),))
     return cfg, inputs.sphere_mask(nx, ny, nz, center, radius)
+
+
+def sphere_curved(radius=12.4, storage="f32", center=(64.0, 64.0, 64.0), **kw):
+    """The sphere box with the true sphere as wall: solid where
+    |x - c| < radius, signed distance phi = |x - c| - radius (> 0 in fluid)
+    for interpolated bounce-back.  Returns (cfg, mask, phi)."""
+    cfg, _ = sphere(storage=storage, center=center, **kw)
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    d = np.sqrt((x - center[0]) ** 2 + (y - center[1]) ** 2 + (z - center[2]) ** 2)
+    phi = (d - radius).astype(np.float32)
+    mask = (phi < 0).astype(np.uint8)
+    return dict(cfg, curved=1), mask, phi
+
+
+def sphere_insulating(B0=0.02, sigma_e=1.0, storage="f32", **kw):
+    """The sphere box in a transverse imposed field (0, B0, 0) with the
+    low-Rm Lorentz force and the zero-net-current field E = -<v> x B."""
+    cfg, mask = sphere(storage=storage, **kw)
+    return dict(cfg, lorentz=1, B=(0.0, B0, 0.0), sigma_e=sigma_e, insulating=1), mask
+
+
+def sphere_brinkman(darcy=1e-4, storage="f32", **kw):
+    """The sphere box with the linear (Stokes) equilibrium and a Darcy
+    resistance (Brinkman flow through a porous medium around the sphere)."""
+    cfg, mask = sphere(storage=storage, **kw)
+    return dict(cfg, stokes=1, darcy=darcy), mask
+
+
+def sphere_induced(B0=0.02, eta=0.05, storage="f32", **kw):
+    """The sphere box in an external field (0, B0, 0) with the induced field
+    on the D3Q7 field lattice, coupled through the Maxwell equilibrium."""
+    cfg, mask = sphere(storage=storage, **kw)
+    return dict(cfg, B=(0.0, B0, 0.0), maxwell=1, mu=1.0, induced=1, eta=eta), mask
 
 
 def cavity(n=128, lid=0.1, tau=0.55, cs=0.1, storage="f32", model="e"):

@@ -113,16 +113,19 @@ def test_stochastic_rounding_only_for_16_bit(lib):
 
 
 def test_insulating_walls_scratch(lib):
-    """Insulating walls add a field block and one row of 3 doubles per step
-    thread (FP64: 2 nodes per thread, else 4) to the scratch buffer."""
-    cfg, mask = workloads.hartmann_insulating(nx=100, ny=40)
+    """Insulating walls add a field block and one row of 3 doubles per warp
+    of the step grid (blocks of 128 threads; a thread takes 2 nodes in FP64,
+    else 4) to the scratch buffer."""
+    cfg, mask = workloads.hartmann_insulating(nx=100, ny=400)
     plain = lbm.lbm_buffer_sizes(lbm.make_config(**dict(cfg, insulating=0)), mask)
     ins = lbm.lbm_buffer_sizes(lbm.make_config(**cfg), mask)
-    threads = (128 // 2) * 40
-    assert ins[lbm.BUF_SCRATCH] >= plain[lbm.BUF_SCRATCH] + 3 * 8 * threads
+    warps = -(-(128 // 2) * 400 // 128) * 4
+    assert ins[lbm.BUF_SCRATCH] >= plain[lbm.BUF_SCRATCH] + 3 * 8 * warps
+    assert ins[lbm.BUF_SCRATCH] < plain[lbm.BUF_SCRATCH] + 3 * 8 * (warps + 1024 + 16) + 512
     assert ins[lbm.BUF_POP_A] == plain[lbm.BUF_POP_A]
     ins32 = lbm.lbm_buffer_sizes(lbm.make_config(**dict(cfg, storage="f32")), mask)
-    assert ins[lbm.BUF_SCRATCH] - ins32[lbm.BUF_SCRATCH] >= 3 * 8 * (threads // 2) - 256
+    warps32 = -(-(128 // 4) * 400 // 128) * 4
+    assert ins[lbm.BUF_SCRATCH] - ins32[lbm.BUF_SCRATCH] >= 3 * 8 * (warps - warps32) - 256
 
 
 def test_curved_walls_buffer(lib):
