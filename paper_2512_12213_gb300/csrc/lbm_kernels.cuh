@@ -320,6 +320,8 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
             }
         }
     }
+    // without the EXT node code nothing below needs the lanes past the last chunk
+    if (!EXT && !active) return;
     // insulating walls: this thread's sum of the flow velocity v over the
     // fluid nodes it relaxes, summed over the warp by a fixed shuffle tree in
     // FP64 (every thread of the block reaches it, inactive ones with zero),
