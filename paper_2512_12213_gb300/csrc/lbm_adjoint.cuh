@@ -28,8 +28,10 @@ template <typename R> struct AdjConst {
 // precomputed row offsets and three x positions, without branches; nodes
 // next to a wall or a closed face take the general path.  Gradient terms are
 // summed per thread in the compute precision and per block in FP64.
+// blocks of RED_THREADS per SM: FP32 compute 3 (80 registers, a few dozen
+// bytes of spill; measured 18% faster than 2 blocks at 126 registers), FP64 1
 template <int Q, class S>
-__global__ void __launch_bounds__(RED_THREADS, sizeof(typename S::R) == 8 ? 1 : 2)
+__global__ void __launch_bounds__(RED_THREADS, sizeof(typename S::R) == 8 ? 1 : 3)
 k_adjoint(const typename S::T* __restrict__ Pprev, const typename S::R* __restrict__ phin,
           typename S::R* __restrict__ phio, const uint8_t* __restrict__ cls, const Geo g,
           const KP<typename S::R> p, int target, const AdjConst<typename S::R> ac, double gscale,

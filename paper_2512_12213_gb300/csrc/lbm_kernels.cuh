@@ -523,7 +523,7 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                     continue;
                 }
                 R d[Q];
-                gather_node<Q, S, true>(src, cls, g, p, x, y, z, d);
+                gather_step<Q, S, true>(src, cls, g, p, x, y, z, d);
                 NodeM<R> m;
                 node_macro<R, Q, EXT>(d, p, m);
                 node_relax<R, Q, EXT>(d, p, m);
@@ -974,7 +974,7 @@ k_mhd_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ ds
             for (int i = 0; i < QM; ++i) gm[k][i] = G[(long long)(k * QM + i) * g.sq + at(i)];
     } else {
         mag_gather<Q>(G, cls, g, p, x, y, z, n, gm);
-        gather_node<Q, S, true>(src, cls, g, p, x, y, z, d);
+        gather_node<Q, S, true, false>(src, cls, g, p, x, y, z, d);   // the induced field has no curved walls
     }
     NodeM<R> m;
 #pragma unroll
