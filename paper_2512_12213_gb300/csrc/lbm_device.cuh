@@ -730,34 +730,6 @@ __device__ __forceinline__ void gather_node(const typename S::T* __restrict__ P,
     }
 }
 
-// The gather of a step kernel's boundary path: halfway bounce-back inline;
-// with a wall distance one out-of-line call.  Inlined into every direction,
-// the interpolation made the fused step ~5% slower on halfway geometries.
-template <typename R, int Q> struct Pops {
-    R d[Q];
-};
-template <int Q, class S, bool RAW>
-__device__ __noinline__ Pops<typename S::R, Q> gather_node_curved(const typename S::T* __restrict__ P,
-                                                                   const uint8_t* __restrict__ cls, const Geo& g,
-                                                                   const KP<typename S::R>& p, int x, int y, int z)
-{
-    Pops<typename S::R, Q> o;
-    gather_node<Q, S, RAW, true>(P, cls, g, p, x, y, z, o.d);
-    return o;
-}
-template <int Q, class S, bool RAW>
-__device__ __forceinline__ void gather_step(const typename S::T* __restrict__ P, const uint8_t* __restrict__ cls,
-                                            const Geo& g, const KP<typename S::R>& p, int x, int y, int z,
-                                            typename S::R (&d)[Q])
-{
-    if (g.phi) {
-        const Pops<typename S::R, Q> o = gather_node_curved<Q, S, RAW>(P, cls, g, p, x, y, z);
-#pragma unroll
-        for (int a = 0; a < Q; ++a) d[a] = o.d[a];
-    } else {
-        gather_node<Q, S, RAW, false>(P, cls, g, p, x, y, z, d);
-    }
-}
 
 // ----------------------------------------------------- induced field
 // Field distributions on the axis velocities of the fluid lattice: the
