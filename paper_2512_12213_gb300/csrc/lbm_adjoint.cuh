@@ -28,10 +28,11 @@ template <typename R> struct AdjConst {
 // precomputed row offsets and three x positions, without branches; nodes
 // next to a wall or a closed face take the general path.  Gradient terms are
 // summed per thread in the compute precision and per block in FP64.
-// blocks of RED_THREADS per SM: FP32 compute 3 (80 registers, a few dozen
-// bytes of spill; measured 18% faster than 2 blocks at 126 registers), FP64 1
+// blocks of RED_THREADS per SM: FP64 1; FP32 compute D3Q19 3 (80 registers,
+// a few dozen bytes of spill; 18% faster than 2 blocks at 126 registers on
+// the 128^3 sphere), D2Q9 2 (the 512 x 256 cylinder ran 23% slower at 3)
 template <int Q, class S>
-__global__ void __launch_bounds__(RED_THREADS, sizeof(typename S::R) == 8 ? 1 : 3)
+__global__ void __launch_bounds__(RED_THREADS, sizeof(typename S::R) == 8 ? 1 : (Q == 19 ? 3 : 2))
 k_adjoint(const typename S::T* __restrict__ Pprev, const typename S::R* __restrict__ phin,
           typename S::R* __restrict__ phio, const uint8_t* __restrict__ cls, const Geo g,
           const KP<typename S::R> p, int target, const AdjConst<typename S::R> ac, double gscale,

@@ -120,11 +120,13 @@ template <class S, bool EXT> struct StepOcc {
     static constexpr int value = sizeof(typename S::T) == 8 ? 3 : 4;
 };
 
-// CURVED: the boundary path interpolates at walls off the half-grid (contexts
-// with a wall distance; always with FACES, which also serves periodic boxes).
-// Kept out of the other instantiations: even as one out-of-line call the
-// interpolation cost the fused step ~3%, inlined ~5%.
-template <int Q, class S, bool EXT, bool FACES, bool SR, bool CURVED = false>
+// FULL: the boundary path interpolates at walls off the half-grid and the
+// EXT node code sums the flow velocity for insulating walls (contexts with a
+// wall distance or insulating walls; always with FACES, which also serves
+// periodic boxes).  Kept out of the other instantiations: even as one
+// out-of-line call the interpolation cost the fused step ~3% (inlined ~5%),
+// and the velocity sums cost the LES cavity 8%.
+template <int Q, class S, bool EXT, bool FACES, bool SR, bool FULL = false>
 __global__ void __launch_bounds__(STEP_THREADS, StepOcc<S, EXT>::value)
 k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
        const uint8_t* __restrict__ cls, const Geo g, const KP<typename S::R> p, uint32_t seed)
@@ -324,22 +326,22 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
             }
         }
     }
-    // without the EXT node code nothing below needs the lanes past the last chunk
-    if (!EXT && !active) return;
+    // only the velocity rows of insulating walls need the lanes past the last chunk
+    if (!(EXT && FULL) && !active) return;
     // insulating walls: this thread's sum of the flow velocity v over the
     // fluid nodes it relaxes, summed over the warp by a fixed shuffle tree in
     // FP64 (every thread of the block reaches it, inactive ones with zero),
     // one row per warp for the fixed-order reduction of the field
     R vs[3] = {R(0), R(0), R(0)};
     auto add_v = [&](const NodeM<R>& m) {
-        if constexpr (EXT) {
+        if constexpr (EXT && FULL) {
             vs[0] += m.v[0];
             vs[1] += m.v[1];
             vs[2] += m.v[2];
         }
     };
     auto put_v = [&]() {
-        if constexpr (EXT) {
+        if constexpr (EXT && FULL) {
             if (p.ins_rows) {
                 double t[3] = {(double)vs[0], (double)vs[1], (double)vs[2]};
 #pragma unroll
@@ -527,7 +529,7 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                     continue;
                 }
                 R d[Q];
-                gather_node<Q, S, true, CURVED>(src, cls, g, p, x, y, z, d);
+                gather_node<Q, S, true, FULL>(src, cls, g, p, x, y, z, d);
                 NodeM<R> m;
                 node_macro<R, Q, EXT>(d, p, m);
                 node_relax<R, Q, EXT>(d, p, m);
@@ -1094,7 +1096,7 @@ cudaError_t launch_step_q(const Ctx& c, const void* src, void* dst, uint32_t see
     const long long nch = (long long)(c.geo.nxp / S::V) * c.geo.ny * c.geo.nz;
     const int blocks = grid_for(nch, STEP_THREADS, 1ll << 31);
     const bool faces = !c.geo.periodic[0] || !c.geo.periodic[1] || (Q == 19 && !c.geo.periodic[2]);
-    if (c.cfg.curved)
+    if (c.cfg.curved || c.insulating)
         k_step<Q, S, EXT, true, SR, true><<<blocks, STEP_THREADS, 0, st>>>((const T*)src, (T*)dst, c.cls, c.geo,
                                                                            kp_step_of<S>(c), seed);
     else if (faces)
