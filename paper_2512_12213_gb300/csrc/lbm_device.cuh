@@ -331,8 +331,9 @@ template <typename R> __device__ __forceinline__ void mom_zero(Mom<R>& mo)
 
 // the per-node quantities of the text after Eq. (1) and the per-model
 // choices of C, u^F and u^eq of Sec. 2, from the raw moments; EXT enables
-// the Lorentz force and LES
-template <typename R, int Q, bool EXT>
+// the Lorentz force and LES; INS reads the Lorentz coefficient of insulating
+// walls from the device (kernels that never serve them compile without it)
+template <typename R, int Q, bool EXT, bool INS = true>
 __device__ __forceinline__ void macro_from_moments(const Mom<R>& mo, const KP<R>& p, NodeM<R>& m)
 {
     constexpr int D = LatDim<Q>::D;
@@ -350,7 +351,7 @@ __device__ __forceinline__ void macro_from_moments(const Mom<R>& mo, const KP<R>
         R wv[3], Ag[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const R aeb = p.aeb_dev ? p.aeb_dev[k] : p.AEB[k];
+            const R aeb = (INS && p.aeb_dev) ? p.aeb_dev[k] : p.AEB[k];
             Ag[k] = (k < D) ? p.AG[k] + aeb * ir : R(0);
             wv[k] = m.u[k] + R(0.5) * Ag[k];
         }
@@ -406,7 +407,7 @@ __device__ __forceinline__ void macro_from_moments(const Mom<R>& mo, const KP<R>
 }
 
 // moments and per-node quantities of the populations d[Q]
-template <typename R, int Q, bool EXT>
+template <typename R, int Q, bool EXT, bool INS = true>
 __device__ __forceinline__ void node_macro(const R (&d)[Q], const KP<R>& p, NodeM<R>& m)
 {
     Mom<R> mo;
@@ -418,7 +419,7 @@ __device__ __forceinline__ void node_macro(const R (&d)[Q], const KP<R>& p, Node
 #pragma unroll
         for (int a = 0; a < Q; ++a) mom_add<R, Q, false>(mo, a, d[a]);
     }
-    macro_from_moments<R, Q, EXT>(mo, p, m);
+    macro_from_moments<R, Q, EXT, INS>(mo, p, m);
 }
 
 // what the relaxation of one node needs, compactly

@@ -121,11 +121,11 @@ template <class S, bool EXT> struct StepOcc {
 };
 
 // FULL: the boundary path interpolates at walls off the half-grid and the
-// EXT node code sums the flow velocity for insulating walls (contexts with a
-// wall distance or insulating walls; always with FACES, which also serves
-// periodic boxes).  Kept out of the other instantiations: even as one
+// EXT node code reads the Lorentz coefficient of insulating walls from the
+// device and sums the flow velocity (contexts with a wall distance or
+// insulating walls).  Kept out of the other instantiations: even as one
 // out-of-line call the interpolation cost the fused step ~3% (inlined ~5%),
-// and the velocity sums cost the LES cavity 8%.
+// and the insulating-wall code cost the LES cavity 8%.
 template <int Q, class S, bool EXT, bool FACES, bool SR, bool FULL = false>
 __global__ void __launch_bounds__(STEP_THREADS, StepOcc<S, EXT>::value)
 k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
@@ -436,13 +436,13 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                     }
                     {
                         NodeM<R> m;
-                        node_macro<R, Q, EXT>(d0, p, m);
+                        node_macro<R, Q, EXT, FULL>(d0, p, m);
                         node_relax<R, Q, EXT>(d0, p, m);
                         add_v(m);
                     }
                     {
                         NodeM<R> m;
-                        node_macro<R, Q, EXT>(d1, p, m);
+                        node_macro<R, Q, EXT, FULL>(d1, p, m);
                         node_relax<R, Q, EXT>(d1, p, m);
                         add_v(m);
                     }
@@ -472,7 +472,7 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                         for (int a = 0; a < Q; ++a) d[a] = S::to_raw(f[a][0]);
                         if (ladd) add_ladd(d, k);
                         NodeM<R> m;
-                        node_macro<R, Q, EXT>(d, p, m);
+                        node_macro<R, Q, EXT, FULL>(d, p, m);
                         node_relax<R, Q, EXT>(d, p, m);
                         add_v(m);
 #pragma unroll
@@ -504,7 +504,7 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                         for (int a = 0; a < Q; ++a) d[a] = S::to_raw(f[a][k]);
                         if (ladd) add_ladd(d, k);
                         NodeM<R> m;
-                        node_macro<R, Q, EXT>(d, p, m);
+                        node_macro<R, Q, EXT, FULL>(d, p, m);
                         node_relax<R, Q, EXT>(d, p, m);
 #pragma unroll
                         for (int a = 0; a < Q; ++a) f[a][k] = S::from_raw(d[a]);
@@ -531,7 +531,7 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                 R d[Q];
                 gather_node<Q, S, true, FULL>(src, cls, g, p, x, y, z, d);
                 NodeM<R> m;
-                node_macro<R, Q, EXT>(d, p, m);
+                node_macro<R, Q, EXT, FULL>(d, p, m);
                 node_relax<R, Q, EXT>(d, p, m);
                 add_v(m);
                 if constexpr (SR) {
@@ -1096,9 +1096,12 @@ cudaError_t launch_step_q(const Ctx& c, const void* src, void* dst, uint32_t see
     const long long nch = (long long)(c.geo.nxp / S::V) * c.geo.ny * c.geo.nz;
     const int blocks = grid_for(nch, STEP_THREADS, 1ll << 31);
     const bool faces = !c.geo.periodic[0] || !c.geo.periodic[1] || (Q == 19 && !c.geo.periodic[2]);
-    if (c.cfg.curved || c.insulating)
+    if ((c.cfg.curved || c.insulating) && faces)
         k_step<Q, S, EXT, true, SR, true><<<blocks, STEP_THREADS, 0, st>>>((const T*)src, (T*)dst, c.cls, c.geo,
                                                                            kp_step_of<S>(c), seed);
+    else if (c.cfg.curved || c.insulating)
+        k_step<Q, S, EXT, false, SR, true><<<blocks, STEP_THREADS, 0, st>>>((const T*)src, (T*)dst, c.cls, c.geo,
+                                                                            kp_step_of<S>(c), seed);
     else if (faces)
         k_step<Q, S, EXT, true, SR><<<blocks, STEP_THREADS, 0, st>>>((const T*)src, (T*)dst, c.cls, c.geo,
                                                                      kp_step_of<S>(c), seed);
