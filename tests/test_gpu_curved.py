@@ -146,3 +146,25 @@ def test_offgrid_channel_second_order(storage):
     yy = np.arange(1, ny - 1)
     exact = g / (2 * nu) * (yy - yw_lo) * (yw_hi - yy)
     assert _rel(vx, exact) < 5e-4
+
+
+@pytest.mark.parametrize("name,storage,model", [
+    ("sphere", "f64", "e"), ("random", "f64", "d"), ("sphere", "f32", "e"), ("random", "f16s", "e")])
+def test_curved_with_insulating_walls_against_oracle(orc, name, storage, model):
+    """Interpolated walls together with insulating walls (the Lorentz force
+    with E = -<v> x B set after every step, Eq. 36): the step kernel's
+    instantiation that carries both, in a periodic box (sphere) and with
+    closed faces (random)."""
+    cfg, mask, phi = _case(name, storage, model)
+    cfg = dict(cfg, lorentz=1, B=(0.02, 0.09, 0.04), E=(1e-4, 0.0, -2e-4), sigma_e=0.8, insulating=1)
+    ocfg, f0 = _start(orc, cfg, mask, phi)
+    sim = lbm.Sim(cfg, mask)
+    sim.set_wall_distance(phi)
+    sim.import_f(f0)
+    steps = 12
+    sim.step(steps)
+    f_ref, E_ref = orc.run_e(ocfg, mask, f0, steps)
+    tol = {"f64": 1e-12, "f32": 2e-6, "f16s": 1e-4}[storage]
+    assert _rel(sim.export_f().cpu().numpy(), f_ref) < tol
+    assert _rel(sim.electric_field(), E_ref) < (1e-11 if storage == "f64" else 50 * tol)
+    assert _rel(E_ref, cfg["E"]) > 1e-3

@@ -587,3 +587,48 @@ def test_induced_field_total_conserved_by_conducting_walls(orc):
             assert drift < 1e-14 * nx * ny * nz
         else:
             assert drift > 1e-6
+
+
+@pytest.mark.parametrize("q", [9, 19])
+def test_induced_field_equilibrium_moments_and_relaxation(orc, q):
+    """On a one-node periodic box propagation maps every field population to
+    itself, so one step is g1 = g0 - (g0 - g^eq)/tau_m.  Recovering g^eq with
+    tau_m = 1/2 + eta/(theta c^2 dt) must give the moments of Dellar's vector
+    equilibrium (Sec. 4): sum_i g^eq_ik = B_k, sum_i e_il g^eq_ik =
+    (v_l B_k - B_l v_k)/c and sum_i e_il e_im g^eq_ik = theta delta_lm B_k,
+    with v the node's flow velocity (no body force: v = u).  The field
+    directions are the rest and axis directions of the fluid lattice, in the
+    fluid lattice's order (D2Q5: 0, +x, +y, -x, -y; D3Q7: 0, +-x, +-y, +-z)."""
+    dx, dt = 0.5, 0.2
+    c = dx / dt
+    eta = 0.07
+    if q == 9:
+        e = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [-1, 0, 0], [0, -1, 0]])
+        theta, dims = 1 / 3, 2
+        B = np.array([0.03, -0.05, 0.0])
+        u = c * np.array([0.02, -0.013, 0.0])
+    else:
+        e = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]])
+        theta, dims = 1 / 4, 3
+        B = np.array([0.03, -0.05, 0.02])
+        u = c * np.array([0.02, -0.013, 0.017])
+    cfg = orc.make_cfg(q=q, nx=1, ny=1, nz=1, periodic=(1, 1, 1), dx=dx, dt=dt, tau=0.8, force_model="e",
+                       B=tuple(B), maxwell=1, mu=1.0, induced=1, eta=eta, wall_u=((0, 0, 0),))
+    mask = np.zeros((1, 1, 1), np.uint8)
+    f0 = orc.init(cfg, mask, np.full((1, 1, 1), 1.02), u.reshape(3, 1, 1, 1))
+    g0 = orc.mag_init(cfg, mask)
+    _, g1, _ = orc.run_mhd(cfg, mask, f0, g0, 1)
+    om = 1 / (0.5 + eta / (theta * c * c * dt))
+    geq = (g0 - (g0 - g1) / om)[:, :, 0, 0, 0]          # [k][i]
+    assert np.allclose(geq.sum(axis=1), B, rtol=0, atol=1e-15)
+    for l in range(dims):
+        first = (e[:, l][None, :] * geq).sum(axis=1)
+        want = (u[l] * B - B[l] * u) / c
+        assert np.allclose(first, want, rtol=0, atol=1e-15), l
+        for m in range(dims):
+            second = (e[:, l][None, :] * e[:, m][None, :] * geq).sum(axis=1)
+            assert np.allclose(second, theta * (l == m) * B, rtol=0, atol=1e-15), (l, m)
+    # a wrong relaxation time would leave a spurious part: the recovered
+    # equilibrium with 1.05 tau_m misses the moments
+    bad = (g0 - (g0 - g1) * (0.5 + eta / (theta * c * c * dt)) * 1.05)[:, :, 0, 0, 0]
+    assert np.abs(sum((e[:, 0][None, :] * bad).sum(axis=1)) - sum((u[0] * B - B[0] * u) / c)) > 1e-6
