@@ -306,6 +306,7 @@ def run_ours(args):
         out["storage_variants"] = variants
         out["drag_error_vs_f64"] = drag_errors(torch, lbm, workloads, args.drag_steps)
         out["cavity_les_f32"] = cavity_bench(torch, lbm, workloads, hbm, args)
+        out["cavity_sweep"] = cavity_sweep(torch, lbm, workloads, hbm, args)
         out["extensions_f32"] = extensions_bench(torch, lbm, workloads, hbm, args)
         out["adjoint"] = adjoint_bench(torch, lbm, workloads, hbm)
         e2e = e2e_bench(torch, lbm, workloads, args)
@@ -402,6 +403,36 @@ def cavity_bench(torch, lbm, workloads, hbm, args):
     return {"workload": "D3Q19 lid-driven cavity 256^3, lid u=0.1, tau=0.55, Smagorinsky Cs=0.1, FP32",
             "mlups": round(N * steps / (t * 1e-3) / 1e6, 1), "kernel_mlups": round(N / (k * 1e-3) / 1e6, 1),
             "achieved_gbs": round(ach, 1), "frac": round(ach / hbm, 4), "steps": steps}
+
+
+def cavity_sweep(torch, lbm, workloads, hbm, args, sizes=(128, 256, 512), steps=20):
+    """The LES lid-driven cavity (lid u = 0.1, tau = 0.55, Cs = 0.1) at 128^3,
+    256^3 and 512^3 in FP64, FP32 and FP32 compute with binary16 storage
+    (stochastic rounding): mean step-kernel rate and achieved HBM bandwidth
+    against the measured peak.  Initial state from device tensors (no host
+    staging buffer for the 512^3 boxes)."""
+    res = {}
+    for n in sizes:
+        row = {}
+        for storage in ("f64", "f32", "f16s"):
+            c, m = workloads.cavity(n=n, storage=storage)
+            if storage == "f16s":
+                c = dict(c, rounding="stochastic", seed=2024)
+            s = lbm.Sim(c, m, stage=False)
+            N = n ** 3
+            s.init_equilibrium(torch.full((n, n, n), 1.0, dtype=torch.float64, device=s.device),
+                               torch.zeros((3, n, n, n), dtype=torch.float64, device=s.device))
+            t, k = timed_run(torch, lbm, s, steps, 3, wall=2)
+            bp = bytes_per_node(19, storage)
+            ach = N * bp / (k * 1e-3) / 1e9
+            row[storage] = {"mlups": round(N * steps / (t * 1e-3) / 1e6, 1),
+                            "kernel_mlups": round(N / (k * 1e-3) / 1e6, 1),
+                            "achieved_gbs": round(ach, 1), "frac": round(ach / hbm, 4)}
+            s.close()
+            del s
+            torch.cuda.empty_cache()
+        res[f"{n}^3"] = row
+    return res
 
 
 def extensions_bench(torch, lbm, workloads, hbm, args):
