@@ -161,9 +161,9 @@ def bytes_per_node(Q, storage, induced=False):
 # the sphere box with each extension of the core step: workload builder,
 # step kernel(s) timed, and a description
 EXTENSIONS = {
-    "curved": ("sphere_curved", "k_step<19,S,EXT=0> (interpolated bounce-back in boundary chunks)",
+    "curved": ("sphere_curved", "k_step<19,S,EXT=0,FULL=1> (interpolated bounce-back in boundary chunks)",
                "true sphere r=12.4 as the wall, linear interpolated bounce-back from the signed distance"),
-    "insulating": ("sphere_insulating", "k_step<19,S,EXT=1> + k_ins_rows + k_reduce_rows + k_ins_field",
+    "insulating": ("sphere_insulating", "k_step<19,S,EXT=1,FULL=1> + k_ins_update",
                    "imposed field (0, 0.02, 0), sigma_e = 1, Lorentz force, insulating walls E = -<v> x B"),
     "brinkman": ("sphere_brinkman", "k_step<19,S,EXT=1>",
                  "linear (Stokes) equilibrium, Darcy resistance 1e-4 (Brinkman)"),
