@@ -163,3 +163,26 @@ def test_induced_field_buffers(lib):
                      (dict(mag_conducting=3), "mag_conducting")):
         with pytest.raises(lbm.LbmError, match=msg):
             lbm.lbm_buffer_sizes(lbm.make_config(**dict(cfg, **bad)), mask)
+
+
+def test_bench_workloads_are_valid_configurations(lib):
+    """Every workload bench.py times (the headline sphere, the LES cavity and
+    the four extension rows) passes the library's configuration checks, and
+    the algorithmic bytes per node it reports match the buffers: two
+    population buffers per step, plus the two field buffers of the induced
+    field."""
+    import bench
+    for name in ["sphere", "cavity"] + list(bench.EXTENSIONS):
+        cfg, mask, phi = bench.make_workload(workloads, name, "f32")
+        sizes = lbm.lbm_buffer_sizes(lbm.make_config(**cfg), mask)
+        if phi is not None:
+            assert phi.shape == mask.shape and np.array_equal(phi < 0, mask > 0)
+        nodes = cfg["nx"] * cfg["ny"] * cfg["nz"]
+        pitch = -(-cfg["nx"] // 64) * 64
+        padded = pitch * cfg["ny"] * cfg["nz"]
+        bpn = bench.bytes_per_node(19, "f32", induced=bool(cfg.get("induced")))
+        stream = 2 * 19 * 4 + 1 + (2 * 3 * 7 * 4 if cfg.get("induced") else 0)
+        assert bpn == stream, name
+        moved = sizes[lbm.BUF_POP_A] + sizes[lbm.BUF_POP_B] + sizes[lbm.BUF_MAG_A] + sizes[lbm.BUF_MAG_B]
+        assert moved >= (bpn - 1) * padded
+        assert nodes <= padded
