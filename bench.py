@@ -64,6 +64,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(torch, dist, ws, value, device):
+    """The largest of every rank's value (the slowest replica's time); the
+    value itself on one rank.  Barrier first, so no rank reads a time that
+    another rank has not finished."""
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(ws, nodes, steps, total_ms):
+    """Node updates of all replicas per second (weak scaling: every rank
+    advances its own box of `nodes` nodes `steps` times), in millions."""
+    return ws * nodes * steps / (total_ms * 1e-3) / 1e6
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -259,13 +276,9 @@ def run_ours(args):
     clocks.active = True
     total_ms, kern_ms = timed_run(torch, lbm, sim, args.steps, args.warmup, wall=hwall)
     clocks.active = False
-    tmax = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.barrier()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    total_ms = float(tmax.item())
+    total_ms = max_over_ranks(torch, dist, ws, total_ms, "cuda")
     ms_step = total_ms / args.steps
-    value = ws * N * args.steps / (total_ms * 1e-3) / 1e6
+    value = whole_job_mlups(ws, N, args.steps, total_ms)
     achieved = N * bpn / (kern_ms * 1e-3) / 1e9
     kname = {"f64": "StoreF64", "f32": "StoreF32", "f16s": "StoreF16", "bf16s": "StoreBF16"}[args.storage]
     kernel = (EXTENSIONS[args.workload][1].replace(",S", "," + kname) if args.workload in EXTENSIONS
