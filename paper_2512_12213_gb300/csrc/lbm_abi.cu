@@ -610,6 +610,7 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
         return LBM_ERR_CUDA;
     }
     choose_tile(x);
+    x.adj_blocks = 0;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(x.cls, cls.data(), cls.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && x.n_links)

@@ -205,9 +205,18 @@ cudaError_t launch_adjoint(const Ctx& c, const void* Pprev, const void* phin, vo
 {
     using T = typename S::T;
     using R = typename S::R;
-    // a fixed grid per context, so every block owns the same partial row each step
+    // a fixed grid per context, so every block owns the same partial row each
+    // step: the blocks resident at once (SMs x occupancy), each walking the
+    // nodes with the grid stride, so no partly filled last wave
     const long long NP = (long long)c.geo.nxp * c.geo.ny * c.geo.nz;
-    const int blocks = grid_for(NP, RED_THREADS, ADJ_BLOCKS);
+    if (c.adj_blocks == 0) {
+        int occ = 0;
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint<Q, S>, RED_THREADS, 0);
+        if (e != cudaSuccess) return e;
+        c.adj_blocks = (int)std::min<long long>(grid_for(NP, RED_THREADS, ADJ_BLOCKS),
+                                                 (long long)std::max(occ, 1) * c.sm_count);
+    }
+    const int blocks = std::min(c.adj_blocks, ADJ_BLOCKS);
     const KP<R>& p = kp_of<S>(c);
     const KP<double>& pd = c.kpd;
     AdjConst<R> ac;

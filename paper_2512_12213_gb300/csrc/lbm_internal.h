@@ -137,6 +137,7 @@ struct Ctx {
     int tile_ntiles;
     size_t tile_smem;
     mutable int tile_blocks;
+    mutable int adj_blocks;  // grid of the adjoint kernel (0: not yet sized)
     unsigned* errflag;
     // curved walls: the wall ids of the geometry (host), to check distances
     std::vector<uint8_t> host_wid;
