@@ -186,3 +186,39 @@ def test_bench_workloads_are_valid_configurations(lib):
         moved = sizes[lbm.BUF_POP_A] + sizes[lbm.BUF_POP_B] + sizes[lbm.BUF_MAG_A] + sizes[lbm.BUF_MAG_B]
         assert moved >= (bpn - 1) * padded
         assert nodes <= padded
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/lbm.h is a C header: a C99 translation unit that takes the
+    address of every declared entry point and fills a configuration compiles
+    with gcc -std=c99 -Wall -Wextra -pedantic -Werror, and links against liblbm.so (no GPU is
+    touched: nothing is called)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    hdr = open(os.path.join(root, "include", "lbm.h")).read()
+    names = sorted(set(re.findall(r"^(?:lbm_status|const char\*)\s+(lbm_\w+)\(", hdr, re.M)))
+    assert "lbm_step" in names and "lbm_export_field" in names
+    src = ['#include <stdio.h>', '#include "lbm.h"', 'int main(void) {',
+           '    lbm_config c = {0};', '    c.lattice = LBM_D3Q19; c.nx = c.ny = c.nz = 4; c.tau = 0.8;',
+           '    c.induced = 0; c.eta = 0.0; c.storage = LBM_STORE_F16S;',
+           '    size_t sizes[LBM_NUM_BUFFERS]; (void)sizes;',
+           '    void (*fns[])(void) = {']
+    src += ['        (void (*)(void))&%s,' % n for n in names]
+    src += ['    };', '    printf("%d %d\\n", (int)(sizeof fns / sizeof fns[0]), c.lattice);', '    return 0;', '}']
+    cfile = tmp_path / "abi.c"
+    cfile.write_text("\n".join(src) + "\n")
+    obj = tmp_path / "abi.o"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                        os.path.join(root, "include"), "-c", str(cfile), "-o", str(obj)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    so = lbm.LIB_PATH
+    if not os.path.exists(so):
+        pytest.skip("liblbm.so not built")
+    exe = tmp_path / "abi"
+    r = subprocess.run([gcc, str(obj), so, "-o", str(exe), "-Wl,-rpath," + os.path.dirname(so)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
