@@ -23,7 +23,8 @@ rank, ws = dist.get_rank(), dist.get_world_size()
 mine = [120.0, 150.0][rank]            # this rank's timed milliseconds
 tmax = bench.max_over_ranks(torch, dist, ws, mine, "cpu")
 rate = bench.whole_job_mlups(ws, 1000, 10, tmax)
-print(json.dumps({"rank": rank, "tmax": tmax, "rate": rate}), flush=True)
+with open(os.path.join(sys.argv[2], "rank%d.json" % rank), "w") as fh:
+    json.dump({"rank": rank, "tmax": tmax, "rate": rate}, fh)
 dist.destroy_process_group()
 '''
 
@@ -38,9 +39,9 @@ def _torchrun(args, timeout=240):
 def test_max_over_ranks_and_whole_job_rate(tmp_path):
     w = tmp_path / "worker.py"
     w.write_text(WORKER)
-    r = _torchrun([str(w), ROOT])
+    r = _torchrun([str(w), ROOT, str(tmp_path)])
     assert r.returncode == 0, r.stderr[-2000:]
-    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    lines = [json.load(open(tmp_path / ("rank%d.json" % k))) for k in (0, 1)]
     assert sorted(x["rank"] for x in lines) == [0, 1]
     for x in lines:
         assert x["tmax"] == 150.0                       # the slower rank's time on both ranks
