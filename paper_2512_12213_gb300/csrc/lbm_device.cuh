@@ -627,6 +627,141 @@ __device__ __forceinline__ void pair_collide(F2 (&d)[Q], const KP<float>& p)
     }
 }
 
+// The EXT node code (Lorentz force and Darcy resistance in the implicit
+// flow velocity, Smagorinsky LES, the Maxwell term of Eq. 10, the linear
+// equilibrium) for two nodes at once: the arithmetic of macro_from_moments
+// and node_relax lane by lane, with the per-node relaxation rate as a pair;
+// square roots and reciprocals per lane in IEEE FP32.  Not for insulating
+// walls (their coefficient lives on the device) or the induced field.
+__device__ __forceinline__ F2 f2rcp(F2 a) { return F2{make_float2(__frcp_rn(a.v.x), __frcp_rn(a.v.y))}; }
+__device__ __forceinline__ F2 f2sqrt(F2 a) { return F2{make_float2(__fsqrt_rn(a.v.x), __fsqrt_rn(a.v.y))}; }
+
+template <int Q>
+__device__ __forceinline__ void pair_collide_ext(F2 (&d)[Q], const KP<float>& p)
+{
+    constexpr int D = LatDim<Q>::D, NP = LatDim<Q>::NP;
+    // raw moments: sum d, sum E d and (LES) sum E_i E_j d
+    F2 drho = d[0];
+    F2 j[3] = {f2s(0.0f), f2s(0.0f), f2s(0.0f)};
+    F2 P[6] = {f2s(0.0f), f2s(0.0f), f2s(0.0f), f2s(0.0f), f2s(0.0f), f2s(0.0f)};
+    const bool les = p.les != 0;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const int a = PAIR<Q>(k), b = OPP<Q>(a);
+        const F2 sm = f2add(d[a], d[b]), df = f2sub(d[a], d[b]);
+        drho = f2add(drho, sm);
+        const int e[3] = {EX<Q>(a), EY<Q>(a), EZ<Q>(a)};
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (e[c]) j[c] = (e[c] > 0) ? f2add(j[c], df) : f2sub(j[c], df);
+        if (les) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                if (e[c]) P[c] = f2add(P[c], sm);
+            if (e[0] * e[1]) P[3] = (e[0] * e[1] > 0) ? f2add(P[3], sm) : f2sub(P[3], sm);
+            if (e[0] * e[2]) P[4] = (e[0] * e[2] > 0) ? f2add(P[4], sm) : f2sub(P[4], sm);
+            if (e[1] * e[2]) P[5] = (e[1] * e[2] > 0) ? f2add(P[5], sm) : f2sub(P[5], sm);
+        }
+    }
+    const F2 rho = f2add(f2s(p.rho0), drho);
+    const F2 ir = f2rcp(rho);
+    F2 u[3], A[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        u[c] = (c < D) ? f2mul(j[c], ir) : f2s(0.0f);
+        A[c] = f2s((c < D) ? p.AG[c] : 0.0f);
+    }
+    if (p.lorentz || p.darcy_h != 0.0f) {
+        // (1 + h + k B^2) v - k B_p (B_p . v) = w, k = kappa/(2 rho)
+        F2 wv[3], Ag[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Ag[c] = (c < D) ? f2fma(f2s(p.AEB[c]), ir, f2s(p.AG[c])) : f2s(0.0f);
+            wv[c] = f2fma(f2s(0.5f), Ag[c], u[c]);
+        }
+        const F2 kk = f2mul(f2s(0.5f * p.kappa), ir);
+        F2 Bw = f2mul(f2s(p.B[0]), wv[0]);
+        Bw = f2fma(f2s(p.B[1]), wv[1], Bw);
+        if (D == 3) Bw = f2fma(f2s(p.B[2]), wv[2], Bw);
+        const float al = 1.0f + p.darcy_h;
+        const F2 den = f2rcp(f2fma(kk, f2s(p.B2), f2s(al)));
+        const F2 sB = f2mul(f2mul(kk, Bw), f2rcp(f2fma(kk, f2s(p.B2 - p.Bp2), f2s(al))));
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const F2 vk = f2mul(f2fma(sB, f2s(p.B[c]), wv[c]), den);
+            A[c] = f2mul(f2s(2.0f), f2sub(vk, u[c]));
+        }
+    }
+    F2 v[3], weq[3];
+    const bool model_e = (p.model == MODEL_E);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        v[c] = f2fma(f2s(0.5f), A[c], u[c]);
+        weq[c] = model_e ? v[c] : u[c];
+    }
+    F2 tau = f2s(p.tau0), om = f2s(p.om0);
+    if (les) {
+        F2 PP = f2s(0.0f);
+        const F2 dr3 = f2mul(drho, f2s(1.0f / 3.0f));
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const int i = (c < 3) ? c : (c == 5 ? 1 : 0);
+            const int jj = (c < 3) ? c : (c == 3 ? 1 : 2);
+            if (D == 2 && (i == 2 || jj == 2)) continue;
+            F2 Pc = P[c];
+            if (!p.stokes) Pc = f2sub(Pc, f2mul(rho, f2mul(weq[i], weq[jj])));
+            if (p.maxwell) Pc = f2sub(Pc, f2s(p.Lh[c]));
+            if (i == jj) Pc = f2sub(Pc, dr3);
+            PP = f2fma(f2s(i == jj ? 1.0f : 2.0f), f2mul(Pc, Pc), PP);
+        }
+        const F2 inner = f2fma(f2mul(f2s(p.lesc), f2sqrt(f2mul(f2s(2.0f), PP))), ir, f2s(p.tau0 * p.tau0));
+        tau = f2mul(f2s(0.5f), f2add(f2s(p.tau0), f2sqrt(inner)));
+        om = f2rcp(tau);
+    }
+    const F2 C = model_e ? f2fma(f2s(-0.5f), om, f2s(1.0f)) : f2s(1.0f);
+    F2 wf[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        switch (p.model) {
+        case MODEL_A: wf[c] = f2s(0.0f); break;
+        case MODEL_B: wf[c] = u[c]; break;
+        case MODEL_C: wf[c] = f2fma(f2mul(f2s(0.5f), tau), A[c], u[c]); break;
+        default: wf[c] = v[c]; break;
+        }
+    }
+    // Eq. (2) with the equilibrium of Eq. (1) (+ Eq. 10) and the force of Eq. (3)
+    const F2 om1 = f2sub(f2s(1.0f), om), Crho = f2mul(C, rho);
+    F2 usq = f2s(0.0f), fa = f2s(0.0f);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        usq = f2fma(weq[c], weq[c], usq);
+        fa = f2fma(wf[c], A[c], fa);
+    }
+    if (p.stokes) usq = f2s(0.0f);
+    // base = om (drho - 3/2 rho u^eq.u^eq) - 3 C rho u^F.A
+    const F2 base = f2fma(om, f2fma(rho, f2mul(usq, f2s(-1.5f)), drho), f2mul(Crho, f2mul(fa, f2s(-3.0f))));
+    {
+        F2 r0 = f2fma(f2s((float)WD<Q>(0)), base, f2mul(om1, d[0]));
+        if (p.maxwell) r0 = f2fma(om, f2s(p.mx[0]), r0);
+        d[0] = r0;
+    }
+    const F2 k1 = p.stokes ? f2s(0.0f) : f2mul(f2mul(f2s(4.5f), om), rho);
+    const F2 k2 = f2mul(f2s(9.0f), Crho), kl = f2mul(f2mul(f2s(3.0f), om), rho), kf = f2mul(f2s(3.0f), Crho);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const int a = PAIR<Q>(k), b = OPP<Q>(a);
+        const float w = (float)WD<Q>(a);
+        const F2 t = f2dot<Q>(a, weq), ea = f2dot<Q>(a, A), ef = f2dot<Q>(a, wf);
+        F2 ps = f2fma(k1, f2mul(t, t), base);
+        ps = f2fma(k2, f2mul(ef, ea), ps);
+        ps = f2mul(f2s(w), ps);
+        if (p.maxwell) ps = f2fma(om, f2s(p.mx[a]), ps);
+        const F2 pa = f2mul(f2s(w), f2fma(kl, t, f2mul(kf, ea)));
+        d[a] = f2fma(om1, d[a], f2add(ps, pa));
+        d[b] = f2fma(om1, d[b], f2sub(ps, pa));
+    }
+}
+
 // -------------------------------------------------------- addressing helpers
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 

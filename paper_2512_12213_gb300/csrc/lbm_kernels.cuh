@@ -116,8 +116,11 @@ __device__ __forceinline__ bool row_out(const FaceInfo& fi, int a, int& wall)
 // blocks of 128 threads per SM the register allocation must allow: FP64 3
 // (168 registers), else 4 (128; for 16-bit storage measured faster than 5
 // blocks at 96 registers, which spill with the FP32x2 node pairs)
-template <class S, bool EXT> struct StepOcc {
-    static constexpr int value = sizeof(typename S::T) == 8 ? 3 : 4;
+// (the EXT node code in FP32x2 node pairs, 32-bit storage with closed faces:
+// 3, where it needs 158 registers without spill)
+template <class S, bool EXT, bool FACES = false, bool FULL = false> struct StepOcc {
+    static constexpr bool PAIRX = EXT && !FULL && FACES && sizeof(typename S::T) == 4;
+    static constexpr int value = (sizeof(typename S::T) == 8 || PAIRX) ? 3 : 4;
 };
 
 // FULL: the boundary path interpolates at walls off the half-grid and the
@@ -127,7 +130,7 @@ template <class S, bool EXT> struct StepOcc {
 // out-of-line call the interpolation cost the fused step ~3% (inlined ~5%),
 // and the insulating-wall code cost the LES cavity 8%.
 template <int Q, class S, bool EXT, bool FACES, bool SR, bool FULL = false>
-__global__ void __launch_bounds__(STEP_THREADS, StepOcc<S, EXT>::value)
+__global__ void __launch_bounds__(STEP_THREADS, StepOcc<S, EXT, FACES, FULL>::value)
 k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
        const uint8_t* __restrict__ cls, const Geo g, const KP<typename S::R> p, uint32_t seed)
 {
@@ -391,17 +394,22 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
         // two nodes at a time in packed FP32x2 arithmetic (FP32 compute without
         // the Lorentz force, Maxwell term or LES)
         constexpr bool PAIR2 = !EXT && sizeof(R) == 4;
+    // the EXT node code in node pairs too: FP32 storage with closed faces (the
+    // LES cavity 24.7k -> 26.6k MLUPS); measured slower for 16-bit storage
+    // (-3.7%) and periodic FP32 boxes (-2.5%, spills), which keep the scalar code
+    constexpr bool PAIRX = StepOcc<S, EXT, FACES, FULL>::PAIRX;
 
         const long long base = row * g.nxp + x0;
         if (!special) {
-            if constexpr (PACKED && PAIR2) {
+            if constexpr (PACKED && (PAIR2 || PAIRX)) {
 #pragma unroll
                 for (int i = 0; i < V / 2; ++i) {
                     F2 dd[Q];
 #pragma unroll
                     for (int a = 0; a < Q; ++a) dd[a] = F2{S::unpack2(w[a][i])};
                     if (ladd) add_ladd2(dd, 2 * i);
-                    pair_collide<Q>(dd, p);
+                    if constexpr (PAIR2) pair_collide<Q>(dd, p);
+                    else pair_collide_ext<Q>(dd, p);
                     if constexpr (SR) {
                         NodeRng rp((uint32_t)(base + 2 * i), seed);     // the pair's first node
 #pragma unroll
@@ -463,7 +471,24 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                     *reinterpret_cast<typename RawVec<sizeof(T) * V>::type*>(dst + (long long)a * g.sq + base) = o.raw;
                 }
             } else {
-                if constexpr (EXT) {
+                if constexpr (PAIRX) {
+                    // the EXT node code in node pairs, as a rolled queue of pairs
+#pragma unroll 1
+                    for (int k = 0; k < V / 2; ++k) {
+                        F2 dd[Q];
+#pragma unroll
+                        for (int a = 0; a < Q; ++a) dd[a] = F2{make_float2(S::to_raw(f[a][0]), S::to_raw(f[a][1]))};
+                        if (ladd) add_ladd2(dd, 2 * k);
+                        pair_collide_ext<Q>(dd, p);
+#pragma unroll
+                        for (int a = 0; a < Q; ++a) {
+#pragma unroll
+                            for (int j = 0; j < V - 2; ++j) f[a][j] = f[a][j + 2];
+                            f[a][V - 2] = S::from_raw(dd[a].v.x);
+                            f[a][V - 1] = S::from_raw(dd[a].v.y);
+                        }
+                    }
+                } else if constexpr (EXT) {
                     // larger node code (Lorentz / Maxwell / LES): the same rolled queue
 #pragma unroll 1
                     for (int k = 0; k < V; ++k) {
