@@ -632,3 +632,43 @@ def test_induced_field_equilibrium_moments_and_relaxation(orc, q):
     # equilibrium with 1.05 tau_m misses the moments
     bad = (g0 - (g0 - g1) * (0.5 + eta / (theta * c * c * dt)) * 1.05)[:, :, 0, 0, 0]
     assert np.abs(sum((e[:, 0][None, :] * bad).sum(axis=1)) - sum((u[0] * B - B[0] * u) / c)) > 1e-6
+
+
+@pytest.mark.parametrize("q,model,conducting", [(9, "e", 0), (9, "c", 1), (19, "d", 0), (19, "e", 1)])
+def test_induced_field_momentum_balance_every_step(orc, q, model, conducting):
+    """The Maxwell term of Eq. (10) at the node's induced field carries no
+    momentum, so every coupled fluid/field step changes the fluid momentum by
+    the body force less what the walls take: the momentum exchange of
+    Eq. (25) (no corrections) equals sum rho a - (M(t+1) - M(t))/dt to
+    rounding (Eq. 32 per step), with moving walls, scattered solids, closed
+    faces, non-unit dx and dt, and the field evolving with either wall rule."""
+    if q == 9:
+        nx, ny, nz, per = 12, 9, 1, (1, 0, 1)
+        B = (0.12, 0.2, 0.0)
+    else:
+        nx, ny, nz, per = 7, 6, 5, (1, 0, 0)
+        B = (0.1, 0.25, -0.05)
+    mask = inputs.random_solids(nx, ny, nz, 0.12, n_walls=2, seed=21 + q)
+    cfg = orc.make_cfg(q=q, nx=nx, ny=ny, nz=nz, periodic=per, dx=0.5, dt=0.2, tau=0.81,
+                       force_model=model, g=(3e-2, -1e-2, 5e-3 if q == 19 else 0.0), B=B, maxwell=1, mu=1.3,
+                       induced=1, eta=0.06, mag_conducting=conducting,
+                       wall_u=((0.01, 0.02, -0.01), (0.0, -0.015, 0.02), (0.03, 0, 0)),
+                       face_wall=(3, 3, 3, 2, 1, 3))
+    c = cfg.dx / cfg.dt
+    D = 2 if q == 9 else 3
+    rho, u = inputs.smooth_fields(nx, ny, nz, dims=D, seed=8)
+    f = orc.init(cfg, mask, rho, u * 0.5 * c, inputs.noise(q, nx, ny, nz, 1e-2, seed=9))
+    g = orc.mag_init(cfg, mask)
+    B0 = orc.mag_field(cfg, mask, g)
+    for _ in range(4):
+        _, M0, rhoa = orc.balance(cfg, mask, f)
+        fn, gn, fr = orc.run_mhd(cfg, mask, f, g, 1)
+        _, M1, _ = orc.balance(cfg, mask, fn)
+        F = orc.wall_force(cfg, mask, fr, fn, -1, 0)
+        ref = rhoa - (M1 - M0) / cfg.dt
+        scale = np.abs(M0).max() / cfg.dt + np.abs(F).max()
+        # rounding of sums over every node and direction: N Q 2^-52 of the scale
+        assert np.allclose(F, ref, rtol=0, atol=nx * ny * nz * q * 2.0 ** -52 * scale), (F, ref)
+        f, g = fn, gn
+    # the field did evolve (the Maxwell term was not the uniform one)
+    assert np.abs(orc.mag_field(cfg, mask, g) - B0).max() > 1e-6
