@@ -121,7 +121,8 @@ enum {
     LBM_BUF_SCRATCH = 4,      /* FP64 reduction partials (required) */
     LBM_BUF_STAGE = 5,        /* canonical staging for host import/export (optional) */
     LBM_BUF_PHI = 6,          /* signed wall distance per node, float (required if curved) */
-    LBM_BUF_MAG_A = 7,        /* induced-field distributions, ping (required if induced) */
+    LBM_BUF_MAG_A = 7,        /* induced-field distributions, ping (required if induced):
+                                 [3][5 or 7][padded node], FP64 for FP64 storage, else FP32 */
     LBM_BUF_MAG_B = 8,        /* induced-field distributions, pong (required if induced) */
     LBM_NUM_BUFFERS = 9
 };
@@ -294,9 +295,12 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, int64_t t, void* stream
  * effect for the next step and every later call; synchronises the stream. */
 lbm_status lbm_set_wall_distance(lbm_ctx* ctx, const float* phi_host, void* stream);
 
-/* The induced field B(x, T) of an induced-field context: B[3][N] doubles,
- * canonical node order (zero at solid nodes), device or host memory
- * (on_host != 0: synchronises; needs the STAGE buffer). */
+/* The induced field B(x, T) of an induced-field context (the sums of the
+ * field distributions pulled to each node, Sec. 4): B[3][N] doubles owned by
+ * the caller, canonical node order (zero at solid nodes), device memory or,
+ * with on_host != 0, host memory through the STAGE buffer (synchronises).
+ * LBM_ERR_ARG if B is NULL, the context was created without induced = 1, or
+ * host output lacks the STAGE buffer. */
 lbm_status lbm_export_field(lbm_ctx* ctx, double* B, int on_host, void* stream);
 
 /* Current time T. */
