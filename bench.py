@@ -92,7 +92,7 @@ def peaks():
 
 # sources that compile into the step kernel (host code, the adjoint and the
 # allocation-free wall force are left out)
-STEP_SOURCES = ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_tile.cuh", "lbm_internal.h",
+STEP_SOURCES = ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_internal.h",
                 "inst_f64.cu", "inst_f32.cu", "inst_f16.cu", "inst_bf16.cu")
 
 

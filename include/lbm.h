@@ -338,9 +338,10 @@ lbm_status lbm_wall_force(lbm_ctx* ctx, int wall, unsigned flags, double weight,
 
 /* lbm_wall_force_noalloc -- the paper has no counterpart; this is a service
  * of the library.  It returns exactly what lbm_wall_force returns (same
- * arguments, same reduction order), but it asks for no device memory: its
+ * arguments; the same launch shape and reduction order, so the results are
+ * bit-identical at every link count), but it asks for no device memory: its
  * block partial sums and its result slot live in a fixed static device array
- * inside the library (98,368 bytes, held by every GPU that loads the library
+ * inside the library (24,640 bytes, held by every GPU that loads the library
  * until the process exits), not in the context's scratch buffer.
  * It is for callers that cannot allocate device memory when they need a
  * force -- their memory is fully committed to population arrays, or is owned
@@ -351,7 +352,10 @@ lbm_status lbm_wall_force(lbm_ctx* ctx, int wall, unsigned flags, double weight,
  *   - at most 1,048,576 links per call (wall < 0 counts every link); larger
  *     requests return LBM_ERR_ARG with a message naming the limit;
  *   - the first call on a device looks up the array's device address (once
- *     per device); make that first call before any stream capture;
+ *     per device) and keeps it for the life of the process; make that first
+ *     call before any stream capture.  A device reset (cudaDeviceReset, or
+ *     the primary context destroyed and created again) invalidates the kept
+ *     address: after one, do not call this entry point again in the process;
  *   - all calls share the one array, which keeps the last call's contents
  *     (each call overwrites what it reads, so nothing needs clearing): calls
  *     that overlap on the GPU -- on different streams, from different

@@ -12,7 +12,6 @@
 #include <vector>
 
 #include "lbm_internal.h"
-#include "lbm_tile.cuh"
 
 using namespace lbm;
 
@@ -371,36 +370,6 @@ void fill_params(Ctx& x)
     bind_insulating(x);
 }
 
-// shape of the shared-memory staged step: R rows per tile so that each of
-// the consumer warps gets one row segment (64 nodes for FP64, 128 otherwise),
-// 2..4 stages within about 100 KB; tile_R = 0 when two one-row stages do not
-// fit in shared memory (the register-tiled kernel is used then)
-void choose_tile(Ctx& x)
-{
-    const size_t Q = x.cfg.lattice, nxp = x.geo.nxp;
-    const size_t per_row = Q * nxp * x.elem + nxp;
-    const size_t seg = (x.elem == 8) ? 64 : 128;
-    const size_t nseg = (nxp + seg - 1) / seg;
-    int R = (int)std::max<size_t>(1, (TILE_CWARPS + nseg - 1) / nseg);
-    R = std::min(R, x.cfg.ny);
-    auto stage_of = [&](int r) { return (per_row * r + 127) / 128 * 128; };
-    auto smem_for = [&](int r, int n) { return n * stage_of(r) + 2 * n * sizeof(uint64_t); };
-    while (R > 1 && smem_for(R, 2) > (size_t)x.smem_optin) --R;
-    int ns = (int)std::min<size_t>(4, std::max<size_t>(2, 102400 / stage_of(R)));
-    while (ns > 2 && smem_for(R, ns) > (size_t)x.smem_optin) --ns;
-    // LBM_STEP_KERNEL=tile selects the shared-memory staged step where it fits;
-    // the register-tiled step is the default
-    const char* sel = getenv("LBM_STEP_KERNEL");
-    const bool want_tile = sel && strcmp(sel, "tile") == 0 && x.cfg.rounding == LBM_ROUND_NEAREST && !x.insulating &&
-                           !x.cfg.curved && !x.cfg.stokes && !(x.cfg.darcy > 0.0) && !x.cfg.induced;
-    const bool fits = want_tile && smem_for(R, ns) <= (size_t)x.smem_optin;
-    x.tile_R = fits ? R : 0;
-    x.tile_stages = fits ? ns : 0;
-    x.tile_smem = fits ? smem_for(R, ns) : 0;
-    x.tile_ntiles = fits ? ((x.cfg.ny + R - 1) / R) * x.cfg.nz : 0;
-    x.tile_blocks = 0;
-}
-
 // signed wall distance in the padded layout: the given canonical values, or
 // +-1/2 (halfway bounce-back) when phi is null; padding gets 0
 std::vector<float> padded_distance(const Ctx& x, const float* phi)
@@ -609,7 +578,6 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
         delete h;
         return LBM_ERR_CUDA;
     }
-    choose_tile(x);
     x.adj_blocks = 0;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(x.cls, cls.data(), cls.size(), cudaMemcpyHostToDevice, st);

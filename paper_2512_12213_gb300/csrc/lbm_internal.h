@@ -129,14 +129,8 @@ struct Ctx {
     int64_t t;
     bool prev_valid;
     std::string err;
-    // shared-memory tiled step (tile_R = 0: rows too long, register kernel)
     int sm_count;
     int smem_optin;
-    int tile_R;
-    int tile_stages;
-    int tile_ntiles;
-    size_t tile_smem;
-    mutable int tile_blocks;
     mutable int adj_blocks;  // grid of the adjoint kernel (0: not yet sized)
     unsigned* errflag;
     // curved walls: the wall ids of the geometry (host), to check distances

@@ -8,7 +8,6 @@
 
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
-#include "lbm_tile.cuh"
 
 namespace lbm {
 
@@ -1136,30 +1135,9 @@ cudaError_t launch_step_q(const Ctx& c, const void* src, void* dst, uint32_t see
     return cudaGetLastError();
 }
 
-template <int Q, class S, bool EXT>
-cudaError_t launch_step_tile(const Ctx& c, const void* src, void* dst, cudaStream_t st)
-{
-    using T = typename S::T;
-    auto kern = k_step_tile<Q, S, EXT>;
-    if (c.tile_blocks == 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem_optin);
-        if (e != cudaSuccess) return e;
-        int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE_THREADS, c.tile_smem);
-        if (e != cudaSuccess) return e;
-        if (occ < 1) return cudaErrorInvalidConfiguration;
-        c.tile_blocks = (int)std::min<long long>((long long)c.sm_count * occ, c.tile_ntiles);
-    }
-    kern<<<c.tile_blocks, TILE_THREADS, c.tile_smem, st>>>((const T*)src, (T*)dst, c.cls, c.geo, kp_step_of<S>(c),
-                                                            c.tile_R, c.tile_ntiles, c.tile_stages, c.errflag);
-    return cudaGetLastError();
-}
-
 template <int Q, class S>
 cudaError_t launch_step(const Ctx& c, const void* src, void* dst, uint32_t seed, cudaStream_t st)
 {
-    if (c.tile_R > 0)
-        return c.ext ? launch_step_tile<Q, S, true>(c, src, dst, st) : launch_step_tile<Q, S, false>(c, src, dst, st);
     if constexpr (sizeof(typename S::T) == 2) {
         if (c.sr)
             return c.ext ? launch_step_q<Q, S, true, true>(c, src, dst, seed, st)

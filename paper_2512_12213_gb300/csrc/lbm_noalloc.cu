@@ -13,8 +13,11 @@
 //
 // How: the block partial sums and the result slot live in one file-scope
 // static device array of fixed size, which every GPU that loads this library
-// holds until the process exits.  One thread block handles 256 links, so one
-// call can take at most NOALLOC_ROWS * 256 links; larger requests are refused.
+// holds until the process exits.  The launch has exactly the shape of
+// lbm_wall_force's (at most MAX_PARTIAL_ROWS blocks of RED_THREADS threads,
+// each thread striding over the links), so the two add the same terms in the
+// same order and agree bit for bit at every link count.  One call takes at
+// most NOALLOC_MAX_LINKS links; larger requests are refused.
 #include <cstdio>
 #include <mutex>
 #include <string>
@@ -23,11 +26,11 @@
 
 namespace {
 
-constexpr int NOALLOC_ROWS = 4096;                                   // block partial rows
-constexpr long long NOALLOC_MAX_LINKS = (long long)NOALLOC_ROWS * lbm::RED_THREADS;   // 1,048,576
+constexpr int NOALLOC_ROWS = lbm::MAX_PARTIAL_ROWS;                 // block partial rows (1024)
+constexpr long long NOALLOC_MAX_LINKS = 1ll << 20;                  // 1,048,576 links per call
 constexpr int NOALLOC_RESULT = NOALLOC_ROWS * 3;                     // offset of the 3-double result slot
 
-// 4096 x 3 partial sums + one result slot: 98,368 bytes per device
+// 1024 x 3 partial sums + one result slot: 24,640 bytes per device
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_ROWS * 3 + 8];
 
 constexpr int MAX_DEVICES = 64;
@@ -129,9 +132,11 @@ extern "C" lbm_status lbm_wall_force_noalloc(lbm_ctx* ctx, int wall, unsigned fl
     if (!scratch_address(x.device, &scratch, x.err)) {
         status = LBM_ERR_CUDA;
     } else {
-        // every partial row and the result slot are written before they are
-        // read, so nothing in the array needs clearing between calls
-        const int rows = (int)((e - b + RED_THREADS - 1) / RED_THREADS);
+        // the grid of lbm_wall_force (launch_links): the same blocks, the same
+        // per-thread strides, the same partial rows.  Every partial row and
+        // the result slot are written before they are read, so nothing in the
+        // array needs clearing between calls
+        const int rows = (e > b) ? grid_for(e - b, RED_THREADS, NOALLOC_ROWS) : 0;
         if (rows > 0) {
             switch (x.cfg.storage) {
             case LBM_STORE_F64: ce = links_rows<StoreF64>(x, x.pop[x.cur], b, e, flags & 3u, scratch, rows, st); break;

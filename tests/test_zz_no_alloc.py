@@ -3,9 +3,10 @@
 The entry point serves callers that cannot allocate device memory when they
 need a force: its partial sums live in a static array inside the library
 instead of a caller buffer.  Its results must equal those of lbm_wall_force
-(same reduction order) on consecutive calls, for host and device outputs,
-every wall and every flag, and it must refuse requests beyond its fixed
-capacity.  This file is collected last on purpose.
+(same launch shape and reduction order) on consecutive calls, for host and
+device outputs, every wall and every flag, at link counts that fit one pass
+of the reduction grid and at counts where every thread sums several links,
+and it must refuse requests beyond its fixed capacity.  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -50,6 +51,38 @@ def test_noalloc_matches_wall_force(storage):
     _compare(sim, [1, 2, 3, -1], [0, lbm.MOVING_CORR, lbm.MAXWELL_REMOVE, 3])
     sim.step(3)
     _compare(sim, [1, -1], [0])
+
+
+def test_noalloc_matches_wall_force_on_a_capped_grid():
+    # 3 * 100,000 = 300,000 links on the bottom wall: more links than one
+    # pass of the 1024-block grid covers, so every thread of both entry
+    # points sums several links; the results must still agree bit for bit
+    nx = 100_000
+    cfg, mask = workloads.poiseuille(nx=nx, ny=4, storage="f32")
+    cfg = dict(cfg, wall_u=((0.01, 0, 0), (0, 0, 0)))
+    sim = lbm.Sim(cfg, mask)
+    rho, u = inputs.smooth_fields(nx, 4, 1, dims=2, u_amplitude=0.03, seed=3)
+    sim.init_equilibrium(rho, u)
+    sim.step(2)
+    n1 = sim.link_count(1)
+    assert 262_144 < n1 <= 1_048_576
+    st = sim.stream
+    for flags in (0, lbm.MOVING_CORR):
+        ref = np.zeros(3)
+        lbm.lbm_wall_force(sim.ctx, 1, flags, 1.0, ref, 1, st)
+        for _ in range(2):
+            got = np.zeros(3)
+            lbm.lbm_wall_force_noalloc(sim.ctx, 1, flags, 1.0, got, 1, st)
+            assert np.array_equal(got, ref), (flags, got, ref)
+        ref_dev = torch.zeros(3, dtype=torch.float64, device=sim.device)
+        got_dev = torch.zeros(3, dtype=torch.float64, device=sim.device)
+        lbm.lbm_wall_force(sim.ctx, 1, flags, 0.25, ref_dev, 0, st)
+        lbm.lbm_wall_force_noalloc(sim.ctx, 1, flags, 0.25, got_dev, 0, st)
+        assert torch.equal(got_dev, ref_dev)
+        for _ in range(2):
+            lbm.lbm_wall_force(sim.ctx, 1, flags | lbm.ACCUMULATE, 0.5, ref_dev, 0, st)
+            lbm.lbm_wall_force_noalloc(sim.ctx, 1, flags | lbm.ACCUMULATE, 0.5, got_dev, 0, st)
+        assert torch.equal(got_dev, ref_dev)
 
 
 def test_noalloc_refuses_more_links_than_it_holds():
