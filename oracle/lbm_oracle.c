@@ -673,6 +673,45 @@ void orc_balance(const orc_cfg* c, const unsigned char* wid, const double* f, do
     }
 }
 
+/* Steady-state residual (Sec. 6: the global balance of Eq. 32 between wall
+ * force and body force holds once the flow no longer changes).  At every
+ * fluid node the flow velocity v = u + dt a/2 of the canonical state f (text
+ * after Eq. 1) is compared with a reference velocity field vref of an earlier
+ * time:
+ *   out[0] = sum_x |v(x) - vref(x)|,  out[1] = sum_x |v(x)|,
+ *   out[2] = out[0] / out[1]  (0 when out[1] = 0),
+ * with |.| the Euclidean norm and the sums over fluid nodes in node order.
+ * vref: [3][N] (NULL: zero); v (may be NULL) receives v [3][N], 0 at solids. */
+void orc_residual(const orc_cfg* c, const unsigned char* wid, const double* f, const double* vref,
+                  double* v, double* out)
+{
+    lat_t L;
+    get_lat(c->q, &L);
+    const long N = nnodes(c);
+    out[0] = out[1] = out[2] = 0.0;
+    for (long n = 0; n < N; ++n) {
+        if (wid[n] != 0) {
+            if (v)
+                for (int k = 0; k < 3; ++k) v[k * N + n] = 0.0;
+            continue;
+        }
+        double fl[19];
+        for (int a = 0; a < L.q; ++a) fl[a] = f[a * N + n];
+        macro_t_r m;
+        macro_r(c, &L, fl, c->g, &m);
+        double dd = 0.0, vv = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            const double r = vref ? vref[k * N + n] : 0.0;
+            dd += (m.v[k] - r) * (m.v[k] - r);
+            vv += m.v[k] * m.v[k];
+            if (v) v[k * N + n] = m.v[k];
+        }
+        out[0] += sqrt(dd);
+        out[1] += sqrt(vv);
+    }
+    out[2] = out[1] > 0.0 ? out[0] / out[1] : 0.0;
+}
+
 /* forward run for the drag functional; stores f(t) for t < T if hist != NULL */
 static double drag_forward(const orc_cfg* c, const lat_t* L, const unsigned char* wid,
                            const double* f0, int T, int wall, const double* d, double* hist)

@@ -172,6 +172,14 @@ void orc_stress(const orc_cfg* c, const unsigned char* wall_id, const double* f,
  * out[0] mass, out[1..3] momentum sum_x sum_a e f, out[4..6] sum rho a */
 void orc_balance(const orc_cfg* c, const unsigned char* wall_id, const double* f, double* out);
 
+/* steady-state residual (Sec. 6): with v the flow velocity v = u + dt a/2 of
+ * the canonical state f at each fluid node and vref [3][N] the velocity of an
+ * earlier time (NULL: zero), out[0] = sum |v - vref|, out[1] = sum |v|,
+ * out[2] = out[0]/out[1] (0 if out[1] = 0), Euclidean norms, fluid nodes
+ * only; v [3][N] (may be NULL) receives the velocity, 0 at solid nodes */
+void orc_residual(const orc_cfg* c, const unsigned char* wall_id, const double* f,
+                  const double* vref, double* v, double* out);
+
 /* time-averaged drag J = (1/T) sum_{t=0}^{T-1} d . F_wall(t) (uncorrected
  * momentum exchange on wall `wall`) from the canonical initial state f0, and
  * its gradient with respect to theta = (g[0..2], u_w[0..2] of `wall`), by the

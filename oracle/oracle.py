@@ -97,6 +97,7 @@ def lib():
             "orc_count_links": (ctypes.c_long, [cp, ub, ctypes.c_int]),
             "orc_stress": (None, [cp, ub, dp, dp, dp, ctypes.c_int, dp, dp, dp, dp]),
             "orc_balance": (None, [cp, ub, dp, dp]),
+            "orc_residual": (None, [cp, ub, dp, dp, dp, dp]),
             "orc_adjoint_drag": (ctypes.c_int, [cp, ub, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp]),
             "orc_drag_average": (d, [cp, ub, dp, ctypes.c_int, ctypes.c_int, dp]),
         }
@@ -304,6 +305,18 @@ def balance(cfg, wall_id, f):
     out = np.zeros(7)
     lib().orc_balance(ctypes.byref(cfg), _ub(_u8(wall_id)), _dp(_f64(f)), _dp(out))
     return out[0], out[1:4].copy(), out[4:7].copy()
+
+
+def residual(cfg, wall_id, f, vref=None):
+    """Steady-state residual of the canonical state f against the velocity
+    field vref (3, nz, ny, nx) of an earlier time (None: zero).  Returns
+    (sum |v - vref|, sum |v|, r, v) with v the flow velocity (3, nz, ny, nx)."""
+    out = np.zeros(3)
+    v = np.zeros((3, cfg.nz, cfg.ny, cfg.nx))
+    vr = _f64(vref) if vref is not None else None
+    lib().orc_residual(ctypes.byref(cfg), _ub(_u8(wall_id)), _dp(_f64(f)),
+                       _dp(vr) if vr is not None else None, _dp(v), _dp(out))
+    return float(out[0]), float(out[1]), float(out[2]), v
 
 
 def adjoint_drag(cfg, wall_id, f0, T, wall, d=(1.0, 0.0, 0.0)):
