@@ -78,8 +78,11 @@ typedef enum lbm_status {
     LBM_ERR_CUDA = 2,         /* a CUDA runtime call failed */
     LBM_ERR_OOM = 3,          /* a host allocation failed */
     LBM_ERR_UNSUPPORTED = 4,  /* valid request that this build does not implement */
-    LBM_ERR_NAN = 5,          /* non-finite values found */
-    LBM_ERR_STATE = 6         /* call not valid in the context's current state */
+    LBM_ERR_NAN = 5,          /* a reduction read back to the host is not finite (the
+                                 values are still written); device and asynchronous
+                                 outputs are not checked */
+    LBM_ERR_STATE = 6,        /* call not valid in the context's current state */
+    LBM_ERR_NOT_CONVERGED = 7 /* lbm_run_steady reached its step limit first */
 } lbm_status;
 
 enum { LBM_D2Q9 = 9, LBM_D3Q19 = 19 };
@@ -366,6 +369,32 @@ lbm_status lbm_wall_force_noalloc(lbm_ctx* ctx, int wall, unsigned flags, double
 /* FP64 sums over fluid nodes of the canonical state f(T), times dx^D:
  * out[0] mass, out[1..3] momentum sum e f, out[4..6] body force sum rho a. */
 lbm_status lbm_balance(lbm_ctx* ctx, double* out, int out_on_host, void* stream);
+
+/* Steady-state residual.  Sec. 6 balances the wall force against the body
+ * force on the fluid (Eq. 32); the steady form holds once the flow stops
+ * changing, which this measures.  With v(x) = u + dt a/2 the flow velocity of
+ * the canonical state f(T) at each fluid node (text after Eq. 1; moments
+ * summed in FP64 from the stored populations) and v_ref the velocity field of
+ * an earlier time:
+ *   out[0] = sum |v - v_ref|, out[1] = sum |v|, out[2] = out[0]/out[1]
+ * (Euclidean norms, fluid nodes, FP64 block sums in a fixed order; out[2] = 0
+ * if out[1] = 0).  v_ref: caller-owned device array of 3*nx*ny*nz doubles,
+ * canonical layout v[k][n], 8-byte aligned; with update != 0 each node's
+ * v(T) replaces its entries after they are read (solid nodes get 0), so
+ * consecutive calls measure the change between them.  out: 3 doubles placed
+ * as out_on_host says; LBM_OUT_HOST returns LBM_ERR_NAN for a non-finite
+ * result. */
+lbm_status lbm_residual(lbm_ctx* ctx, double* v_ref, int update, double* out, int out_on_host, void* stream);
+
+/* Advance until steady: take the residual of the current state into v_ref,
+ * then repeat { lbm_step(every); lbm_residual(update) } until the residual
+ * over `every` steps is <= tol (LBM_OK) or max_steps steps have been taken
+ * (LBM_ERR_NOT_CONVERGED); a non-finite residual stops with LBM_ERR_NAN.
+ * v_ref as for lbm_residual; *r_out (may be NULL) receives the last residual
+ * and *steps_out (may be NULL) the steps taken.  Synchronises the stream once
+ * per `every` steps. */
+lbm_status lbm_run_steady(lbm_ctx* ctx, int every, double tol, int64_t max_steps, double* v_ref, double* r_out,
+                          int64_t* steps_out, void* stream);
 
 /* Discrete adjoint of J = (1/T) sum_{t<T} d . F_wall(t) (uncorrected momentum
  * exchange on `wall`) for theta = (g, u_w of `wall`), one reverse step t:

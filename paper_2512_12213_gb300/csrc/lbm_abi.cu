@@ -450,7 +450,15 @@ lbm_status finish_reduce(Ctx& x, const double* partials, int nb, int W, double* 
     double tmp[8];
     CK(cudaMemcpyAsync(tmp, slot, sizeof(double) * W, cudaMemcpyDeviceToHost, st), "copy result");
     CK(cudaStreamSynchronize(st), "synchronize");
-    for (int k = 0; k < W; ++k) out[k] = accumulate ? out[k] + tmp[k] : tmp[k];
+    bool finite = true;
+    for (int k = 0; k < W; ++k) {
+        out[k] = accumulate ? out[k] + tmp[k] : tmp[k];
+        finite = finite && std::isfinite(tmp[k]);
+    }
+    if (!finite) {
+        x.err = "the reduction is not finite (the state holds NaN or Inf values)";
+        return LBM_ERR_NAN;
+    }
     return LBM_OK;
 }
 
@@ -923,6 +931,72 @@ lbm_status lbm_balance(lbm_ctx* ctx, double* out, int out_on_host, void* stream)
     return finish_reduce(x, part, nb, 7, out, out_on_host, 1.0, false, st);
 }
 
+lbm_status lbm_residual(lbm_ctx* ctx, double* v_ref, int update, double* out, int out_on_host, void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (!out || !v_ref) return arg_fail(x, "out and v_ref are required");
+    if (((uintptr_t)v_ref) % 8) return arg_fail(x, "v_ref must be 8-byte aligned");
+    GUARD(x);
+    if (!out_mode_ok(out_on_host, false, out, x.err)) return LBM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    double* part = x.scratch + SCRATCH_RED_OFF;
+    int nb = 0;
+    CK(x.ops->residual(x, x.pop[x.cur], v_ref, update ? 1 : 0, part, &nb, st), "residual kernel");
+    if (out_on_host == LBM_OUT_HOST) {
+        double sums[2] = {0.0, 0.0};
+        const lbm_status s = finish_reduce(x, part, nb, 2, sums, LBM_OUT_HOST, 1.0, false, st);
+        out[0] = sums[0];
+        out[1] = sums[1];
+        out[2] = sums[1] > 0.0 ? sums[0] / sums[1] : 0.0;
+        if (s == LBM_OK && !std::isfinite(out[2])) {
+            x.err = "the residual is not finite";
+            return LBM_ERR_NAN;
+        }
+        return s;
+    }
+    // device or page-locked host output: the two sums and their ratio in the
+    // result slot, copied in stream order (HOST_ASYNC) or written to out
+    double* slot = (out_on_host == LBM_OUT_DEVICE) ? out : x.scratch + SCRATCH_OUT_OFF;
+    CK(launch_reduce_rows(part, nb, 2, slot, 1.0, 0, st), "reduce");
+    CK(launch_ratio(slot, st), "ratio");
+    if (out_on_host == LBM_OUT_HOST_ASYNC)
+        CK(cudaMemcpyAsync(out, slot, 3 * sizeof(double), cudaMemcpyDeviceToHost, st), "copy result");
+    return LBM_OK;
+}
+
+lbm_status lbm_run_steady(lbm_ctx* ctx, int every, double tol, int64_t max_steps, double* v_ref, double* r_out,
+                          int64_t* steps_out, void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (every < 1 || !(tol >= 0.0) || max_steps < 0 || !v_ref) return arg_fail(x, "every >= 1, tol >= 0, max_steps >= 0 and v_ref are required");
+    double out[3];
+    int64_t taken = 0;
+    if (steps_out) *steps_out = 0;
+    // the reference field of the starting state
+    lbm_status s = lbm_residual(ctx, v_ref, 1, out, LBM_OUT_HOST, stream);
+    if (s != LBM_OK) return s;
+    double r = -1.0;
+    while (taken < max_steps) {
+        const int n = (int)std::min<int64_t>(every, max_steps - taken);
+        s = lbm_step(ctx, n, stream);
+        if (s != LBM_OK) return s;
+        taken += n;
+        s = lbm_residual(ctx, v_ref, 1, out, LBM_OUT_HOST, stream);
+        if (steps_out) *steps_out = taken;
+        if (s != LBM_OK) return s;
+        r = out[2];
+        if (r_out) *r_out = r;
+        if (n == every && r <= tol) return LBM_OK;
+    }
+    char buf[160];
+    snprintf(buf, sizeof buf, "not steady after %lld steps: residual %.3e over %d steps > %.3e", (long long)taken, r,
+             every, tol);
+    x.err = buf;
+    return LBM_ERR_NOT_CONVERGED;
+}
+
 lbm_status lbm_adjoint_buffer_bytes(const lbm_ctx* ctx, size_t* bytes)
 {
     if (!ctx || !bytes) return LBM_ERR_ARG;
@@ -1074,6 +1148,17 @@ __global__ void k_ins_reset(double* blk, double E0, double E1, double E2, double
     af[0] = f0; af[1] = f1; af[2] = f2;
     as[0] = s0; as[1] = s1; as[2] = s2;
     *reinterpret_cast<unsigned*>(blk + INS_TICKET) = 0u;
+}
+
+__global__ void k_ratio(double* out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) out[2] = out[1] > 0.0 ? out[0] / out[1] : 0.0;
+}
+
+cudaError_t launch_ratio(double* out, cudaStream_t st)
+{
+    k_ratio<<<1, 32, 0, st>>>(out);
+    return cudaGetLastError();
 }
 
 __global__ void k_zero(double* p, long long n)

@@ -79,6 +79,8 @@ struct Dispatch {
     cudaError_t (*links)(const Ctx&, const void* P, long long begin, long long end, unsigned flags,
                          double* partials, int* nblocks, cudaStream_t);
     cudaError_t (*balance)(const Ctx&, const void* P, double* partials, int* nblocks, cudaStream_t);
+    cudaError_t (*residual)(const Ctx&, const void* P, double* vref, int update, double* partials, int* nblocks,
+                            cudaStream_t);
     cudaError_t (*stress)(const Ctx&, const void* cur, const void* prev, int variant, void* sig, void* S,
                           void* rho, void* v, cudaStream_t);
     // induced field: the coupled step, both field buffers at rest in the
@@ -99,6 +101,8 @@ const Dispatch& dispatch_bf16();
 cudaError_t launch_reduce_rows(const double* partials, int nb, int W, double* out, double weight, int accumulate,
                                cudaStream_t st);
 cudaError_t launch_zero(double* p, long long n, cudaStream_t st);
+// out[2] = out[0] / out[1] (0 when out[1] is 0), on the device
+cudaError_t launch_ratio(double* out, cudaStream_t st);
 // insulating walls: set the field from the last step's mean flow velocity /
 // reset it to the configured field
 cudaError_t ins_update(const Ctx& x, cudaStream_t st);

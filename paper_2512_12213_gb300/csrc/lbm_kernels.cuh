@@ -827,6 +827,64 @@ k_balance(const typename S::T* __restrict__ P, const uint8_t* __restrict__ cls, 
         for (int k = 0; k < 7; ++k) partials[(long long)blockIdx.x * 7 + k] = acc[k];
 }
 
+// ------------------------------------------------------- steady residual
+// Sec. 6: the balance of Eq. (32) between wall force and body force holds
+// once the flow stops changing.  Per fluid node of f(T): the flow velocity
+// v = c (j/rho + A/2) (text after Eq. 1; the moments summed in FP64 from the
+// stored values), |v - v_ref| and |v| (Euclidean norms), block sums in FP64
+// for the fixed-order pass; with `update` the node's v replaces v_ref (each
+// thread reads its own entries before it writes them; solid nodes get 0).
+template <int Q, class S, bool EXT>
+__global__ void __launch_bounds__(RED_THREADS)
+k_residual(const typename S::T* __restrict__ P, const uint8_t* __restrict__ cls, const Geo g,
+           const KP<typename S::R> p, double* __restrict__ vref, int update, double* __restrict__ partials)
+{
+    using R = typename S::R;
+    __shared__ double sm[2 * 32];
+    double acc[2] = {0.0, 0.0};
+    const long long N = (long long)g.nx * g.ny * g.nz;
+    const double c = (double)p.c;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % g.nx);
+        const long long r = n / g.nx;
+        const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+        if (nc_solid(cls[r * g.nxp + x])) {
+            if (update)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) vref[(long long)k * N + n] = 0.0;
+            continue;
+        }
+        R d[Q];
+        gather_node<Q, S>(P, cls, g, p, x, y, z, d);
+        NodeM<R> m;
+        node_macro<R, Q, EXT>(d, p, m);
+        double dr = 0.0, j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const double da = (double)d[a];
+            dr += da;
+            j[0] += EX<Q>(a) * da;
+            j[1] += EY<Q>(a) * da;
+            j[2] += EZ<Q>(a) * da;
+        }
+        const double rho = (double)p.rho0 + dr;
+        double dd = 0.0, vv = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double vk = c * (j[k] / rho + 0.5 * (double)m.A[k]);
+            const double dk = vk - vref[(long long)k * N + n];
+            dd += dk * dk;
+            vv += vk * vk;
+            if (update) vref[(long long)k * N + n] = vk;
+        }
+        acc[0] += sqrt(dd);
+        acc[1] += sqrt(vv);
+    }
+    block_sum<2>(acc, sm);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 2; ++k) partials[(long long)blockIdx.x * 2 + k] = acc[k];
+}
+
 // ----------------------------------------------------------------- stress
 // Variants 1, 2 at f(T) = gather(cur); 3, 4 at the half step between T-1 and
 // T: fbar = (cur + gather(cur))/2 with the node's state at T-1 = gather(prev).
@@ -1217,6 +1275,23 @@ cudaError_t launch_balance(const Ctx& c, const void* P, double* partials, int* n
 }
 
 template <int Q, class S>
+cudaError_t launch_residual(const Ctx& c, const void* P, double* vref, int update, double* partials, int* nblocks,
+                            cudaStream_t st)
+{
+    using T = typename S::T;
+    const long long N = (long long)c.geo.nx * c.geo.ny * c.geo.nz;
+    const int blocks = grid_for(N, RED_THREADS, MAX_PARTIAL_ROWS);
+    *nblocks = blocks;
+    if (c.ext)
+        k_residual<Q, S, true><<<blocks, RED_THREADS, 0, st>>>((const T*)P, c.cls, c.geo, kp_of<S>(c), vref, update,
+                                                               partials);
+    else
+        k_residual<Q, S, false><<<blocks, RED_THREADS, 0, st>>>((const T*)P, c.cls, c.geo, kp_of<S>(c), vref, update,
+                                                                partials);
+    return cudaGetLastError();
+}
+
+template <int Q, class S>
 cudaError_t launch_stress(const Ctx& c, const void* cur, const void* prev, int variant, void* sig, void* Sv,
                           void* rho, void* v, cudaStream_t st)
 {
@@ -1300,6 +1375,10 @@ template <class S> Dispatch make_dispatch()
     };
     d.balance = [](const Ctx& c, const void* P, double* pa, int* nb, cudaStream_t st) {
         return c.cfg.lattice == 9 ? launch_balance<9, S>(c, P, pa, nb, st) : launch_balance<19, S>(c, P, pa, nb, st);
+    };
+    d.residual = [](const Ctx& c, const void* P, double* vr, int up, double* pa, int* nb, cudaStream_t st) {
+        return c.cfg.lattice == 9 ? launch_residual<9, S>(c, P, vr, up, pa, nb, st)
+                                  : launch_residual<19, S>(c, P, vr, up, pa, nb, st);
     };
     d.stress = [](const Ctx& c, const void* cu, const void* pr, int var, void* sg, void* Sv, void* rh, void* v,
                   cudaStream_t st) {

@@ -29,7 +29,8 @@ OUT_DEVICE, OUT_HOST, OUT_HOST_ASYNC = 0, 1, 2
  NUM_BUFFERS) = range(10)
 MAX_WALLS = 16
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_UNSUPPORTED", 5: "ERR_NAN",
-          6: "ERR_STATE"}
+          6: "ERR_STATE", 7: "ERR_NOT_CONVERGED"}
+ERR_ARG, ERR_NAN, ERR_NOT_CONVERGED = 1, 5, 7
 
 
 class LbmError(RuntimeError):
@@ -96,6 +97,8 @@ _SIGS = {
     "lbm_wall_force": [_vp, _i, ctypes.c_uint, _d, _vp, _i, _vp],
     "lbm_wall_force_noalloc": [_vp, _i, ctypes.c_uint, _d, _vp, _i, _vp],
     "lbm_balance": [_vp, _vp, _i, _vp],
+    "lbm_residual": [_vp, _vp, _i, _vp, _i, _vp],
+    "lbm_run_steady": [_vp, _i, _d, ctypes.c_int64, _vp, _P(_d), _P(ctypes.c_int64), _vp],
     "lbm_adjoint_buffer_bytes": [_vp, _P(ctypes.c_size_t)],
     "lbm_adjoint_reset": [_vp, _vp],
     "lbm_adjoint_step": [_vp, _vp, _vp, _vp, _i, _P(_d), _d, _vp],
@@ -289,6 +292,21 @@ def lbm_balance(ctx, out, out_on_host, stream):
     _check(load().lbm_balance(ctx, _ptr(out), int(out_on_host), stream), ctx)
 
 
+def lbm_residual(ctx, v_ref, update, out, out_on_host, stream):
+    _check(load().lbm_residual(ctx, _ptr(v_ref), int(update), _ptr(out), int(out_on_host), stream), ctx)
+
+
+def lbm_run_steady(ctx, every, tol, max_steps, v_ref, stream):
+    """Returns (residual, steps taken); raises LbmError (status
+    ERR_NOT_CONVERGED) when max_steps is reached first."""
+    r = ctypes.c_double(-1.0)
+    n = ctypes.c_int64(0)
+    st = load().lbm_run_steady(ctx, int(every), float(tol), int(max_steps), _ptr(v_ref), ctypes.byref(r),
+                               ctypes.byref(n), stream)
+    _check(st, ctx)
+    return r.value, n.value
+
+
 def lbm_adjoint_buffer_bytes(ctx):
     n = ctypes.c_size_t()
     _check(load().lbm_adjoint_buffer_bytes(ctx, ctypes.byref(n)), ctx)
@@ -425,6 +443,20 @@ class Sim:
         out = np.zeros(7)
         lbm_balance(self.ctx, out, 1, self.stream)
         return out[0], out[1:4].copy(), out[4:7].copy()
+
+    def velocity_buffer(self):
+        """A zeroed device array for the residual's reference velocity, (3, nz, ny, nx) float64."""
+        return self.torch.zeros((3,) + self.shape, dtype=self.torch.float64, device=self.device)
+
+    def residual(self, v_ref, update=True):
+        """(sum |v - v_ref|, sum |v|, r) of the current state; updates v_ref."""
+        out = np.zeros(3)
+        lbm_residual(self.ctx, v_ref, update, out, OUT_HOST, self.stream)
+        return float(out[0]), float(out[1]), float(out[2])
+
+    def run_steady(self, every, tol, max_steps, v_ref=None):
+        v = self.velocity_buffer() if v_ref is None else v_ref
+        return lbm_run_steady(self.ctx, every, tol, max_steps, v, self.stream)
 
     def link_count(self, wall=-1):
         return lbm_link_count(self.ctx, wall)

@@ -218,6 +218,50 @@ def test_wall_force_stress_balance_fp64(orc, name, model):
     assert np.abs(bg - bo).max() < 1e-12 * max(np.abs(bo).max(), 1e-30)
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16s", "bf16s"])
+@pytest.mark.parametrize("name,model", [("d2q9", "b"), ("d2q9_mhd", "e"), ("d3q19", "d"), ("d3q19_ext", "c"),
+                                        ("cavity", "e"), ("periodic_ragged", "e")])
+def test_stress_reduced_precision(orc, name, model, storage):
+    """Stress variants S1-S4 of the FP32-compute paths against the FP64
+    oracle, node by node.  The stored populations differ from the oracle's
+    by at most TOL[storage] max|f| (the population bound above); the second
+    moment sums Q of them times c^2, so each stress component is within
+    Q TOL max|f| c^2, the strain rate S = sigma/(2 rho nu) within that over
+    2 rho_min nu, the density within Q TOL max|f| and the velocity within
+    Q TOL max|f| c / rho_min.  (The FP32 arithmetic itself adds ~1e-7 of
+    the moment scale, far below these bounds.)"""
+    cfg, mask = _case(name, model, storage)
+    ocfg, f0, _, _ = _initial(orc, cfg, mask)
+    sim = lbm.Sim(cfg, mask)
+    sim.import_f(f0)
+    K = 7
+    sim.step(K)
+    f_prev = orc.run(ocfg, mask, f0, K - 1)
+    f_K, frel = orc.step(ocfg, mask, f_prev)
+    Q = cfg["lattice"]
+    c = cfg.get("dx", 1.0) / cfg.get("dt", 1.0)
+    fmax = np.abs(f_K).max()
+    tol = Q * TOL[storage] * fmax
+    nu = cfg.get("dt", 1.0) * c * c * (cfg["tau"] - 0.5) / 3
+    fluid = mask == 0
+    worst = {}
+    for variant in (1, 2, 3, 4):
+        sg, Sg, rg, vg = [x.cpu().numpy().astype(np.float64) for x in sim.stress(variant)]
+        so, So, ro, vo = orc.stress(ocfg, mask, f_K if variant <= 2 else f_prev, frel, f_K, variant)
+        rmin = ro[fluid].min()
+        e_sig = np.abs(sg - so).max() / (c * c)
+        e_S = np.abs(Sg - So).max() * 2 * rmin * nu / (c * c)
+        e_rho = np.abs(rg - ro).max()
+        e_v = np.abs(vg - vo).max() * rmin / c
+        worst[variant] = e_sig / fmax
+        assert e_sig <= tol, (variant, e_sig, tol)
+        assert e_S <= tol * (1 + 1e-6) + 1e-7 * fmax, (variant, e_S, tol)
+        assert e_rho <= tol, (variant, e_rho, tol)
+        assert e_v <= tol, (variant, e_v, tol)
+        assert np.all(sg[:, ~fluid] == 0) and np.all(Sg[:, ~fluid] == 0)
+    print(f"stress error / (c^2 max|f|), {name} {storage}:", {k: f"{v:.2e}" for k, v in worst.items()})
+
+
 @pytest.mark.parametrize("name,model", [("d2q9", "a"), ("d3q19", "e"), ("d3q19_ext", "d")])
 def test_exact_momentum_balance_on_gpu(orc, name, model):
     """Every step: F_wall = sum rho a - [M(t+dt) - M(t)]/dt (FP64 path)."""
