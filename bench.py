@@ -570,66 +570,144 @@ def e2e_bench(torch, lbm, workloads, args):
             "d2h_bytes_per_step": round((state_bytes + 24 * steps) / steps, 1)}
 
 
-def cpu_baseline(budget_s=20.0):
-    """The FP64 oracle as it stands, single-threaded, on a bounded sample of
-    the headline workload: steps of the full 256x128x128 sphere box."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def _oracle_mlups(orc, ocfg, mask, f, budget_s, max_steps, omp):
+    """Oracle steps within a time budget, as one call after a one-step probe
+    (the per-call copy of the state is then paid once); (MLUPS, steps, s)."""
+    t0 = time.perf_counter()
+    f = orc.run(ocfg, mask, f, 1, omp=omp)
+    probe = time.perf_counter() - t0
+    n = int(max(1, min(max_steps, budget_s / max(probe, 1e-9))))
+    t0 = time.perf_counter()
+    orc.run(ocfg, mask, f, n, omp=omp)
+    t = time.perf_counter() - t0
+    return mask.size * n / t / 1e6, n, t
+
+
+def cpu_baseline(budget_s=10.0):
+    """The FP64 oracle as it stands on the host: its OpenMP timing build on
+    every core (the parallel node loops of a step; results identical to the
+    single-threaded parity build) and the parity build on one thread, each on
+    a bounded sample of the headline workload (steps of the full
+    256x128x128 sphere box); plus the two small 2-D configurations run in
+    full: the Poiseuille channel (64x32, 10,000 steps) and the Hartmann channel
+    (256x128, 50,000 steps, all cores, if it fits in about a minute and a half)."""
+    cores = host_cores()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
     from oracle import oracle as orc
     from paper_2512_12213_gb300 import workloads
     orc.build()
+    orc.build(omp=True)
+    threads = orc.threads(omp=True)
     cfg, mask = workloads.sphere(storage="f64")
     ocfg = orc.make_cfg(**workloads.oracle_kwargs(cfg))
     nz, ny, nx = mask.shape
     f = orc.init(ocfg, mask, np.ones((nz, ny, nx)), np.zeros((3, nz, ny, nx)))
-    steps, t = 0, 0.0
+    v_all, s_all, t_all = _oracle_mlups(orc, ocfg, mask, f, budget_s, 200, True)
+    v_one, s_one, t_one = _oracle_mlups(orc, ocfg, mask, f, budget_s, 20, False)
+    out = {"value": round(v_all, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
+           "sample": f"{s_all} FP64 step(s) of the full 256x128x128 sphere box, OpenMP timing build on "
+                     f"{threads} thread(s)",
+           "cpu_model": cpu_model(), "host_cores": cores,
+           "single_thread": {"value": round(v_one, 3), "unit": "MLUPS", "cores": 1,
+                             "sample": f"{s_one} FP64 step(s) of the same box, parity build"}}
+    # C1 in full, single thread
+    c1, m1 = workloads.poiseuille(storage="f64")
+    o1 = orc.make_cfg(**workloads.oracle_kwargs(c1))
+    f1 = orc.init(o1, m1, np.ones(m1.shape), np.zeros((3,) + m1.shape))
     t0 = time.perf_counter()
-    while t < budget_s and steps < 10:
-        f = orc.run(ocfg, mask, f, 1)
-        steps += 1
-        t = time.perf_counter() - t0
-    N = nx * ny * nz
-    return {"value": round(N * steps / t / 1e6, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} FP64 step(s) of the full 256x128x128 sphere box, single thread"}
+    orc.run(o1, m1, f1, 10000)
+    t1 = time.perf_counter() - t0
+    out["poiseuille_64x32_10000_steps"] = {"seconds": round(t1, 3), "mlups": round(m1.size * 1e4 / t1 / 1e6, 3),
+                                            "cores": 1}
+    # C2 in full on every core, if the first 2,000 steps project it within ~90 s
+    c2, m2 = workloads.hartmann(storage="f64")
+    o2 = orc.make_cfg(**workloads.oracle_kwargs(c2))
+    f2 = orc.init(o2, m2, np.ones(m2.shape), np.zeros((3,) + m2.shape))
+    t0 = time.perf_counter()
+    f2 = orc.run(o2, m2, f2, 2000, omp=True)
+    tp = time.perf_counter() - t0
+    if tp * 25 <= 90.0:
+        orc.run(o2, m2, f2, 48000, omp=True)
+        t2 = time.perf_counter() - t0
+        out["hartmann_256x128_50000_steps"] = {"seconds": round(t2, 3),
+                                                "mlups": round(m2.size * 5e4 / t2 / 1e6, 3), "cores": threads}
+    else:
+        out["hartmann_256x128_50000_steps"] = {"projected_seconds": round(tp * 25, 1),
+                                                "mlups": round(m2.size * 2000 / tp / 1e6, 3), "cores": threads,
+                                                "note": "first 2,000 steps timed; the full run would exceed 90 s"}
+    return out
 
 
 # --------------------------------------------------------- reference arm
 def run_reference(args):
-    """The FP64 CPU oracle as it stands on the headline workload's metric:
-    each step is one oracle step on a z-slab of the sphere box (periodic),
-    sized so the whole run stays within a few minutes."""
+    """The FP64 CPU oracle as it stands on the headline workload's metric, on
+    the host's cores (its OpenMP timing build; the per-node arithmetic of the
+    parity build): each step is one oracle step on a z-slab of the sphere box
+    (periodic), sized so the whole run stays within a few minutes."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
+    cores = host_cores()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
     from oracle import oracle as orc
     from paper_2512_12213_gb300 import workloads
-    orc.build()
+    orc.build(omp=True)
+    threads = orc.threads(omp=True)
     cfg, mask = workloads.sphere(storage="f64")
     total_steps = args.steps + args.warmup
-    # pick the slab thickness from a one-layer probe: ~120 s for the whole run
+
     def slab(nzs):
         m = mask[64 - nzs // 2: 64 - nzs // 2 + nzs].copy()
         c = dict(cfg, nz=nzs)
         oc = orc.make_cfg(**workloads.oracle_kwargs(c))
         f = orc.init(oc, m, np.ones(m.shape), np.zeros((3,) + m.shape))
         return oc, m, f
-    oc, m, f = slab(1)
+    # pick the slab thickness from an 8-layer probe: ~120 s for the whole run
+    oc, m, f = slab(8)
     t0 = time.perf_counter()
-    f = orc.run(oc, m, f, 2)
-    per_layer = (time.perf_counter() - t0) / 2
+    f = orc.run(oc, m, f, 2, omp=True)
+    per_layer = (time.perf_counter() - t0) / 2 / 8
     nzs = int(max(1, min(128, 120.0 / max(total_steps * per_layer, 1e-9))))
     oc, m, f = slab(nzs)
-    f = orc.run(oc, m, f, args.warmup)
+    f = orc.run(oc, m, f, args.warmup, omp=True)
     t0 = time.perf_counter()
-    f = orc.run(oc, m, f, args.steps)
+    f = orc.run(oc, m, f, args.steps, omp=True)
     t = time.perf_counter() - t0
     N = m.size
     value = N * args.steps / t / 1e6
-    sample = f"each step: one FP64 oracle step on a 256x128x{nzs} z-slab through the sphere (periodic)"
+    sample = (f"each step: one FP64 oracle step on a 256x128x{nzs} z-slab through the sphere (periodic), "
+              f"OpenMP timing build on {threads} thread(s)")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "MLUPS", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample_nodes": N},
-            "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                             "sample": sample, "cpu_model": cpu_model()},
             "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -161,7 +161,21 @@ typedef struct lbm_config {
     int32_t induced;                 /* 1: induced magnetic field (needs maxwell = 1), see below */
     double eta;                      /* magnetic diffusivity of the induced field, > 0 */
     int32_t mag_conducting;          /* induced field at walls: 0 insulating, 1 perfectly conducting */
+    int32_t step_kernel;             /* LBM_STEP_*: which kernel runs the step (see below) */
 } lbm_config;
+
+/* Kernel of the fused step.  Both compute the same arithmetic and store the
+ * same bits; they differ in how the pull sources reach the registers.
+ * LBM_STEP_AUTO (0) picks the staged kernel wherever it applies and enough
+ * shared memory holds its pipeline, else the register-tiled one.
+ * LBM_STEP_REGISTER (1): every thread loads its vectors straight from HBM.
+ * LBM_STEP_STAGED (2): a persistent kernel stages each tile's source rows in
+ * shared memory with bulk asynchronous copies; it applies to boxes periodic
+ * on every axis, FP32 or 16-bit storage, and none of lorentz, maxwell, les,
+ * stokes, darcy, curved, insulating, induced (else LBM_ERR_ARG); where its
+ * pipeline does not fit in shared memory (rows of more than about 1,100
+ * 16-bit or 550 FP32 nodes) the register-tiled kernel runs instead. */
+enum { LBM_STEP_AUTO = 0, LBM_STEP_REGISTER = 1, LBM_STEP_STAGED = 2 };
 
 /* Induced magnetic field (Sec. 4 cites Dellar's vector lattice Boltzmann
  * model for the induction equation dB/dt + div(v B - B v) = eta lap B).
@@ -315,9 +329,12 @@ lbm_status lbm_time(const lbm_ctx* ctx, int64_t* t);
 lbm_status lbm_electric_field(lbm_ctx* ctx, double* E, void* stream);
 
 /* Error flags raised by kernels since the last clear (synchronises the
- * stream): bit 0 = a bounded wait for staged input expired (the step was not
- * completed; the state is invalid).  clear != 0 resets them. */
+ * stream): bit 0 = a bounded wait of the staged step kernel expired (about a
+ * second without progress; the step was not completed and the state is
+ * invalid); bit 1 = the staged step was launched with a pipeline shape it
+ * refuses (nothing was computed).  clear != 0 resets them. */
 #define LBM_DEVICE_WAIT_TIMEOUT 1u
+#define LBM_DEVICE_BAD_LAUNCH 2u
 lbm_status lbm_device_status(lbm_ctx* ctx, uint32_t* flags, int clear, void* stream);
 
 /* Stress tensor (Eqs. 8-9, 27-30).  Outputs are dense device arrays in the

@@ -18,6 +18,19 @@
 #include <string.h>
 
 #include "lbm_oracle.h"
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* threads the node loops of a step use: 1 in the parity build */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 typedef struct {
     int q, d;
@@ -248,6 +261,10 @@ static void propagate(const orc_cfg* c, const lat_t* L, const unsigned char* wid
     const long N = nnodes(c);
     const int Q = L->q;
     memset(fnew, 0, sizeof(double) * N * Q);
+    /* every destination entry is written by exactly one (node, direction), so
+     * the planes are independent; the pragma only acts in the OpenMP timing
+     * build (the parity build is compiled without -fopenmp) */
+#pragma omp parallel for schedule(static)
     for (int z = 0; z < c->nz; ++z)
         for (int y = 0; y < c->ny; ++y)
             for (int x = 0; x < c->nx; ++x) {
@@ -288,9 +305,9 @@ static void step_work(const orc_cfg* c, const lat_t* L, const unsigned char* wid
 {
     const long N = nnodes(c);
     const int Q = L->q;
-    double vs[3] = {0.0, 0.0, 0.0};
-    long nf = 0;
-    /* relaxation with the force term at every fluid node, Eq. (2) */
+    /* relaxation with the force term at every fluid node, Eq. (2) (nodes
+     * independent: parallel in the OpenMP timing build only) */
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
         if (wid[n] != 0) {
             for (int a = 0; a < Q; ++a) frel[a * N + n] = 0.0;
@@ -300,15 +317,22 @@ static void step_work(const orc_cfg* c, const lat_t* L, const unsigned char* wid
         for (int a = 0; a < Q; ++a) fl[a] = f[a * N + n];
         collide_r(c, L, fl, c->g, out);
         for (int a = 0; a < Q; ++a) frel[a * N + n] = out[a];
-        if (vmean) {
+    }
+    /* the mean flow velocity of the pre-collision state, summed in node order */
+    if (vmean) {
+        double vs[3] = {0.0, 0.0, 0.0};
+        long nf = 0;
+        for (long n = 0; n < N; ++n) {
+            if (wid[n] != 0) continue;
+            double fl[19];
+            for (int a = 0; a < Q; ++a) fl[a] = f[a * N + n];
             macro_t_r m;
             macro_r(c, L, fl, c->g, &m);
             for (int k = 0; k < 3; ++k) vs[k] += m.v[k];
             ++nf;
         }
-    }
-    if (vmean)
         for (int k = 0; k < 3; ++k) vmean[k] = nf ? vs[k] / (double)nf : 0.0;
+    }
     propagate(c, L, wid, frel, fnew);
     memcpy(f, fnew, sizeof(double) * N * Q);
 }
@@ -331,10 +355,11 @@ void orc_run_e(const orc_cfg* c, const unsigned char* wid, double* f, int nsteps
     double* fnew = (double*)malloc(sizeof(double) * N * L.q);
     orc_cfg cc = *c;
     for (int k = 0; k < 3; ++k) cc.E[k] = E[k];
+    const int ins = c->insulating && c->lorentz;
     for (int s = 0; s < nsteps; ++s) {
         double vm[3];
-        step_work(&cc, &L, wid, f, frel, fnew, vm);
-        if (c->insulating && c->lorentz) insulating_field(c, vm, cc.E);
+        step_work(&cc, &L, wid, f, frel, fnew, ins ? vm : NULL);
+        if (ins) insulating_field(c, vm, cc.E);
     }
     for (int k = 0; k < 3; ++k) E[k] = cc.E[k];
     free(frel);

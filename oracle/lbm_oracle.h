@@ -88,6 +88,10 @@ typedef struct orc_cfg {
                               orc_wall_force use instead of B (induced runs) */
 } orc_cfg;
 
+/* threads of the node loops: 1 for the parity build, the OpenMP thread count
+ * for the timing build (the same source compiled with -fopenmp) */
+int orc_threads(void);
+
 /* lattice tables: e (unit-speed integers, Q*3), w (Q), opposite index (Q) */
 int orc_lattice(int q, int* e, double* w, int* opp);
 

@@ -21,6 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = [os.path.join(_HERE, "lbm_oracle.c"), os.path.join(_HERE, "oracle_node.inc"),
         os.path.join(_HERE, "lbm_oracle.h")]
 _LIB_PATH = os.path.join(_HERE, "liblbm_oracle.so")
+_OMP_PATH = os.path.join(_HERE, "liblbm_oracle_omp.so")
 
 MAX_WALLS = 16
 FORCE = {"a": 0, "b": 1, "c": 2, "d": 3, "e": 4}
@@ -28,15 +29,20 @@ MOVING_CORR = 1
 MAXWELL_REMOVE = 2
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no fused multiply-add contraction)."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle with gcc (no fused multiply-add contraction).  The
+    parity build is single threaded; omp=True builds the timing copy, the
+    same source with OpenMP over the independent node loops of a step (the
+    per-node arithmetic, and so every result, is the same)."""
+    path = _OMP_PATH if omp else _LIB_PATH
     newest = max(os.path.getmtime(p) for p in _SRC)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
-        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    if force or not os.path.exists(path) or os.path.getmtime(path) < newest:
+        tmp = path + f".{os.getpid()}.tmp"
         subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
+                        "-Wl,-Bsymbolic", *(["-fopenmp"] if omp else []),
                         "-o", tmp, _SRC[0], "-lm"], check=True)
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+        os.replace(tmp, path)
+    return path
 
 
 class OrcCfg(ctypes.Structure):
@@ -66,19 +72,21 @@ class OrcCfg(ctypes.Structure):
     ]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
+def lib(omp: bool = False):
+    """The parity build (default) or the OpenMP timing build of the oracle."""
+    _lib = _libs.get(omp)
     if _lib is None:
-        _lib = ctypes.CDLL(build())
+        _lib = _libs[omp] = ctypes.CDLL(build(omp=omp))
         P = ctypes.POINTER
         d = ctypes.c_double
         dp = P(d)
         ub = P(ctypes.c_ubyte)
         cp = P(OrcCfg)
         sig = {
+            "orc_threads": (ctypes.c_int, []),
             "orc_lattice": (ctypes.c_int, [ctypes.c_int, P(ctypes.c_int), dp, P(ctypes.c_int)]),
             "orc_feq": (None, [cp, d, dp, dp]),
             "orc_node_macro": (None, [cp, dp, dp]),
@@ -158,6 +166,11 @@ def _u8(a):
     return np.ascontiguousarray(a, dtype=np.uint8)
 
 
+def threads(omp=False):
+    """Threads of a step's node loops in the parity (1) or timing build."""
+    return int(lib(omp).orc_threads())
+
+
 def lattice(q):
     e = np.zeros((q, 3), dtype=np.int32)
     w = np.zeros(q)
@@ -214,9 +227,10 @@ def step(cfg, wall_id, f):
     return fn, frel
 
 
-def run(cfg, wall_id, f, n):
+def run(cfg, wall_id, f, n, omp=False):
+    """n steps; omp=True runs the OpenMP timing build (same results)."""
     fn = _f64(f).copy()
-    lib().orc_run(ctypes.byref(cfg), _ub(_u8(wall_id)), _dp(fn), int(n))
+    lib(omp).orc_run(ctypes.byref(cfg), _ub(_u8(wall_id)), _dp(fn), int(n))
     return fn
 
 

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "lbm_internal.h"
+#include "lbm_staged.cuh"
 
 using namespace lbm;
 
@@ -34,6 +35,15 @@ size_t elem_of(int storage)
     case LBM_STORE_F32: return 4;
     default: return 2;
     }
+}
+
+// the staged step serves periodic boxes with the plain node code
+bool staged_applies(const lbm_config* c)
+{
+    const bool periodic = c->periodic[0] && c->periodic[1] && (c->lattice == LBM_D2Q9 || c->periodic[2]);
+    const bool plain = !c->lorentz && !c->maxwell && !c->les && !c->stokes && !(c->darcy > 0.0) && !c->curved &&
+                       !c->insulating && !c->induced;
+    return periodic && plain && c->storage != LBM_STORE_F64;
 }
 
 bool validate(const lbm_config* c, const uint8_t* wid, std::string& err)
@@ -88,6 +98,10 @@ bool validate(const lbm_config* c, const uint8_t* wid, std::string& err)
         if (!(c->eta > 0.0) || !std::isfinite(c->eta)) return fail("eta must be finite and > 0");
         if (c->mag_conducting != 0 && c->mag_conducting != 1) return fail("mag_conducting must be 0 or 1");
     }
+    if (c->step_kernel < LBM_STEP_AUTO || c->step_kernel > LBM_STEP_STAGED) return fail("step_kernel must be 0..2");
+    if (c->step_kernel == LBM_STEP_STAGED && !staged_applies(c))
+        return fail("the staged step kernel needs a box periodic on every axis, FP32 or 16-bit storage and none of "
+                    "lorentz, maxwell, les, stokes, darcy, curved, insulating, induced");
     if (!wid) return fail("wall_id is NULL");
     const long long N = nodes_of(c);
     for (long long n = 0; n < N; ++n)
@@ -177,7 +191,19 @@ void build_geometry(const lbm_config* c, const uint8_t* wid, int nxp, std::vecto
     }
 }
 
-void count_links(const lbm_config* c, const uint8_t* wid, long long* per_wall /* MAX+1 */)
+// the 4-node chunks of the padded layout that hold a node other than a bulk
+// fluid node (a wall or face neighbour, a solid node, padding): the first
+// node of each, in order.  The staged step leaves them to its boundary warps.
+std::vector<uint32_t> special_chunks(const std::vector<uint8_t>& cls)
+{
+    std::vector<uint32_t> out;
+    for (size_t i = 0; i + 3 < cls.size(); i += 4)
+        if (cls[i] != NC_BULK || cls[i + 1] != NC_BULK || cls[i + 2] != NC_BULK || cls[i + 3] != NC_BULK)
+            out.push_back((uint32_t)i);
+    return out;
+}
+
+void count_links(const lbm_config* c, const uint8_t* wid, long long* per_wall /* MAX+1 */, long long* n_special)
 {
     std::fill(per_wall, per_wall + LBM_MAX_WALLS + 1, 0);
     std::vector<uint8_t> cls;
@@ -185,6 +211,7 @@ void count_links(const lbm_config* c, const uint8_t* wid, long long* per_wall /*
     if (c->lattice == 9) build_geometry<9>(c, wid, pitch_of(c->nx), cls, &links);
     else build_geometry<19>(c, wid, pitch_of(c->nx), cls, &links);
     for (const Link& L : links) per_wall[L.wall]++;
+    *n_special = (long long)special_chunks(cls).size();
 }
 
 // threads of the register-tiled step kernel: one per vector chunk
@@ -201,12 +228,19 @@ long long ins_rows_of(const lbm_config* c)
     return (step_threads_of(c) + 127) / 128 * 4;
 }
 
-void sizes_of(const lbm_config* c, long long n_links, size_t s[LBM_NUM_BUFFERS])
+// contexts that may run the staged step keep the list of special chunks in
+// the node buffer, after the class bytes
+bool keeps_special_list(const lbm_config* c)
+{
+    return c->step_kernel != LBM_STEP_REGISTER && staged_applies(c);
+}
+
+void sizes_of(const lbm_config* c, long long n_links, long long n_special, size_t s[LBM_NUM_BUFFERS])
 {
     const long long sq = (long long)pitch_of(c->nx) * c->ny * c->nz;
     const long long N = nodes_of(c);
     s[LBM_BUF_POP_A] = s[LBM_BUF_POP_B] = round256((size_t)c->lattice * sq * elem_of(c->storage));
-    s[LBM_BUF_NODE] = round256((size_t)sq);
+    s[LBM_BUF_NODE] = round256((size_t)sq) + (keeps_special_list(c) ? round256((size_t)n_special * 4) : 0);
     s[LBM_BUF_LINKS] = n_links ? round256((size_t)n_links * sizeof(Link)) : 0;
     s[LBM_BUF_SCRATCH] = round256(SCRATCH_DOUBLES * sizeof(double));
     if (c->insulating)
@@ -370,6 +404,41 @@ void fill_params(Ctx& x)
     bind_insulating(x);
 }
 
+// shape of the staged step: tiles of R rows such that each direction's copy
+// moves at least 2 KB (R nxp = 1024 nodes for 16-bit storage, 512 for FP32:
+// a bulk copy costs the copy engine a fixed time, so small copies starve the
+// pipeline), and as many stages (an even count, 4..8) as the shared memory
+// holds; stage_R = 0
+// where the kernel does not apply, was not asked for, or fewer than 4 stages
+// fit (rows of more than ~1,100 16-bit or ~550 FP32 nodes): the
+// register-tiled kernel serves those contexts
+void choose_stage(Ctx& x)
+{
+    x.stage_R = 0;
+    x.stage_n = 0;
+    x.stage_tiles = 0;
+    x.stage_smem = 0;
+    x.stage_ready = false;
+    if (!keeps_special_list(&x.cfg)) return;
+    // automatic choice: the boundary warps keep pace while at most 2% of the
+    // chunks are special (a sphere or a few bodies in a periodic box); boxes
+    // full of small solids go to the register-tiled kernel
+    if (x.cfg.step_kernel == LBM_STEP_AUTO && x.n_special * 50 > x.geo.sq / 4) return;
+    const size_t Q = x.cfg.lattice, nxp = x.geo.nxp;
+    const size_t row_bytes = nxp * x.elem;
+    const int R = (int)std::max<size_t>(1, std::min<size_t>((STG_COPY_BYTES + row_bytes - 1) / row_bytes,
+                                                            (size_t)x.cfg.ny));
+    const size_t stage = (Q * R * nxp * x.elem + R * nxp + 127) / 128 * 128;
+    const size_t budget = (size_t)x.smem_optin - 1024;
+    // an even count: each consumer group owns every other stage
+    const int n = (int)std::min<size_t>(8, budget / (stage + 2 * sizeof(uint64_t))) & ~1;
+    if (n < 4) return;
+    x.stage_R = R;
+    x.stage_n = n;
+    x.stage_tiles = (long long)((x.cfg.ny + R - 1) / R) * x.cfg.nz;
+    x.stage_smem = n * stage + 2 * n * sizeof(uint64_t);
+}
+
 // signed wall distance in the padded layout: the given canonical values, or
 // +-1/2 (halfway bounce-back) when phi is null; padding gets 0
 std::vector<float> padded_distance(const Ctx& x, const float* phi)
@@ -475,11 +544,11 @@ lbm_status lbm_buffer_sizes(const lbm_config* cfg, const uint8_t* host_wall_id, 
         return LBM_ERR_ARG;
     }
     if (!validate(cfg, host_wall_id, g_cfg_err)) return LBM_ERR_ARG;
-    long long per_wall[LBM_MAX_WALLS + 1];
-    count_links(cfg, host_wall_id, per_wall);
+    long long per_wall[LBM_MAX_WALLS + 1], n_special = 0;
+    count_links(cfg, host_wall_id, per_wall, &n_special);
     long long nl = 0;
     for (int w = 0; w <= LBM_MAX_WALLS; ++w) nl += per_wall[w];
-    sizes_of(cfg, nl, sizes);
+    sizes_of(cfg, nl, n_special, sizes);
     return LBM_OK;
 }
 
@@ -535,8 +604,10 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
         x.wall_begin[LBM_MAX_WALLS + 1] = pos;
     }
 
+    const std::vector<uint32_t> special = special_chunks(cls);
+    x.n_special = (long long)special.size();
     size_t need[LBM_NUM_BUFFERS];
-    sizes_of(&x.cfg, x.n_links, need);
+    sizes_of(&x.cfg, x.n_links, x.n_special, need);
     for (int b = 0; b < LBM_NUM_BUFFERS; ++b) {
         const bool optional = (b == LBM_BUF_STAGE) || ((b == LBM_BUF_LINKS || b == LBM_BUF_PHI || b == LBM_BUF_MAG_A ||
                                                          b == LBM_BUF_MAG_B) &&
@@ -565,6 +636,9 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
     x.mag[0] = x.cfg.induced ? buffers[LBM_BUF_MAG_A] : nullptr;
     x.mag[1] = x.cfg.induced ? buffers[LBM_BUF_MAG_B] : nullptr;
     x.cls = (uint8_t*)buffers[LBM_BUF_NODE];
+    x.special = keeps_special_list(&x.cfg)
+                    ? reinterpret_cast<const uint32_t*>(x.cls + round256((size_t)x.geo.sq))
+                    : nullptr;
     x.links = (Link*)buffers[LBM_BUF_LINKS];
     x.scratch = (double*)buffers[LBM_BUF_SCRATCH];
     bind_insulating(x);
@@ -586,9 +660,13 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
         delete h;
         return LBM_ERR_CUDA;
     }
+    choose_stage(x);
     x.adj_blocks = 0;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(x.cls, cls.data(), cls.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && x.special && x.n_special)
+        e = cudaMemcpyAsync((void*)x.special, special.data(), special.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                            st);
     if (e == cudaSuccess && x.n_links)
         e = cudaMemcpyAsync(x.links, links.data(), links.size() * sizeof(Link), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = launch_zero(x.scratch, (long long)SCRATCH_DOUBLES, st);

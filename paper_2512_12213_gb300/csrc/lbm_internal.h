@@ -124,6 +124,8 @@ struct Ctx {
     int cur;                 // index of the buffer holding f^rel(T-1) (and, induced, G(T-1))
     void* mag[2];            // induced field: post-collision field distributions, null otherwise
     uint8_t* cls;
+    const uint32_t* special;  // first nodes of the 4-node chunks with a non-bulk node (staged step), or null
+    long long n_special;
     Link* links;
     long long wall_begin[LBM_MAX_WALLS + 2];   // link ranges per wall id (sorted)
     long long n_links;
@@ -135,6 +137,12 @@ struct Ctx {
     std::string err;
     int sm_count;
     int smem_optin;
+    // staged step (stage_R = 0: the register-tiled k_step serves the context)
+    int stage_R;             // rows per tile
+    int stage_n;             // pipeline stages
+    long long stage_tiles;   // tiles per step
+    size_t stage_smem;       // dynamic shared memory per block
+    mutable bool stage_ready;
     mutable int adj_blocks;  // grid of the adjoint kernel (0: not yet sized)
     unsigned* errflag;
     // curved walls: the wall ids of the geometry (host), to check distances

@@ -8,6 +8,7 @@
 
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
+#include "lbm_staged.cuh"
 
 namespace lbm {
 
@@ -1193,9 +1194,35 @@ cudaError_t launch_step_q(const Ctx& c, const void* src, void* dst, uint32_t see
     return cudaGetLastError();
 }
 
+// the staged step (periodic boxes with the plain node code, 16-bit or FP32
+// storage; the host chose the tile rows and stage count at create)
+template <int Q, class S, bool SR>
+cudaError_t launch_step_staged(const Ctx& c, const void* src, void* dst, uint32_t seed, cudaStream_t st)
+{
+    using T = typename S::T;
+    auto kern = k_step_staged<Q, S, SR>;
+    if (!c.stage_ready) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.stage_smem);
+        if (e != cudaSuccess) return e;
+        c.stage_ready = true;
+    }
+    const int blocks = (int)std::min<long long>((long long)c.sm_count, c.stage_tiles);
+    kern<<<blocks, STG_THREADS, c.stage_smem, st>>>((const T*)src, (T*)dst, c.cls, c.special, c.n_special, c.geo,
+                                                     kp_step_of<S>(c), seed, c.stage_R, c.stage_tiles, c.stage_n,
+                                                     c.errflag);
+    return cudaGetLastError();
+}
+
 template <int Q, class S>
 cudaError_t launch_step(const Ctx& c, const void* src, void* dst, uint32_t seed, cudaStream_t st)
 {
+    if constexpr (sizeof(typename S::T) == 2) {
+        if (c.stage_R > 0)
+            return c.sr ? launch_step_staged<Q, S, true>(c, src, dst, seed, st)
+                        : launch_step_staged<Q, S, false>(c, src, dst, seed, st);
+    } else if constexpr (sizeof(typename S::T) == 4) {
+        if (c.stage_R > 0) return launch_step_staged<Q, S, false>(c, src, dst, seed, st);
+    }
     if constexpr (sizeof(typename S::T) == 2) {
         if (c.sr)
             return c.ext ? launch_step_q<Q, S, true, true>(c, src, dst, seed, st)

@@ -1,0 +1,368 @@
+// lbm_staged.cuh -- the fused collide-stream step (Eq. 2 with Eqs. 1 and 3)
+// as a persistent kernel whose input rows are staged in shared memory by the
+// bulk asynchronous copies of the tensor memory accelerator, for periodic
+// boxes whose nodes need the plain node code (no Lorentz force, Maxwell
+// term, LES, curved or insulating walls) and 16-bit or FP32 storage.
+//
+// Pull scheme: a tile is R consecutive rows (y0 .. y0+R-1) of one z plane;
+// for direction a the tile reads the R source rows shifted by (E_y, E_z),
+// which lie contiguously in that direction's plane, so one bulk copy per
+// direction (two where the rows wrap around the periodic y axis) brings them
+// in, and every stored population is read from HBM once per step.  The x
+// shift of the pull is an offset inside the staged row (the periodic x wrap
+// an index at the row ends): no shuffles, and no register holds a load in
+// flight.  A bulk copy costs the copy engine of an SM a fixed time (measured
+// ~33 ns on GB300 whether it moves 512 B or 1 KB), so R is chosen for copies
+// of at least 2 KB per direction (R nxp = 1024 nodes for 16-bit storage, 512
+// for FP32), and the relaxed populations leave with ordinary coalesced
+// stores, which cost the copy engine nothing.
+//
+// One producer warp keeps up to 8 stages in flight (lane a copies direction
+// a): it refills a stage as soon as the consumer warps that read it have
+// released it (full / empty mbarriers, the full one with the copies'
+// transaction bytes).  Consumer warps form two groups that take alternate
+// tiles.  The stage count is even, so tile k uses stage k mod n and every
+// stage belongs to one group, which consumes its uses in order: a warp can
+// then only wait on the phase of a use whose predecessor its group has
+// finished, and a parity wait cannot mistake a phase two uses old for the
+// current one (with an odd count a stage alternates between the groups and
+// a group running ahead could do exactly that); a thread relaxes one pair of nodes of a 64-node warp task at a time
+// (one 32-bit word per direction for 16-bit storage, one float2 for FP32)
+// with the FP32x2 node code of k_step.  The 4-node chunks that touch a solid
+// node, a wall or the padding are not the pipeline's: a boundary warp per
+// block takes its share of their list (built on the host) and computes them
+// node by node from global memory with explicit bounce-back, exactly as
+// k_step does, beside the pipeline -- inline, one such chunk held up its
+// stage and with it the in-order producer (the sphere box ran at half the
+// rate of the same box without the sphere).  The arithmetic and the
+// stochastic rounding stream are those of k_step, so the two kernels store
+// the same bits.
+//
+// Every mbarrier wait is bounded (about a second of the global timer); on
+// expiry a warp records a flag for lbm_device_status and stops, and the
+// producer waits (again bounded) for the copies it issued before it returns.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+constexpr int STG_GROUPS = 2;                         // consumer groups (alternate tiles)
+constexpr int STG_GROUP_WARPS = 8;                    // warps per group
+constexpr int STG_CWARPS = STG_GROUPS * STG_GROUP_WARPS;
+constexpr int STG_THREADS = 32 * (STG_CWARPS + 2);    // plus the producer and the boundary warp
+constexpr int STG_COPY_BYTES = 2048;                  // least bytes per direction and tile
+constexpr int STG_TASK_NODES = 64;                    // nodes per warp task (32 pairs)
+constexpr int STG_MAX_STAGES = 8;
+constexpr unsigned long long STG_WAIT_NS = 1000000000ull;   // bounded waits: 1 s
+constexpr unsigned STG_ERR_TIMEOUT = 1u;
+constexpr unsigned STG_ERR_CONFIG = 2u;                     // a launch with an odd stage count
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// true once the phase of this parity has completed; false after ~1 s
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > STG_WAIT_NS) return false;
+    return true;
+}
+// bulk copy global -> shared, completing on the mbarrier's transaction count;
+// both addresses 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__host__ __device__ inline size_t stg_round128(size_t b) { return (b + 127) / 128 * 128; }
+
+// bytes of one stage: Q directions x R rows x nxp values, then R x nxp class bytes
+template <int Q, class S>
+__host__ __device__ inline size_t stg_stage_bytes(int R, int nxp)
+{
+    return stg_round128((size_t)Q * R * nxp * sizeof(typename S::T) + (size_t)R * nxp);
+}
+
+// producer warp: stage the source rows of tile t (plane z, rows y0 .. y0+nr-1).
+// Lane 0 arms the full barrier with the tile's bytes; then lane a < Q copies
+// direction a's rows (shift ey, ez of that lane) and lane Q the class bytes,
+// so the copies of a tile are issued in parallel
+template <int Q, class S>
+__device__ __forceinline__ void stg_issue(const typename S::T* __restrict__ src, const uint8_t* __restrict__ cls,
+                                          const Geo& g, int R, int nty, int t, unsigned char* stage, uint64_t* bar,
+                                          int lane, int ey, int ez)
+{
+    using T = typename S::T;
+    const int z = t / nty, y0 = (t - z * nty) * R;
+    const int nr = min(R, g.ny - y0);
+    const uint32_t rowb = (uint32_t)g.nxp * (uint32_t)sizeof(T);
+    if (lane == 0) mbar_expect_tx(bar, (uint32_t)Q * nr * rowb + (uint32_t)nr * g.nxp);
+    __syncwarp();
+    if (lane < Q) {
+        const int zs = wrapi(z - ez, g.nz);
+        const int ys0 = y0 - ey;
+        T* d = reinterpret_cast<T*>(stage) + (size_t)lane * R * g.nxp;
+        const T* s = src + (long long)lane * g.sq + (long long)zs * g.ny * g.nxp;
+        if (ys0 < 0) {                       // row -1 is row ny-1
+            bulk_g2s(d, s + (long long)(g.ny - 1) * g.nxp, rowb, bar);
+            if (nr > 1) bulk_g2s(d + g.nxp, s, (uint32_t)(nr - 1) * rowb, bar);
+        } else if (ys0 + nr > g.ny) {        // row ny is row 0
+            const int n1 = g.ny - ys0;
+            if (n1 > 0) bulk_g2s(d, s + (long long)ys0 * g.nxp, (uint32_t)n1 * rowb, bar);
+            bulk_g2s(d + (size_t)n1 * g.nxp, s, (uint32_t)(nr - n1) * rowb, bar);
+        } else {
+            bulk_g2s(d, s + (long long)ys0 * g.nxp, (uint32_t)nr * rowb, bar);
+        }
+    } else if (lane == Q) {
+        bulk_g2s(stage + (size_t)Q * R * g.nxp * sizeof(T), cls + ((long long)z * g.ny + y0) * g.nxp,
+                 (uint32_t)nr * g.nxp, bar);
+    }
+}
+
+// the pair (x0, x0+1) of direction a from a staged row: the pull sources
+// x0 - E_x and x0 + 1 - E_x, wrapped at the row ends (periodic x)
+template <int Q, class S>
+__device__ __forceinline__ float2 stg_pair(const typename S::T* __restrict__ row, int a, int x0, int nx)
+{
+    using T = typename S::T;
+    const int ex = EX<Q>(a);
+    if constexpr (sizeof(T) == 2) {
+        const uint32_t w = *reinterpret_cast<const uint32_t*>(row + x0);
+        if (ex == 0) return S::unpack2(w);
+        const unsigned short* h = reinterpret_cast<const unsigned short*>(row);
+        if (ex == 1) {                                    // values x0-1, x0
+            const uint32_t e = h[x0 == 0 ? nx - 1 : x0 - 1];
+            return S::unpack2(__byte_perm(e, w, 0x5410));
+        }
+        const uint32_t e = h[x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2];   // values x0+1, x0+2
+        return S::unpack2(__byte_perm(w, e, 0x5432));
+    } else {
+        const float2 v = *reinterpret_cast<const float2*>(row + x0);
+        if (ex == 0) return v;
+        if (ex == 1) return make_float2(row[x0 == 0 ? nx - 1 : x0 - 1], v.x);
+        return make_float2(v.y, row[x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2]);
+    }
+}
+
+// the canonical post-propagation deviations d_b(x) (storage units) of a node
+// of a box periodic on every axis with halfway walls, as gather_node: the
+// pull source P_b(x - E_b), or through a link into a solid node the bounced
+// P_opp(b)(x) plus Ladd's term of the solid's wall.  Every load is issued
+// before any is used (one memory round trip for the boundary warps).
+template <int Q, class S>
+__device__ __forceinline__ void gather_periodic(const typename S::T* __restrict__ P, const uint8_t* __restrict__ cls,
+                                                const Geo& g, const KP<typename S::R>& p, int x, int y, int z,
+                                                long long own, typename S::R (&d)[Q])
+{
+    using T = typename S::T;
+    using R = typename S::R;
+    uint8_t cs[Q];
+    T pv[Q], bv[Q];
+#pragma unroll
+    for (int b = 1; b < Q; ++b) {
+        const int xs = wrapi(x - EX<Q>(b), g.nx), ys = wrapi(y - EY<Q>(b), g.ny), zs = wrapi(z - EZ<Q>(b), g.nz);
+        const long long src = ((long long)zs * g.ny + ys) * g.nxp + xs;
+        cs[b] = cls[src];
+        pv[b] = P[(long long)b * g.sq + src];
+        bv[b] = P[(long long)OPP<Q>(b) * g.sq + own];
+    }
+    d[0] = S::to_raw(P[own]);
+#pragma unroll
+    for (int b = 1; b < Q; ++b) {
+        if (nc_solid(cs[b])) {
+            const int wall = nc_wall(cs[b]);
+            const R L = R(WD<Q>(b)) * (R(EX<Q>(b)) * p.LW[wall][0] + R(EY<Q>(b)) * p.LW[wall][1] +
+                                       R(EZ<Q>(b)) * p.LW[wall][2]);
+            d[b] = S::to_raw(bv[b]) + L;
+        } else {
+            d[b] = S::to_raw(pv[b]);
+        }
+    }
+}
+
+template <int Q, class S, bool SR>
+__global__ void __launch_bounds__(STG_THREADS, 1)
+k_step_staged(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
+              const uint8_t* __restrict__ cls, const uint32_t* __restrict__ special, long long nspecial, const Geo g,
+              const KP<float> p, uint32_t seed, int R, int ntiles, int nstages, unsigned* __restrict__ errflag)
+{
+    using T = typename S::T;
+    using Rt = typename S::R;
+    static_assert(sizeof(Rt) == 4, "the staged step computes in FP32");
+    extern __shared__ __align__(128) unsigned char smem[];
+    const size_t stage_bytes = stg_stage_bytes<Q, S>(R, g.nxp);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)nstages * stage_bytes);
+    uint64_t* empty = full + nstages;
+    const int nty = (g.ny + R - 1) / R;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the barrier protocol needs an even number of stages (see above)
+    if (nstages < 2 || (nstages & 1) || nstages > STG_MAX_STAGES) {
+        if (threadIdx.x == 0) atomicOr(errflag, STG_ERR_CONFIG);
+        return;
+    }
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < nstages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], STG_GROUP_WARPS);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const int my_tiles = ((int)blockIdx.x < ntiles) ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+    if (warp == STG_CWARPS) {
+        // producer warp: refill a stage once the group that read it released it
+        int ey = 0, ez = 0;                  // the pull shift of this lane's direction
+#pragma unroll
+        for (int b = 0; b < Q; ++b)
+            if (b == lane) {
+                ey = EY<Q>(b);
+                ez = EZ<Q>(b);
+            }
+        int k = 0;
+        for (; k < my_tiles; ++k) {
+            const int s = k % nstages, use = k / nstages;
+            if (use > 0) {
+                int ok = 0;
+                if (lane == 0) ok = mbar_wait_bounded(&empty[s], (uint32_t)(use - 1) & 1u) ? 1 : 0;
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) {
+                    if (lane == 0) atomicOr(errflag, STG_ERR_TIMEOUT);
+                    break;
+                }
+            }
+            stg_issue<Q, S>(src, cls, g, R, nty, (int)blockIdx.x + k * (int)gridDim.x, smem + (size_t)s * stage_bytes,
+                            &full[s], lane, ey, ez);
+        }
+        if (k < my_tiles && lane == 0) {
+            // stopped early: let the copies already issued land before leaving
+            for (int j = (k > nstages ? k - nstages : 0); j < k; ++j)
+                mbar_wait_bounded(&full[j % nstages], (uint32_t)(j / nstages) & 1u);
+        }
+        return;
+    }
+
+    if (warp == STG_CWARPS + 1) {
+        // boundary warp: the listed chunks, node by node (lane per node)
+        const long long nn = 4 * nspecial;
+        for (long long j = (long long)blockIdx.x * 32 + lane; j < nn; j += (long long)gridDim.x * 32) {
+            const long long node = (long long)special[j >> 2] + (j & 3);
+            const int x = (int)(node % g.nxp);
+            const long long row = node / g.nxp;
+            const int y = (int)(row % g.ny), z = (int)(row / g.ny);
+            const uint8_t c = cls[node];
+            if (x >= g.nx || nc_solid(c) || c == NC_PAD) {
+#pragma unroll
+                for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + node] = S::from_raw(Rt(0));
+                continue;
+            }
+            Rt d[Q];
+            gather_periodic<Q, S>(src, cls, g, p, x, y, z, node, d);
+            NodeM<Rt> m;
+            node_macro<Rt, Q, false, false>(d, p, m);
+            node_relax<Rt, Q, false>(d, p, m);
+            if constexpr (SR) {
+                NodeRng rng((uint32_t)node, seed);
+#pragma unroll
+                for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + node] = S::from_raw_sr(d[a], rng.bits(a));
+            } else {
+#pragma unroll
+                for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + node] = S::from_raw(d[a]);
+            }
+        }
+        return;
+    }
+
+    const int group = warp / STG_GROUP_WARPS, gw = warp % STG_GROUP_WARPS;
+    const int tasks_per_row = g.nxp / STG_TASK_NODES;
+    const long long sq = g.sq;
+    for (int k = group; k < my_tiles; k += STG_GROUPS) {
+        const int s = k % nstages, use = k / nstages;
+        if (!mbar_wait_bounded(&full[s], (uint32_t)use & 1u)) {
+            if (lane == 0) atomicOr(errflag, STG_ERR_TIMEOUT);
+            return;
+        }
+        const int t = (int)blockIdx.x + k * (int)gridDim.x;
+        const int z = t / nty, y0 = (t - z * nty) * R;
+        const int nr = min(R, g.ny - y0);
+        const T* sp = reinterpret_cast<const T*>(smem + (size_t)s * stage_bytes);
+        const uint8_t* sc = smem + (size_t)s * stage_bytes + (size_t)Q * R * g.nxp * sizeof(T);
+        for (int task = gw; task < nr * tasks_per_row; task += STG_GROUP_WARPS) {
+            const int r = task / tasks_per_row;
+            const int x0 = (task - r * tasks_per_row) * STG_TASK_NODES + 2 * lane;
+            const int y = y0 + r;
+            const long long base = ((long long)z * g.ny + y) * g.nxp + x0;
+            // the pair path serves pairs whose aligned 4-node chunk is all bulk,
+            // as in k_step (whose vector chunks are 4 nodes), so both kernels
+            // run the same code on every node
+            const uint32_t cb = *reinterpret_cast<const uint32_t*>(sc + (size_t)r * g.nxp + (x0 & ~3));
+            if (cb == 0u) {
+                F2 dd[Q];
+#pragma unroll
+                for (int a = 0; a < Q; ++a)
+                    dd[a] = F2{stg_pair<Q, S>(sp + ((size_t)a * R + r) * g.nxp, a, x0, g.nx)};
+                pair_collide<Q>(dd, p);
+                if constexpr (sizeof(T) == 2) {
+                    if constexpr (SR) {
+                        NodeRng rp((uint32_t)base, seed);
+#pragma unroll
+                        for (int a = 0; a < Q; ++a)
+                            *reinterpret_cast<uint32_t*>(dst + (long long)a * sq + base) =
+                                S::pack2_sr(dd[a].v.x, dd[a].v.y, rp.word());
+                    } else {
+#pragma unroll
+                        for (int a = 0; a < Q; ++a)
+                            *reinterpret_cast<uint32_t*>(dst + (long long)a * sq + base) =
+                                S::pack2(dd[a].v.x, dd[a].v.y);
+                    }
+                } else {
+#pragma unroll
+                    for (int a = 0; a < Q; ++a) *reinterpret_cast<float2*>(dst + (long long)a * sq + base) = dd[a].v;
+                }
+            }
+            // other chunks are the boundary warps' (listed on the host)
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);     // this warp is done with stage s
+    }
+}
+
+}  // namespace lbm

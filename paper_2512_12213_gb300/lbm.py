@@ -22,6 +22,7 @@ D2Q9, D3Q19 = 9, 19
 FORCE = {"a": 0, "b": 1, "c": 2, "d": 3, "e": 4}
 STORE = {"f64": 0, "f32": 1, "f16s": 2, "bf16s": 3}
 ROUND = {"nearest": 0, "stochastic": 1}
+STEP_KERNEL = {"auto": 0, "register": 1, "staged": 2}
 S1, S2, S3, S4 = 1, 2, 3, 4
 MOVING_CORR, MAXWELL_REMOVE, ACCUMULATE = 1, 2, 4
 OUT_DEVICE, OUT_HOST, OUT_HOST_ASYNC = 0, 1, 2
@@ -64,6 +65,7 @@ class LbmConfig(ctypes.Structure):
         ("induced", ctypes.c_int32),
         ("eta", ctypes.c_double),
         ("mag_conducting", ctypes.c_int32),
+        ("step_kernel", ctypes.c_int32),
     ]
 
 
@@ -133,7 +135,8 @@ def make_config(lattice=9, nx=4, ny=4, nz=1, periodic=(1, 1, 1), dx=1.0, dt=1.0,
                 force_model="e", g=(0.0, 0.0, 0.0), lorentz=0, B=(0.0, 0.0, 0.0), E=(0.0, 0.0, 0.0),
                 sigma_e=0.0, mu=1.0, maxwell=0, les=0, cs=0.1, storage="f64", wall_u=(),
                 face_wall=(1, 1, 1, 1, 1, 1), rounding="nearest", seed=0, insulating=0, curved=0,
-                stokes=0, darcy=0.0, induced=0, eta=0.0, mag_conducting=0, **_ignored) -> LbmConfig:
+                stokes=0, darcy=0.0, induced=0, eta=0.0, mag_conducting=0, step_kernel="auto",
+                **_ignored) -> LbmConfig:
     c = LbmConfig()
     c.lattice, c.nx, c.ny, c.nz = int(lattice), int(nx), int(ny), int(nz)
     for k in range(3):
@@ -156,6 +159,7 @@ def make_config(lattice=9, nx=4, ny=4, nz=1, periodic=(1, 1, 1), dx=1.0, dt=1.0,
     c.curved = int(curved)
     c.stokes, c.darcy = int(stokes), float(darcy)
     c.induced, c.eta, c.mag_conducting = int(induced), float(eta), int(mag_conducting)
+    c.step_kernel = STEP_KERNEL[step_kernel] if isinstance(step_kernel, str) else int(step_kernel)
     return c
 
 

@@ -222,3 +222,14 @@ def test_header_is_plain_c(tmp_path):
     r = subprocess.run([gcc, str(obj), so, "-o", str(exe), "-Wl,-rpath," + os.path.dirname(so)],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+@pytest.mark.parametrize("change", [dict(periodic=(1, 0, 1)), dict(storage="f64"), dict(les=1),
+                                    dict(maxwell=1), dict(lorentz=1, sigma_e=0.1)])
+def test_staged_kernel_refused_where_it_does_not_apply(lib, change):
+    cfg, mask = workloads.sphere(nx=32, ny=16, nz=16, radius=4, center=(8, 8, 8), storage="f16s")
+    c = lbm.make_config(**dict(cfg, step_kernel="staged", face_wall=(1, 1, 1, 1, 1, 1), **change))
+    with pytest.raises(lbm.LbmError, match="staged"):
+        lbm.lbm_buffer_sizes(c, mask)
+    # the same configuration with the automatic choice is accepted
+    lbm.lbm_buffer_sizes(lbm.make_config(**dict(cfg, face_wall=(1, 1, 1, 1, 1, 1), **change)), mask)

@@ -118,3 +118,18 @@ def test_reference_fields_zero_and_reversed(orc):
     assert r2 == pytest.approx(2.0, rel=1e-14)
     _, _, rs, _ = orc.residual(cfg, mask, f, v)
     assert rs == 0.0
+
+
+def test_openmp_timing_build_gives_the_same_state(orc):
+    """The OpenMP timing copy of the oracle (parallel node loops only) steps
+    to exactly the state of the single-threaded parity build."""
+    from paper_2512_12213_gb300 import inputs
+    nx, ny, nz = 17, 9, 6
+    mask = inputs.sphere_mask(nx, ny, nz, (8.2, 4.1, 3.0), 2.4, wall=1)
+    cfg = orc.make_cfg(q=19, nx=nx, ny=ny, nz=nz, periodic=(1, 0, 1), tau=0.7, force_model="e",
+                       g=(1e-4, 0, 2e-5), wall_u=((0, 0, 0), (0.02, 0, 0)), face_wall=(1, 1, 1, 2, 1, 1))
+    rho, u = inputs.smooth_fields(nx, ny, nz, dims=3, u_amplitude=0.03, seed=5)
+    f = orc.init(cfg, mask, rho, u)
+    a = orc.run(cfg, mask, f, 5)
+    b = orc.run(cfg, mask, f, 5, omp=True)
+    assert np.array_equal(a, b)
