@@ -43,6 +43,9 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--repeats", type=int, default=5, help="timed blocks of --steps steps; the median is reported")
+    p.add_argument("--study", default=None, choices=["steady"],
+                   help="instead of the benchmark: run the sphere to steady state in every storage (long)")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--drag-steps", type=int, default=2000)
     p.add_argument("--no-extras", action="store_true", help="headline only")
@@ -201,17 +204,18 @@ def make_workload(workloads, name, storage):
     return out if len(out) == 3 else (out[0], out[1], None)
 
 
-def timed_run(torch, lbm, sim, steps, warmup, wall=1, events=True):
-    """Warm up, then time `steps` steps with CUDA events on the launching
-    stream.  A step is the fused collide-stream kernel plus the FP64 wall
-    force of the interval it advances over; the force reads the stored state
-    that the step only reads, so it runs on a second stream beside the step
-    (it waits for the previous step, and the next step waits for it).
-    Returns (total_ms, mean step-kernel ms)."""
+def timed_run(torch, lbm, sim, steps, warmup, wall=1, events=True, repeats=1):
+    """Warm up, then time `repeats` blocks of exactly `steps` steps with CUDA
+    events on the launching stream.  A step is the fused collide-stream
+    kernel plus the FP64 wall force of the interval it advances over; the
+    force reads the stored state that the step only reads, so it runs on a
+    second stream beside the step (it waits for the previous step, and the
+    next step waits for it).  Returns (median block ms, every block's ms,
+    mean step-kernel ms over all blocks)."""
     st = sim.stream
     cs = torch.cuda.current_stream()
     side = torch.cuda.Stream(device=cs.device)
-    hist = torch.zeros((max(steps, warmup), 3), dtype=torch.float64, device=sim.device)
+    hist = torch.zeros((max(steps, warmup, 1), 3), dtype=torch.float64, device=sim.device)
 
     def one(i, a=None, b=None):
         side.wait_stream(cs)
@@ -227,17 +231,21 @@ def timed_run(torch, lbm, sim, steps, warmup, wall=1, events=True):
     for i in range(warmup):
         one(i)
     torch.cuda.synchronize()
-    a = [torch.cuda.Event(enable_timing=True) for _ in range(steps)] if events else [None] * steps
-    b = [torch.cuda.Event(enable_timing=True) for _ in range(steps)] if events else [None] * steps
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record(cs)
-    for i in range(steps):
-        one(i, a[i], b[i])
-    t1.record(cs)
-    torch.cuda.synchronize()
-    total = t0.elapsed_time(t1)
-    kern = sum(x.elapsed_time(y) for x, y in zip(a, b)) / steps if events else None
-    return total, kern
+    blocks, kern = [], []
+    for _ in range(repeats):
+        a = [torch.cuda.Event(enable_timing=True) for _ in range(steps)] if events else [None] * steps
+        b = [torch.cuda.Event(enable_timing=True) for _ in range(steps)] if events else [None] * steps
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(cs)
+        for i in range(steps):
+            one(i, a[i], b[i])
+        t1.record(cs)
+        torch.cuda.synchronize()
+        blocks.append(t0.elapsed_time(t1))
+        if events:
+            kern.extend(x.elapsed_time(y) for x, y in zip(a, b))
+    return statistics.median(blocks), blocks, (sum(kern) / len(kern) if events else None)
 
 
 def run_ours(args):
@@ -267,6 +275,7 @@ def run_ours(args):
     if phi is not None:
         sim.set_wall_distance(phi)
     sim.rest()
+    step_kernel = sim.step_kernel
     N = cfg["nx"] * cfg["ny"] * cfg["nz"]
     fluid = int((mask == 0).sum())
     bpn = bytes_per_node(19, args.storage, induced=bool(cfg.get("induced")))
@@ -274,20 +283,25 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.active = True
-    total_ms, kern_ms = timed_run(torch, lbm, sim, args.steps, args.warmup, wall=hwall)
+    total_ms, blocks_ms, kern_ms = timed_run(torch, lbm, sim, args.steps, args.warmup, wall=hwall,
+                                             repeats=args.repeats)
     clocks.active = False
     total_ms = max_over_ranks(torch, dist, ws, total_ms, "cuda")
     ms_step = total_ms / args.steps
     value = whole_job_mlups(ws, N, args.steps, total_ms)
     achieved = N * bpn / (kern_ms * 1e-3) / 1e9
     kname = {"f64": "StoreF64", "f32": "StoreF32", "f16s": "StoreF16", "bf16s": "StoreBF16"}[args.storage]
-    kernel = (EXTENSIONS[args.workload][1].replace(",S", "," + kname) if args.workload in EXTENSIONS
-              else f"k_step<19,{kname},EXT={int(bool(cfg.get('les')))},SR={int(sr)}>")
+    if args.workload in EXTENSIONS:
+        kernel = EXTENSIONS[args.workload][1].replace(",S", "," + kname)
+    elif step_kernel == "staged":
+        kernel = f"k_step_staged<19,{kname},SR={int(sr)}>"
+    else:
+        kernel = f"k_step<19,{kname},EXT={int(bool(cfg.get('les')))},SR={int(sr)}>"
     roof = {"kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1),
             "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "peak_source": peak_kind,
             "bytes_per_node": bpn, "step_kernel_ms": round(kern_ms, 5),
             "kernel_mlups": round(N / (kern_ms * 1e-3) / 1e6, 1),
-            "traffic": traffic_for(f"{args.workload}256_{args.storage}{'_sr' if sr else ''}")}
+            "traffic": traffic_for(f"{args.workload}256_{args.storage}{'_sr' if sr else ''}_{step_kernel}")}
     sim.close()
     del sim
     torch.cuda.empty_cache()
@@ -304,7 +318,7 @@ def run_ours(args):
             s = lbm.Sim(c, m)
             s.rest()
             clocks.active = True
-            t, k = timed_run(torch, lbm, s, steps, args.warmup)
+            t, _, k = timed_run(torch, lbm, s, steps, args.warmup)
             clocks.active = False
             bp = bytes_per_node(19, storage)
             ach = N * bp / (k * 1e-3) / 1e9
@@ -318,6 +332,8 @@ def run_ours(args):
                                "achieved_gbs": roof["achieved"], "frac": roof["frac"]}
         out["storage_variants"] = variants
         out["drag_error_vs_f64"] = drag_errors(torch, lbm, workloads, args.drag_steps)
+        out["near_steady_vs_f64"] = {f"re{re}": near_steady(torch, lbm, workloads, re) for re in (20, 100)}
+        out["steady_state_study"] = steady_record()
         out["cavity_les_f32"] = cavity_bench(torch, lbm, workloads, hbm, args)
         out["cavity_sweep"] = cavity_sweep(torch, lbm, workloads, hbm, args)
         out["extensions_f32"] = extensions_bench(torch, lbm, workloads, hbm, args)
@@ -343,6 +359,10 @@ def run_ours(args):
                   "written per step",
                        "parallelism": f"{ws} independent replica(s)"},
             "roofline": roof, "gpu_launches": 3 * args.steps, "clocks": clocks.summary(),
+            "repeats": {"blocks": args.repeats, "block_ms": [round(b, 4) for b in blocks_ms],
+                        "value_from": "median block; gpu_launches counts one block (step kernel, link kernel, "
+                                      "fixed-order reduction per step)"},
+            "step_kernel": step_kernel,
         }
         if e2e:
             line["e2e"] = e2e
@@ -355,19 +375,41 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def sphere_measure(s, mask, cfg, radius=12):
+    """(drag F_x on the sphere, mean fluid velocity U, C_d, Re) of a sphere
+    context after a step: F from the FP64 momentum exchange of the last step,
+    U = M_x / mass, C_d = F / (rho U^2 pi r^2 / 2), Re = U 2r / nu."""
+    F = s.wall_force(1)[0]
+    mass, mom, _ = s.balance()
+    fluid = int((mask == 0).sum())
+    U = mom[0] / mass
+    rho = mass / fluid
+    nu = (cfg["tau"] - 0.5) / 3
+    return F, U, F / (0.5 * rho * U * U * np.pi * radius ** 2), U * 2 * radius / nu
+
+
+PRECISIONS = ("f64", "f32", "f16s", "bf16s", "f16s_sr", "bf16s_sr")
+
+
+def _sphere_sim(lbm, workloads, key, Re=20):
+    storage = key.split("_")[0]
+    c, m = workloads.sphere(storage=storage, Re=Re)
+    if key.endswith("_sr"):
+        c = dict(c, rounding="stochastic", seed=2024)
+    return c, m, lbm.Sim(c, m)
+
+
 def drag_errors(torch, lbm, workloads, steps, checkpoints=(1000, 5000, 20000), radius=12):
-    """Drag on the sphere from rest in each storage format, relative to FP64:
-    at fixed steps of the transient (`checkpoints`), averaged over the first
-    `steps` steps, and as the drag coefficient C_d = F / (rho U^2 pi r^2 / 2)
-    at the last checkpoint, U the mean fluid velocity there."""
+    """Drag on the sphere (Re 20 configuration) from rest in each storage
+    format, relative to FP64: at fixed steps of the start-up transient
+    (`checkpoints`), averaged over the first `steps` steps, and as the drag
+    coefficient C_d = F / (rho U^2 pi r^2 / 2) at the last checkpoint, U the
+    mean fluid velocity there (the flow is still accelerating: see the
+    near-steady block for the calibrated Reynolds number)."""
     T = max(max(checkpoints), steps)
     res = {}
-    for key in ("f64", "f32", "f16s", "bf16s", "f16s_sr", "bf16s_sr"):
-        storage = key.split("_")[0]
-        c, m = workloads.sphere(storage=storage)
-        if key.endswith("_sr"):
-            c = dict(c, rounding="stochastic", seed=2024)
-        s = lbm.Sim(c, m)
+    for key in PRECISIONS:
+        c, m, s = _sphere_sim(lbm, workloads, key)
         s.rest()
         st = s.stream
         acc = torch.zeros(3, dtype=torch.float64, device=s.device)
@@ -378,26 +420,80 @@ def drag_errors(torch, lbm, workloads, steps, checkpoints=(1000, 5000, 20000), r
                 lbm.lbm_wall_force(s.ctx, 1, lbm.ACCUMULATE, 1.0 / steps, acc, 0, st)
             if i + 1 in checkpoints:
                 lbm.lbm_wall_force(s.ctx, 1, 0, 1.0, at[checkpoints.index(i + 1)], 0, st)
-        mass, mom, _ = s.balance()
-        fluid = int((m == 0).sum())
-        U = mom[0] / mass
-        rho = mass / fluid
+        F, U, cd, re = sphere_measure(s, m, c, radius)
         Fx = at[:, 0].cpu().numpy()
-        res[key] = {"at": Fx, "mean": float(acc[0].item()),
-                    "cd": float(Fx[-1] / (0.5 * rho * U * U * np.pi * radius ** 2)),
-                    "re": float(U * 2 * radius / ((c["tau"] - 0.5) / 3))}
+        res[key] = {"at": Fx, "mean": float(acc[0].item()), "cd": cd, "re": re}
         s.close()
         del s
         torch.cuda.empty_cache()
     ref = res["f64"]
-    out = {"checkpoints": list(checkpoints), "mean_window": steps,
+    out = {"workload": "sphere 256x128x128 from rest, Re 20 configuration (tau 0.68, calibrated g)",
+           "checkpoints": list(checkpoints), "mean_window": steps,
            "f64_drag_at": [float(v) for v in ref["at"]], "f64_drag_mean": ref["mean"],
            "f64_cd_at_last": ref["cd"], "re_at_last": ref["re"]}
-    for k in ("f32", "f16s", "bf16s", "f16s_sr", "bf16s_sr"):
+    for k in PRECISIONS[1:]:
         out[k] = {"rel_err_at": [float(abs(a / b - 1)) for a, b in zip(res[k]["at"], ref["at"])],
                   "rel_err_mean": abs(res[k]["mean"] / ref["mean"] - 1),
                   "cd_rel_err": abs(res[k]["cd"] / ref["cd"] - 1)}
     return out
+
+
+def near_steady(torch, lbm, workloads, Re, checkpoints=(2000, 5000, 10000), radius=12):
+    """The sphere at the calibrated Reynolds number: every storage format
+    starts from the same uniform stream at the target speed (U0 of the
+    workload) and runs 10,000 steps; at each checkpoint the drag, the mean
+    velocity U, C_d and Re are compared with FP64, and at the last one the
+    S2 shear stress field too (max |sigma - sigma_FP64| / max |sigma_FP64|
+    over the fluid nodes)."""
+    U0 = workloads.SPHERE_RE[Re]["U0"]
+    res, sig64 = {}, None
+    for key in PRECISIONS:
+        c, m, s = _sphere_sim(lbm, workloads, key, Re)
+        nz, ny, nx = m.shape
+        u = torch.zeros((3, nz, ny, nx), dtype=torch.float64, device=s.device)
+        u[0] = U0 * torch.from_numpy(m == 0).to(s.device)
+        s.init_equilibrium(torch.ones((nz, ny, nx), dtype=torch.float64, device=s.device), u)
+        rows, done = [], 0
+        for cp in checkpoints:
+            s.step(cp - done)
+            done = cp
+            rows.append(sphere_measure(s, m, c, radius))
+        sig = s.stress(lbm.S2)[0].double()
+        if key == "f64":
+            sig64 = sig
+            sig_err = 0.0
+        else:
+            sig_err = float((sig - sig64).abs().max() / sig64.abs().max())
+        res[key] = {"rows": rows, "sigma_rel_err": sig_err}
+        s.close()
+        del s, sig
+        torch.cuda.empty_cache()
+    del sig64
+    torch.cuda.empty_cache()
+    ref = res["f64"]["rows"]
+    out = {"workload": f"sphere 256x128x128, Re {Re} configuration (tau {workloads.SPHERE_RE[Re]['tau']}, "
+                       f"g {workloads.SPHERE_RE[Re]['g']:.5g}), from a uniform stream at U0 = {U0}",
+           "checkpoints": list(checkpoints),
+           "f64": {"drag": [r[0] for r in ref], "U": [r[1] for r in ref], "cd": [r[2] for r in ref],
+                   "re": [r[3] for r in ref]}}
+    for k in PRECISIONS[1:]:
+        rows = res[k]["rows"]
+        out[k] = {"drag_rel_err": [abs(a[0] / b[0] - 1) for a, b in zip(rows, ref)],
+                  "U_rel_err": [abs(a[1] / b[1] - 1) for a, b in zip(rows, ref)],
+                  "cd_rel_err": [abs(a[2] / b[2] - 1) for a, b in zip(rows, ref)],
+                  "sigma_s2_rel_err_at_last": res[k]["sigma_rel_err"]}
+    return out
+
+
+def steady_record():
+    """The steady-state study as last recorded (profiles/steady_sphere.json,
+    written by `python bench.py --study steady`), or None."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "steady_sphere.json")))
+        d["source"] = "profiles/steady_sphere.json (python bench.py --study steady)"
+        return d
+    except Exception:
+        return None
 
 
 def cavity_bench(torch, lbm, workloads, hbm, args):
@@ -407,7 +503,7 @@ def cavity_bench(torch, lbm, workloads, hbm, args):
     s.rest()
     N = n ** 3
     steps = max(args.steps // 4, 50)
-    t, k = timed_run(torch, lbm, s, steps, args.warmup, wall=2)
+    t, _, k = timed_run(torch, lbm, s, steps, args.warmup, wall=2)
     bp = bytes_per_node(19, "f32")
     ach = N * bp / (k * 1e-3) / 1e9
     s.close()
@@ -435,7 +531,7 @@ def cavity_sweep(torch, lbm, workloads, hbm, args, sizes=(128, 256, 512), steps=
             N = n ** 3
             s.init_equilibrium(torch.full((n, n, n), 1.0, dtype=torch.float64, device=s.device),
                                torch.zeros((3, n, n, n), dtype=torch.float64, device=s.device))
-            t, k = timed_run(torch, lbm, s, steps, 3, wall=2)
+            t, _, k = timed_run(torch, lbm, s, steps, 3, wall=2)
             bp = bytes_per_node(19, storage)
             ach = N * bp / (k * 1e-3) / 1e9
             row[storage] = {"mlups": round(N * steps / (t * 1e-3) / 1e6, 1),
@@ -462,7 +558,7 @@ def extensions_bench(torch, lbm, workloads, hbm, args):
             s.set_wall_distance(phi)
         s.rest()
         N = c["nx"] * c["ny"] * c["nz"]
-        t, k = timed_run(torch, lbm, s, steps, args.warmup)
+        t, _, k = timed_run(torch, lbm, s, steps, args.warmup)
         bp = bytes_per_node(19, "f32", induced=bool(c.get("induced")))
         ach = N * bp / (k * 1e-3) / 1e9
         res[name] = {"workload": desc, "kernel": kernel.replace(",S", ",StoreF32"), "steps": steps,
@@ -518,11 +614,11 @@ def adjoint_bench(torch, lbm, workloads, hbm):
     from paper_2512_12213_gb300 import adjoint
     out = {}
     c, m = workloads.cylinder(storage="f32")
-    T = 400
+    T = 2000
     out["cylinder_2d"] = dict(workload=f"D2Q9 cylinder r=20 in 512x256, T={T} (sqrt(T) checkpoints), FP32",
                               **adjoint_case(torch, lbm, adjoint, c, m, T, hbm))
     c, m = workloads.sphere_small(storage="f32")
-    T = 100
+    T = 2000
     out["sphere_3d"] = dict(workload=f"D3Q19 sphere r=10 in 128^3, T={T} (sqrt(T) checkpoints), FP32",
                             **adjoint_case(torch, lbm, adjoint, c, m, T, hbm))
     return out
@@ -567,7 +663,10 @@ def e2e_bench(torch, lbm, workloads, args):
     state_bytes = 19 * N * 4
     return {"value": round(N * steps / (t1 - t0) / 1e6, 1), "unit": "MLUPS",
             "h2d_bytes_per_step": round(state_bytes / steps, 1),
-            "d2h_bytes_per_step": round((state_bytes + 24 * steps) / steps, 1)}
+            "d2h_bytes_per_step": round((state_bytes + 24 * steps) / steps, 1),
+            "note": (f"per run: the canonical FP32 state ({state_bytes} B) in from pinned host memory and out "
+                     f"again; per step: the 24-byte drag out (asynchronous, beside the next step); the byte "
+                     f"counts above spread the state copies over the {steps} steps")}
 
 
 def cpu_model():
@@ -663,6 +762,165 @@ def cpu_baseline(budget_s=10.0):
     return out
 
 
+# ------------------------------------------------------ steady-state study
+def _shift_mean_flow(torch, lbm, sim, fluid, dU):
+    """Re-initialise the state at equilibrium with the node's density and
+    flow velocity (from the library's residual and stress outputs) plus dU
+    along x at the fluid nodes: a new initial condition for the same
+    dynamics, which moves the slow mean-flow mode toward its steady value
+    (the steady state reached afterwards does not depend on it)."""
+    v = sim.velocity_buffer()
+    sim.residual(v)
+    rho = sim.stress(lbm.S2)[2].double()
+    v[0] += dU * fluid
+    sim.init_equilibrium(rho, v)
+
+
+def _aitken(u0, u1, u2):
+    """Limit of a geometric sequence from three equally spaced samples."""
+    d1, d2 = u1 - u0, u2 - u1
+    if d1 == 0.0 or not (0.0 < d2 / d1 < 0.98):
+        return u2            # not a converging geometric approach: no correction
+    return u2 - d2 * d2 / (d2 - d1)
+
+
+def _series(torch, lbm, sim, mask, cfg, steps, every, vref=None):
+    """Run `steps` steps sampling (step, F, U, C_d, Re, r) every `every` steps;
+    r is the residual over `every` steps when vref is given."""
+    out = []
+    for i in range(steps // every):
+        sim.step(every)
+        r = sim.residual(vref)[2] if vref is not None else None
+        out.append((every * (i + 1),) + sphere_measure(sim, mask, cfg) + (r,))
+    return out
+
+
+def _window(rows, frac=0.25):
+    """Means of F, U, C_d, Re over the last `frac` of a series, and the
+    spread (max - min) / mean of F there."""
+    w = rows[-max(2, int(len(rows) * frac)):]
+    F = [r[1] for r in w]
+    return {"F": float(np.mean(F)), "U": float(np.mean([r[2] for r in w])), "cd": float(np.mean([r[3] for r in w])),
+            "re": float(np.mean([r[4] for r in w])), "F_spread": float((max(F) - min(F)) / abs(np.mean(F)))}
+
+
+def steady_study(torch, lbm, workloads, budget_f64=300_000):
+    """The sphere (256x128x128, r = 12) at Re 20 and Re 100 run toward steady
+    state, FP64 first, then every reduced storage from the FP64 state.
+
+    FP64 is slow on GB300 (its arithmetic, not HBM, limits it), so the FP64
+    run starts from an FP32 run: a uniform stream at the target speed, two
+    mean-flow corrections (Aitken extrapolation of the mean velocity over
+    three equally spaced samples), then FP32 until its residual stops
+    falling; the FP32 state is exported in FP64, imported into the FP64
+    context and run with one more correction until the residual over 100
+    steps, r = sum |v(t) - v(t-100)| / sum |v(t)|, is below 1e-9 or the step
+    budget is spent.  At steady state the momentum-exchange drag equals the
+    body force on the fluid (the steady form of Eq. 32), which F / (g m)
+    checks.  Each reduced storage then starts from the FP64 state and runs
+    400,000 steps (Re 20) or 300,000 (Re 100); its drag, U and C_d are the
+    means over the last quarter of the run, against the FP64 values."""
+    out = {}
+    for Re in (20, 100):
+        res = {}
+        t0 = time.perf_counter()
+        c32, m, s32 = _sphere_sim(lbm, workloads, "f32", Re)
+        nz, ny, nx = m.shape
+        fluid = torch.from_numpy(m == 0).to(s32.device)
+        U0 = workloads.SPHERE_RE[Re]["U0"]
+        u = torch.zeros((3, nz, ny, nx), dtype=torch.float64, device=s32.device)
+        u[0] = U0 * fluid
+        s32.init_equilibrium(torch.ones((nz, ny, nx), dtype=torch.float64, device=s32.device), u)
+        warm = []
+        for cyc in range(3):
+            rows = _series(torch, lbm, s32, m, c32, 60_000, 2_000)
+            warm.extend(rows)
+            Us = [r[2] for r in rows]
+            U_inf = _aitken(np.mean(Us[6:10]), np.mean(Us[16:20]), np.mean(Us[26:30]))
+            if cyc < 2:
+                _shift_mean_flow(torch, lbm, s32, fluid, U_inf - Us[-1])
+        v32 = s32.velocity_buffer()
+        s32.residual(v32)
+        tail32 = _series(torch, lbm, s32, m, c32, 100_000, 2_000, v32)
+        res["f32_warmup"] = {"steps": 280_000, "last": tail32[-1][1:], "window": _window(tail32)}
+        f = s32.export_f()
+        s32.close()
+        del s32, v32
+        torch.cuda.empty_cache()
+        # FP64 from the FP32 state
+        c64, _, s64 = _sphere_sim(lbm, workloads, "f64", Re)
+        s64.import_f(f)
+        del f
+        rows = _series(torch, lbm, s64, m, c64, 30_000, 1_000)
+        Us = [r[2] for r in rows]
+        _shift_mean_flow(torch, lbm, s64, fluid, _aitken(np.mean(Us[3:7]), np.mean(Us[13:17]),
+                                                         np.mean(Us[23:27])) - Us[-1])
+        v64 = s64.velocity_buffer()
+        s64.residual(v64)
+        series64, steps64, r = [], 30_000, None
+        while steps64 < budget_f64:
+            chunk = _series(torch, lbm, s64, m, c64, 10_000, 100, v64)
+            series64.extend(chunk[-1:])
+            steps64 += 10_000
+            r = chunk[-1][5]
+            if r is not None and r < 1e-9:
+                break
+        mass, _, rho_a = s64.balance()
+        F, U, cd, re = sphere_measure(s64, m, c64)
+        g = c64["g"][0]
+        res["f64"] = {"steps": steps64, "r_100": r, "F": F, "U": U, "cd": cd, "re": re,
+                      "F_over_body_force": F / (g * mass), "F_over_sum_rho_a": F / rho_a[0],
+                      "series": [list(x) for x in series64], "window": _window(series64),
+                      "seconds": round(time.perf_counter() - t0, 1)}
+        ref = res["f64"]["window"] if (r is None or r >= 1e-9) else {"F": F, "U": U, "cd": cd, "re": re}
+        f64state = s64.export_f()
+        s64.close()
+        del s64, v64
+        torch.cuda.empty_cache()
+        steps = 400_000 if Re == 20 else 300_000
+        for key in PRECISIONS[1:]:
+            c, _, s = _sphere_sim(lbm, workloads, key, Re)
+            s.import_f(f64state)
+            rows = _series(torch, lbm, s, m, c, steps, 5_000)
+            w = _window(rows)
+            mass, _, _ = s.balance()
+            res[key] = {"steps": steps, "window": w, "F_over_body_force": w["F"] / (c["g"][0] * mass),
+                        "drag_rel_err": abs(w["F"] / ref["F"] - 1), "U_rel_err": abs(w["U"] / ref["U"] - 1),
+                        "cd_rel_err": abs(w["cd"] / ref["cd"] - 1),
+                        "series_U": [r[2] for r in rows[::8]]}
+            s.close()
+            del s
+            torch.cuda.empty_cache()
+        del f64state
+        torch.cuda.empty_cache()
+        res["reference"] = "f64 final state" if (r is not None and r < 1e-9) else "f64 last-quarter means"
+        out[f"re{Re}"] = res
+    return out
+
+
+def run_study(args):
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2512_12213_gb300 import build, lbm, workloads
+    build.build()
+    lbm.load()
+    clocks = Clocks(0)
+    clocks.start()
+    clocks.active = True
+    t0 = time.perf_counter()
+    res = steady_study(torch, lbm, workloads)
+    clocks.active = False
+    clocks.stop()
+    res["seconds"] = round(time.perf_counter() - t0, 1)
+    res["clocks"] = clocks.summary()
+    res["command"] = "python bench.py --study steady"
+    line = json.dumps(res, default=float)
+    print(line, flush=True)
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    with open(os.path.join(ROOT, "gpurun_out", "steady_sphere.json"), "w") as fh:
+        fh.write(line + "\n")
+
+
 # --------------------------------------------------------- reference arm
 def run_reference(args):
     """The FP64 CPU oracle as it stands on the headline workload's metric, on
@@ -714,7 +972,9 @@ def run_reference(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.study:
+        run_study(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

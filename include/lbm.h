@@ -323,6 +323,10 @@ lbm_status lbm_export_field(lbm_ctx* ctx, double* B, int on_host, void* stream);
 /* Current time T. */
 lbm_status lbm_time(const lbm_ctx* ctx, int64_t* t);
 
+/* The kernel that runs this context's step: LBM_STEP_REGISTER or
+ * LBM_STEP_STAGED (the automatic choice resolved at lbm_create). */
+lbm_status lbm_step_kernel(const lbm_ctx* ctx, int32_t* kind);
+
 /* The imposed electric field that the next step uses (3 doubles, host
  * memory; synchronises the stream): the configured E, or with insulating
  * walls the field set by the last step. */

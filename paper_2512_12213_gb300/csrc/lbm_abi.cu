@@ -883,6 +883,13 @@ lbm_status lbm_time(const lbm_ctx* ctx, int64_t* t)
     return LBM_OK;
 }
 
+lbm_status lbm_step_kernel(const lbm_ctx* ctx, int32_t* kind)
+{
+    if (!ctx || !kind) return LBM_ERR_ARG;
+    *kind = ctx->c.stage_R > 0 ? LBM_STEP_STAGED : LBM_STEP_REGISTER;
+    return LBM_OK;
+}
+
 lbm_status lbm_set_wall_distance(lbm_ctx* ctx, const float* phi_host, void* stream)
 {
     if (!ctx) return LBM_ERR_ARG;

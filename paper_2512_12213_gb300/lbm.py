@@ -91,6 +91,7 @@ _SIGS = {
     "lbm_save_state": [_vp, _vp, _vp],
     "lbm_load_state": [_vp, _vp, ctypes.c_int64, _vp],
     "lbm_time": [_vp, _P(ctypes.c_int64)],
+    "lbm_step_kernel": [_vp, _P(ctypes.c_int32)],
     "lbm_electric_field": [_vp, _P(ctypes.c_double), _vp],
     "lbm_set_wall_distance": [_vp, _P(ctypes.c_float), _vp],
     "lbm_export_field": [_vp, _vp, _i, _vp],
@@ -246,6 +247,13 @@ def lbm_time(ctx):
     t = ctypes.c_int64()
     _check(load().lbm_time(ctx, ctypes.byref(t)), ctx)
     return t.value
+
+
+def lbm_step_kernel(ctx):
+    """'staged' or 'register': the kernel that runs this context's step."""
+    k = ctypes.c_int32()
+    _check(load().lbm_step_kernel(ctx, ctypes.byref(k)), ctx)
+    return {1: "register", 2: "staged"}[k.value]
 
 
 def lbm_set_wall_distance(ctx, phi, stream):
@@ -408,6 +416,10 @@ class Sim:
 
     def step(self, n=1):
         lbm_step(self.ctx, n, self.stream)
+
+    @property
+    def step_kernel(self):
+        return lbm_step_kernel(self.ctx)
 
     @property
     def time(self):

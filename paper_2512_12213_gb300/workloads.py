@@ -76,14 +76,20 @@ def hartmann_induced(nx=2, ny=128, tau=0.8, Ha=4.0, B0=0.05, conducting=0, model
     return cfg, inputs.empty_mask(nx, ny)
 
 
-# body forces for the sphere case, from a Stokes estimate with a finite-Re
-# drag factor (the measured Reynolds number is reported by the benchmark)
-SPHERE_RE = {20: dict(tau=0.68, g=4.5e-7), 100: dict(tau=0.536, g=1.9e-7)}
+# The sphere case at Re = U 2r / nu in {20, 100} with U the mean fluid
+# velocity: tau fixes nu (0.06 and 0.012), U = 0.05 for both; the body force
+# g that holds the flow at U was calibrated on the GPU by drag matching
+# (start from a uniform stream at U, set g to the drag per unit fluid mass
+# once the flow around the sphere has formed, repeat, then run long): Re 20
+# measured 19.99 in FP32 after 360,000 steps; Re 100 (whose wake does not
+# settle to a steady state) about 98 at g = 9.224e-8, so g is raised by
+# (100/98)^1.5.  U0 is the stream the near-steady runs start from.
+SPHERE_RE = {20: dict(tau=0.68, g=3.33075e-7, U0=0.05), 100: dict(tau=0.536, g=9.5e-8, U0=0.05)}
 
 
 def sphere(nx=256, ny=128, nz=128, radius=12, Re=20, model="e", storage="f16s", center=(64, 64, 64)):
     """D3Q19 periodic box with a staircase sphere (wall id 1), body force
-    along x."""
+    along x (SPHERE_RE: tau and the calibrated g for Re 20 or 100)."""
     p = SPHERE_RE[Re]
     cfg = dict(lattice=19, nx=nx, ny=ny, nz=nz, periodic=(1, 1, 1), tau=p["tau"], force_model=model,
                g=(p["g"], 0.0, 0.0), storage=storage, wall_u=((0, 0, 0),))
