@@ -95,7 +95,7 @@ def peaks():
 
 # sources that compile into the step kernel (host code, the adjoint and the
 # allocation-free wall force are left out)
-STEP_SOURCES = ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_internal.h",
+STEP_SOURCES = ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_staged.cuh", "lbm_internal.h",
                 "inst_f64.cu", "inst_f32.cu", "inst_f16.cu", "inst_bf16.cu")
 
 
@@ -207,17 +207,30 @@ def make_workload(workloads, name, storage):
 def timed_run(torch, lbm, sim, steps, warmup, wall=1, events=True, repeats=1):
     """Warm up, then time `repeats` blocks of exactly `steps` steps with CUDA
     events on the launching stream.  A step is the fused collide-stream
-    kernel plus the FP64 wall force of the interval it advances over; the
-    force reads the stored state that the step only reads, so it runs on a
-    second stream beside the step (it waits for the previous step, and the
-    next step waits for it).  Returns (median block ms, every block's ms,
-    mean step-kernel ms over all blocks)."""
+    kernel plus the FP64 wall force of the interval it advances over.  With
+    the staged kernel both are one call (lbm_step_force: the force summed
+    inside the step kernel, then its fixed-order pass; the step-kernel time
+    then includes the force).  Otherwise the force reads the stored state
+    that the step only reads, so it runs on a second stream beside the step
+    (it waits for the previous step, and the next step waits for it).
+    Returns (median block ms, every block's ms, mean step-kernel ms of the
+    extra block whose launches carry events)."""
     st = sim.stream
     cs = torch.cuda.current_stream()
     side = torch.cuda.Stream(device=cs.device)
     hist = torch.zeros((max(steps, warmup, 1), 3), dtype=torch.float64, device=sim.device)
+    fused = sim.step_kernel == "staged"
 
     def one(i, a=None, b=None):
+        if fused:
+            # the staged kernel sums the wall force inside the step (one
+            # launch, plus the fixed-order pass of its block rows)
+            if a is not None:
+                a.record(cs)
+            lbm.lbm_step_force(sim.ctx, wall, 0, 1.0, hist[i], 0, st)
+            if b is not None:
+                b.record(cs)
+            return
         side.wait_stream(cs)
         lbm.lbm_wall_force(sim.ctx, wall, 0, 1.0, hist[i], 0, side.cuda_stream)
         if a is not None:
@@ -231,10 +244,8 @@ def timed_run(torch, lbm, sim, steps, warmup, wall=1, events=True, repeats=1):
     for i in range(warmup):
         one(i)
     torch.cuda.synchronize()
-    blocks, kern = [], []
-    for _ in range(repeats):
-        a = [torch.cuda.Event(enable_timing=True) for _ in range(steps)] if events else [None] * steps
-        b = [torch.cuda.Event(enable_timing=True) for _ in range(steps)] if events else [None] * steps
+
+    def block(a, b):
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         t0.record(cs)
@@ -242,10 +253,19 @@ def timed_run(torch, lbm, sim, steps, warmup, wall=1, events=True, repeats=1):
             one(i, a[i], b[i])
         t1.record(cs)
         torch.cuda.synchronize()
-        blocks.append(t0.elapsed_time(t1))
-        if events:
-            kern.extend(x.elapsed_time(y) for x, y in zip(a, b))
-    return statistics.median(blocks), blocks, (sum(kern) / len(kern) if events else None)
+        return t0.elapsed_time(t1)
+
+    # the value blocks carry no per-step events (an event between two steps
+    # opens a gap of a few microseconds); one more block times every
+    # step-kernel launch for the roofline
+    blocks = [block([None] * steps, [None] * steps) for _ in range(repeats)]
+    kern = None
+    if events:
+        a = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        b = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        block(a, b)
+        kern = sum(x.elapsed_time(y) for x, y in zip(a, b)) / steps
+    return statistics.median(blocks), blocks, kern
 
 
 def run_ours(args):
@@ -354,14 +374,19 @@ def run_ours(args):
                        "nodes": N, "fluid_nodes": fluid,
                        "storage": args.storage + (" (shifted x2^12, stochastic rounding)" if sr and args.storage == "f16s"
                                                   else (" (stochastic rounding)" if sr else "")),
-                       "compute": "f32", "step": "fused collide-stream + FP64 drag reduction (on a second stream beside the step)",
+                       "compute": "f32",
+                       "step": ("collide-stream with the FP64 drag summed in the step kernel + its fixed-order "
+                                "reduction" if step_kernel == "staged" else
+                                "fused collide-stream + FP64 drag reduction (on a second stream beside the step)"),
                        "l2": f"inputs larger than L2: {N * (bpn - 1) / 2 / 1e6:.0f} MB of populations read and the same "
                   "written per step",
                        "parallelism": f"{ws} independent replica(s)"},
-            "roofline": roof, "gpu_launches": 3 * args.steps, "clocks": clocks.summary(),
+            "roofline": roof, "gpu_launches": (2 if step_kernel == "staged" else 3) * args.steps,
+            "clocks": clocks.summary(),
             "repeats": {"blocks": args.repeats, "block_ms": [round(b, 4) for b in blocks_ms],
-                        "value_from": "median block; gpu_launches counts one block (step kernel, link kernel, "
-                                      "fixed-order reduction per step)"},
+                        "value_from": "median block (no per-step events); the roofline's kernel time comes "
+                                      "from one more block with an event pair around every step launch; "
+                                      "gpu_launches counts one block"},
             "step_kernel": step_kernel,
         }
         if e2e:

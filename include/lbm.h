@@ -166,8 +166,9 @@ typedef struct lbm_config {
 
 /* Kernel of the fused step.  Both compute the same arithmetic and store the
  * same bits; they differ in how the pull sources reach the registers.
- * LBM_STEP_AUTO (0) picks the staged kernel wherever it applies and enough
- * shared memory holds its pipeline, else the register-tiled one.
+ * LBM_STEP_AUTO (0) picks the staged kernel for 16-bit storage wherever it
+ * applies, enough shared memory holds its pipeline and at most 2% of the
+ * 4-node chunks touch a wall, solid or padding; else the register-tiled one.
  * LBM_STEP_REGISTER (1): every thread loads its vectors straight from HBM.
  * LBM_STEP_STAGED (2): a persistent kernel stages each tile's source rows in
  * shared memory with bulk asynchronous copies; it applies to boxes periodic
@@ -386,6 +387,20 @@ lbm_status lbm_wall_force(lbm_ctx* ctx, int wall, unsigned flags, double weight,
  *     contexts or threads on the same device -- race; serialise them. */
 lbm_status lbm_wall_force_noalloc(lbm_ctx* ctx, int wall, unsigned flags, double weight, double* out,
                                   int out_on_host, void* stream);
+
+/* One step of Eq. (2) with the wall force of lbm_wall_force fused in: the
+ * momentum exchange of Eq. (25) on `wall` during the step T-1 -> T that
+ * produced the stored state (what lbm_wall_force returns just before this
+ * call), then T -> T+1.  Arguments, flags and outputs as for lbm_wall_force
+ * (LBM_MAXWELL_REMOVE adds nothing: the kernel that fuses the force serves
+ * contexts without the Maxwell term).  Needs T >= 1.  With the staged step
+ * kernel the links are summed inside the step kernel (FP64 per link and
+ * lane, a fixed shuffle tree, one row per block, then the fixed-order pass
+ * over the rows by the block that finishes last: deterministic, but in
+ * another order than lbm_wall_force, so the two agree to rounding, not bit
+ * for bit); otherwise the call is lbm_wall_force then lbm_step. */
+lbm_status lbm_step_force(lbm_ctx* ctx, int wall, unsigned flags, double weight, double* out, int out_on_host,
+                          void* stream);
 
 /* FP64 sums over fluid nodes of the canonical state f(T), times dx^D:
  * out[0] mass, out[1..3] momentum sum e f, out[4..6] body force sum rho a. */

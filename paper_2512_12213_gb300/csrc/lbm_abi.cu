@@ -424,6 +424,10 @@ void choose_stage(Ctx& x)
     // chunks are special (a sphere or a few bodies in a periodic box); boxes
     // full of small solids go to the register-tiled kernel
     if (x.cfg.step_kernel == LBM_STEP_AUTO && x.n_special * 50 > x.geo.sq / 4) return;
+    // ... and 16-bit storage: with FP32 the register-tiled kernel already
+    // keeps enough bytes in flight (measured on the sphere box: 0.84 of HBM
+    // against 0.81 staged), with 16-bit it does not (0.52 against 0.80)
+    if (x.cfg.step_kernel == LBM_STEP_AUTO && x.elem != 2) return;
     const size_t Q = x.cfg.lattice, nxp = x.geo.nxp;
     const size_t row_bytes = nxp * x.elem;
     const int R = (int)std::max<size_t>(1, std::min<size_t>((STG_COPY_BYTES + row_bytes - 1) / row_bytes,
@@ -872,7 +876,11 @@ lbm_status lbm_device_status(lbm_ctx* ctx, uint32_t* flags, int clear, void* str
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaMemcpyAsync(flags, x.errflag, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "copy flags");
     CK(cudaStreamSynchronize(st), "synchronize");
-    if (clear) CK(cudaMemsetAsync(x.errflag, 0, sizeof(uint32_t), st), "clear flags");
+    if (clear) {
+        CK(cudaMemsetAsync(x.errflag, 0, sizeof(uint32_t), st), "clear flags");
+        // a step that stopped on a flag may have left the fused force's ticket set
+        CK(cudaMemsetAsync(x.scratch + SCRATCH_TICKET_OFF, 0, sizeof(uint32_t), st), "clear ticket");
+    }
     return LBM_OK;
 }
 
@@ -1000,6 +1008,68 @@ lbm_status lbm_wall_force(lbm_ctx* ctx, int wall, unsigned flags, double weight,
     int nb = 0;
     if (e > b) CK(x.ops->links(x, x.pop[x.cur], b, e, flags & 3u, part, &nb, st), "link kernel");
     return finish_reduce(x, part, nb, 3, out, out_on_host, weight, (flags & LBM_ACCUMULATE) != 0, st);
+}
+
+lbm_status lbm_step_force(lbm_ctx* ctx, int wall, unsigned flags, double weight, double* out, int out_on_host,
+                          void* stream)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    Ctx& x = ctx->c;
+    if (!out) return arg_fail(x, "out is NULL");
+    if (wall > LBM_MAX_WALLS) return arg_fail(x, "wall id out of range");
+    if (flags & ~7u) return arg_fail(x, "unknown flag");
+    if (x.t < 1) {
+        x.err = "the wall force needs at least one step";
+        return LBM_ERR_STATE;
+    }
+    GUARD(x);
+    if (!out_mode_ok(out_on_host, (flags & LBM_ACCUMULATE) != 0, out, x.err)) return LBM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (x.stage_R <= 0) {
+        // the register-tiled step: the two calls in sequence
+        const lbm_status s = lbm_wall_force(ctx, wall, flags, weight, out, out_on_host, stream);
+        if (s != LBM_OK) return s;
+        return lbm_step(ctx, 1, stream);
+    }
+    StgForce fw;
+    memset(&fw, 0, sizeof fw);
+    fw.out = x.scratch + SCRATCH_RED_OFF;
+    fw.wall = wall;
+    fw.flags = flags & 1u;
+    fw.c = x.kpd.c;
+    fw.rho0 = x.kpd.rho0;
+    fw.svol = x.kpd.svol;
+    for (int w = 0; w <= MAXW; ++w)
+        for (int k = 0; k < 3; ++k) fw.lw[w][k] = x.kpf.LW[w][k];
+    // the kernel's last block writes the sum: to out (device output) or to
+    // the result slot, copied to the host below
+    fw.ticket = reinterpret_cast<unsigned*>(x.scratch + SCRATCH_TICKET_OFF);
+    const bool dev = out_on_host == LBM_OUT_DEVICE;
+    fw.result = dev ? out : x.scratch + SCRATCH_OUT_OFF;
+    fw.weight = weight;
+    fw.accumulate = dev && (flags & LBM_ACCUMULATE) ? 1 : 0;
+    CK(x.ops->step_force(x, x.pop[x.cur], x.pop[1 - x.cur], step_seed(x, x.t), fw, st), "step kernel");
+    x.cur = 1 - x.cur;
+    x.t += 1;
+    x.prev_valid = true;
+    if (dev) return LBM_OK;
+    if (out_on_host == LBM_OUT_HOST_ASYNC) {
+        CK(cudaMemcpyAsync(out, fw.result, 3 * sizeof(double), cudaMemcpyDeviceToHost, st), "copy result");
+        return LBM_OK;
+    }
+    double tmp[3];
+    CK(cudaMemcpyAsync(tmp, fw.result, sizeof tmp, cudaMemcpyDeviceToHost, st), "copy result");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    bool finite = true;
+    for (int k = 0; k < 3; ++k) {
+        out[k] = (flags & LBM_ACCUMULATE) ? out[k] + tmp[k] : tmp[k];
+        finite = finite && std::isfinite(tmp[k]);
+    }
+    if (!finite) {
+        x.err = "the wall force is not finite (the state holds NaN or Inf values)";
+        return LBM_ERR_NAN;
+    }
+    return LBM_OK;
 }
 
 lbm_status lbm_balance(lbm_ctx* ctx, double* out, int out_on_host, void* stream)

@@ -56,6 +56,7 @@ constexpr size_t SCRATCH_RED_OFF = 0;
 constexpr size_t SCRATCH_ADJ_OFF = (size_t)MAX_PARTIAL_ROWS * PARTIAL_WIDTH;
 constexpr size_t SCRATCH_OUT_OFF = SCRATCH_ADJ_OFF + (size_t)ADJ_BLOCKS * 6;
 constexpr size_t SCRATCH_FLAG_OFF = SCRATCH_OUT_OFF + 8;   // device error flags (unsigned)
+constexpr size_t SCRATCH_TICKET_OFF = SCRATCH_FLAG_OFF + 1; // last-block ticket of the fused wall force (unsigned)
 constexpr size_t SCRATCH_DOUBLES = SCRATCH_FLAG_OFF + 8;
 // insulating walls only, after the above: the field block (E, the sum of v,
 // the force coefficient in FP64, FP32 and FP32 storage units, the ticket of
@@ -69,9 +70,13 @@ constexpr size_t SCRATCH_INS_RED = SCRATCH_INS_OFF + 16;
 constexpr size_t SCRATCH_INS_ROWS = SCRATCH_INS_RED + (size_t)INS_RED_ROWS * 3;
 
 struct Ctx;
+struct StgForce;
 
 struct Dispatch {
     cudaError_t (*step)(const Ctx&, const void* src, void* dst, uint32_t seed, cudaStream_t);
+    // the staged step with the wall force of the stored state's step fused in
+    cudaError_t (*step_force)(const Ctx&, const void* src, void* dst, uint32_t seed, const StgForce& fw,
+                              cudaStream_t);
     cudaError_t (*import_f)(const Ctx&, const void* src, int dtype, void* dst, cudaStream_t);
     cudaError_t (*init_fields)(const Ctx&, const double* rho, const double* u, const double* xi, void* dst,
                                cudaStream_t);
@@ -152,6 +157,10 @@ struct Ctx {
     long long ins_rows;
     long long n_fluid;
 };
+
+// blocks of the staged step: one per SM, at most one per tile (each writes
+// one partial row of the fused wall force)
+inline int staged_blocks(const Ctx& c) { return (int)(c.stage_tiles < c.sm_count ? c.stage_tiles : c.sm_count); }
 
 }  // namespace lbm
 

@@ -1197,7 +1197,8 @@ cudaError_t launch_step_q(const Ctx& c, const void* src, void* dst, uint32_t see
 // the staged step (periodic boxes with the plain node code, 16-bit or FP32
 // storage; the host chose the tile rows and stage count at create)
 template <int Q, class S, bool SR>
-cudaError_t launch_step_staged(const Ctx& c, const void* src, void* dst, uint32_t seed, cudaStream_t st)
+cudaError_t launch_step_staged(const Ctx& c, const void* src, void* dst, uint32_t seed, cudaStream_t st,
+                               const StgForce& fw)
 {
     using T = typename S::T;
     auto kern = k_step_staged<Q, S, SR>;
@@ -1206,22 +1207,25 @@ cudaError_t launch_step_staged(const Ctx& c, const void* src, void* dst, uint32_
         if (e != cudaSuccess) return e;
         c.stage_ready = true;
     }
-    const int blocks = (int)std::min<long long>((long long)c.sm_count, c.stage_tiles);
+    const int blocks = staged_blocks(c);
     kern<<<blocks, STG_THREADS, c.stage_smem, st>>>((const T*)src, (T*)dst, c.cls, c.special, c.n_special, c.geo,
                                                      kp_step_of<S>(c), seed, c.stage_R, c.stage_tiles, c.stage_n,
-                                                     c.errflag);
+                                                     c.errflag, fw);
     return cudaGetLastError();
 }
 
 template <int Q, class S>
-cudaError_t launch_step(const Ctx& c, const void* src, void* dst, uint32_t seed, cudaStream_t st)
+cudaError_t launch_step(const Ctx& c, const void* src, void* dst, uint32_t seed, cudaStream_t st,
+                        const StgForce* fw = nullptr)
 {
+    StgForce none{};
+    const StgForce& f = fw ? *fw : none;
     if constexpr (sizeof(typename S::T) == 2) {
         if (c.stage_R > 0)
-            return c.sr ? launch_step_staged<Q, S, true>(c, src, dst, seed, st)
-                        : launch_step_staged<Q, S, false>(c, src, dst, seed, st);
+            return c.sr ? launch_step_staged<Q, S, true>(c, src, dst, seed, st, f)
+                        : launch_step_staged<Q, S, false>(c, src, dst, seed, st, f);
     } else if constexpr (sizeof(typename S::T) == 4) {
-        if (c.stage_R > 0) return launch_step_staged<Q, S, false>(c, src, dst, seed, st);
+        if (c.stage_R > 0) return launch_step_staged<Q, S, false>(c, src, dst, seed, st, f);
     }
     if constexpr (sizeof(typename S::T) == 2) {
         if (c.sr)
@@ -1385,6 +1389,10 @@ template <class S> Dispatch make_dispatch()
     Dispatch d;
     d.step = [](const Ctx& c, const void* s, void* t, uint32_t seed, cudaStream_t st) {
         return c.cfg.lattice == 9 ? launch_step<9, S>(c, s, t, seed, st) : launch_step<19, S>(c, s, t, seed, st);
+    };
+    d.step_force = [](const Ctx& c, const void* s, void* t, uint32_t seed, const StgForce& fw, cudaStream_t st) {
+        return c.cfg.lattice == 9 ? launch_step<9, S>(c, s, t, seed, st, &fw)
+                                  : launch_step<19, S>(c, s, t, seed, st, &fw);
     };
     d.import_f = [](const Ctx& c, const void* s, int dt, void* t, cudaStream_t st) {
         return c.cfg.lattice == 9 ? launch_import<9, S>(c, s, dt, t, st) : launch_import<19, S>(c, s, dt, t, st);

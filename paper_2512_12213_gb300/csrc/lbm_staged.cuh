@@ -181,15 +181,37 @@ __device__ __forceinline__ float2 stg_pair(const typename S::T* __restrict__ row
     }
 }
 
+// the wall force fused into the staged step: the momentum exchange of Eq.
+// (25) of the step that produced the stored state, summed over the links of
+// one wall (wall < 0: every wall) in FP64; null `out`: not asked for
+struct StgForce {
+    double* out;          // one row of 3 doubles per block, or null
+    int wall;
+    unsigned flags;       // LBM_MOVING_CORR
+    double c, rho0, svol; // physical units
+    float lw[MAXW + 1][3];  // 6 rho0 u_w / c per wall id (physical units)
+    // the last block to write its row sums the rows (ticket: zero between
+    // launches) into result: result = (accumulate ? result : 0) + weight sum
+    unsigned* ticket;
+    double* result;
+    double weight;
+    int accumulate;
+};
+
 // the canonical post-propagation deviations d_b(x) (storage units) of a node
 // of a box periodic on every axis with halfway walls, as gather_node: the
 // pull source P_b(x - E_b), or through a link into a solid node the bounced
 // P_opp(b)(x) plus Ladd's term of the solid's wall.  Every load is issued
-// before any is used (one memory round trip for the boundary warps).
+// before any is used (one memory round trip for the boundary warps).  With
+// a force asked for, each link (x, a' = opp(b)) into a solid adds
+// (dx^D/dt) [e_a' (fbar_a' + fbar_b) (+ u_w (fbar_b - fbar_a'))] to acc, with
+// fbar_a' = f^rel_a'(x, T-1) and fbar_b = f_b(x, T) its bounced population,
+// as the link kernel of lbm_wall_force does.
 template <int Q, class S>
 __device__ __forceinline__ void gather_periodic(const typename S::T* __restrict__ P, const uint8_t* __restrict__ cls,
                                                 const Geo& g, const KP<typename S::R>& p, int x, int y, int z,
-                                                long long own, typename S::R (&d)[Q])
+                                                long long own, typename S::R (&d)[Q], const StgForce& fw,
+                                                double (&acc)[3])
 {
     using T = typename S::T;
     using R = typename S::R;
@@ -211,6 +233,20 @@ __device__ __forceinline__ void gather_periodic(const typename S::T* __restrict_
             const R L = R(WD<Q>(b)) * (R(EX<Q>(b)) * p.LW[wall][0] + R(EY<Q>(b)) * p.LW[wall][1] +
                                        R(EZ<Q>(b)) * p.LW[wall][2]);
             d[b] = S::to_raw(bv[b]) + L;
+            if (fw.out && (fw.wall < 0 || fw.wall == wall)) {
+                const float* lw = fw.lw[wall];
+                const double w = WD<Q>(b);
+                const float Lp = (float)w * ((float)EX<Q>(b) * lw[0] + (float)EY<Q>(b) * lw[1] + (float)EZ<Q>(b) * lw[2]);
+                const double fo = (double)S::to_r(bv[b]) + w * fw.rho0;
+                const double fi = (double)(S::to_r(bv[b]) + Lp) + w * fw.rho0;
+                const int e[3] = {-EX<Q>(b), -EY<Q>(b), -EZ<Q>(b)};     // e_a', a' = opp(b)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    double t = fw.c * e[k] * (fo + fi);
+                    if (fw.flags & 1u) t += (double)lw[k] * fw.c / (6.0 * fw.rho0) * (fi - fo);
+                    acc[k] += fw.svol * t;
+                }
+            }
         } else {
             d[b] = S::to_raw(pv[b]);
         }
@@ -221,7 +257,8 @@ template <int Q, class S, bool SR>
 __global__ void __launch_bounds__(STG_THREADS, 1)
 k_step_staged(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
               const uint8_t* __restrict__ cls, const uint32_t* __restrict__ special, long long nspecial, const Geo g,
-              const KP<float> p, uint32_t seed, int R, int ntiles, int nstages, unsigned* __restrict__ errflag)
+              const KP<float> p, uint32_t seed, int R, int ntiles, int nstages, unsigned* __restrict__ errflag,
+              const StgForce fw)
 {
     using T = typename S::T;
     using Rt = typename S::R;
@@ -281,7 +318,10 @@ k_step_staged(const typename S::T* __restrict__ src, typename S::T* __restrict__
     }
 
     if (warp == STG_CWARPS + 1) {
-        // boundary warp: the listed chunks, node by node (lane per node)
+        // boundary warp: the listed chunks, node by node (lane per node), and
+        // the wall force of their links when asked for (each lane sums its
+        // nodes in a fixed order, then a fixed shuffle tree, one row per block)
+        double acc[3] = {0.0, 0.0, 0.0};
         const long long nn = 4 * nspecial;
         for (long long j = (long long)blockIdx.x * 32 + lane; j < nn; j += (long long)gridDim.x * 32) {
             const long long node = (long long)special[j >> 2] + (j & 3);
@@ -295,7 +335,7 @@ k_step_staged(const typename S::T* __restrict__ src, typename S::T* __restrict__
                 continue;
             }
             Rt d[Q];
-            gather_periodic<Q, S>(src, cls, g, p, x, y, z, node, d);
+            gather_periodic<Q, S>(src, cls, g, p, x, y, z, node, d, fw, acc);
             NodeM<Rt> m;
             node_macro<Rt, Q, false, false>(d, p, m);
             node_relax<Rt, Q, false>(d, p, m);
@@ -306,6 +346,33 @@ k_step_staged(const typename S::T* __restrict__ src, typename S::T* __restrict__
             } else {
 #pragma unroll
                 for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + node] = S::from_raw(d[a]);
+            }
+        }
+        if (fw.out) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+                if (lane == 0) fw.out[(long long)blockIdx.x * 3 + k] = acc[k];
+            }
+            // the last block's boundary warp sums the rows: lane l takes rows
+            // l, l+32, ..., then a fixed shuffle tree (the order of the
+            // library's fixed-order pass), and clears the ticket
+            __threadfence();
+            unsigned last = 0;
+            if (lane == 0) last = (atomicAdd(fw.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence();
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    double sum = 0.0;
+                    for (int r = lane; r < (int)gridDim.x; r += 32) sum += __ldcg(fw.out + (long long)r * 3 + k);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+                    if (lane == 0) fw.result[k] = (fw.accumulate ? fw.result[k] : 0.0) + fw.weight * sum;
+                }
+                if (lane == 0) *fw.ticket = 0u;
             }
         }
         return;

@@ -99,6 +99,7 @@ _SIGS = {
     "lbm_stress": [_vp, _i, _vp, _vp, _vp, _vp, _vp],
     "lbm_wall_force": [_vp, _i, ctypes.c_uint, _d, _vp, _i, _vp],
     "lbm_wall_force_noalloc": [_vp, _i, ctypes.c_uint, _d, _vp, _i, _vp],
+    "lbm_step_force": [_vp, _i, ctypes.c_uint, _d, _vp, _i, _vp],
     "lbm_balance": [_vp, _vp, _i, _vp],
     "lbm_residual": [_vp, _vp, _i, _vp, _i, _vp],
     "lbm_run_steady": [_vp, _i, _d, ctypes.c_int64, _vp, _P(_d), _P(ctypes.c_int64), _vp],
@@ -298,6 +299,12 @@ def lbm_wall_force_noalloc(ctx, wall, flags, weight, out, out_on_host, stream):
     scratch; at most 1,048,576 links per call; overlapping calls race)."""
     _check(load().lbm_wall_force_noalloc(ctx, int(wall), int(flags), float(weight), _ptr(out),
                                          int(out_on_host), stream), ctx)
+
+
+def lbm_step_force(ctx, wall, flags, weight, out, out_on_host, stream):
+    """One step with the wall force of the step before it fused in."""
+    _check(load().lbm_step_force(ctx, int(wall), int(flags), float(weight), _ptr(out), int(out_on_host), stream),
+           ctx)
 
 
 def lbm_balance(ctx, out, out_on_host, stream):

@@ -83,3 +83,65 @@ def test_staged_equals_register_kernel(orc, name, storage, rounding):
     assert torch.equal(a[:n], b[:n])
     assert np.array_equal(fa, fb)
     assert np.all(np.isfinite(fa))
+
+
+@pytest.mark.parametrize("storage,rounding", [("f16s", "stochastic"), ("bf16s", "nearest"), ("f32", "nearest")])
+def test_step_force_fused_in_the_staged_step(orc, storage, rounding):
+    """lbm_step_force on the staged kernel: the wall force of the step before
+    it, summed inside the step kernel, equals lbm_wall_force called before
+    lbm_step to rounding (FP64 sums in another fixed order), for one wall,
+    another and every wall, with and without the moving-wall correction, to
+    host and device outputs; the populations stepped are bit for bit those of
+    the plain step."""
+    nx, ny, nz = 96, 40, 24
+    mask = inputs.sphere_mask(nx, ny, nz, (30.2, 19.6, 11.3), 5.2, wall=1)
+    mask = np.where(inputs.sphere_mask(nx, ny, nz, (70.7, 12.1, 13.0), 4.1, wall=2) > 0, 2, mask).astype(np.uint8)
+    cfg = dict(lattice=19, nx=nx, ny=ny, nz=nz, periodic=(1, 1, 1), tau=0.7, force_model="e", g=(2e-5, 0, 0),
+               storage=storage, rounding=rounding, seed=11, wall_u=((0, 0, 0), (0.01, -0.02, 0.005)),
+               step_kernel="staged")
+    ocfg = orc.make_cfg(**workloads.oracle_kwargs(cfg))
+    rho, u = inputs.smooth_fields(nx, ny, nz, dims=3, u_amplitude=0.03, seed=3)
+    f0 = orc.init(ocfg, mask, rho, u, inputs.noise(19, nx, ny, nz, 1e-3, seed=2))
+    a = lbm.Sim(cfg, mask)
+    b = lbm.Sim(cfg, mask)
+    a.import_f(f0)
+    b.import_f(f0)
+    assert a.step_kernel == "staged"
+    a.step(1)
+    b.step(1)
+    scale = np.abs(a.wall_force(-1)).max()
+    for wall, flags in [(1, 0), (2, lbm.MOVING_CORR), (-1, 0), (-1, lbm.MOVING_CORR), (2, 0)]:
+        ref = a.wall_force(wall, flags)
+        a.step(1)
+        got = np.zeros(3)
+        lbm.lbm_step_force(b.ctx, wall, flags, 1.0, got, lbm.OUT_HOST, b.stream)
+        assert np.abs(got - ref).max() <= 1e-12 * scale, (wall, flags, got, ref)
+    # device output with accumulation, over three steps
+    acc = torch.zeros(3, dtype=torch.float64, device=b.device)
+    ref = np.zeros(3)
+    for _ in range(3):
+        ref += 0.5 * a.wall_force(-1)
+        a.step(1)
+        lbm.lbm_step_force(b.ctx, -1, lbm.ACCUMULATE, 0.5, acc, lbm.OUT_DEVICE, b.stream)
+    assert np.abs(acc.cpu().numpy() - ref).max() <= 1e-12 * scale
+    assert b.time == a.time
+    assert np.array_equal(a.export_f().cpu().numpy(), b.export_f().cpu().numpy())
+    assert a.device_status() == 0 and b.device_status() == 0
+
+
+def test_step_force_on_the_register_kernel(orc):
+    """Without the staged kernel lbm_step_force is lbm_wall_force then
+    lbm_step: the same values and the same state."""
+    cfg, mask = workloads.poiseuille(nx=70, ny=20, storage="f32")
+    a, b = lbm.Sim(cfg, mask), lbm.Sim(cfg, mask)
+    for s in (a, b):
+        s.rest()
+        s.step(2)
+    assert b.step_kernel == "register"
+    for _ in range(3):
+        ref = a.wall_force(1)
+        a.step(1)
+        got = np.zeros(3)
+        lbm.lbm_step_force(b.ctx, 1, 0, 1.0, got, lbm.OUT_HOST, b.stream)
+        assert np.array_equal(got, ref)
+    assert np.array_equal(a.export_f().cpu().numpy(), b.export_f().cpu().numpy())
