@@ -166,16 +166,17 @@ typedef struct lbm_config {
 
 /* Kernel of the fused step.  Both compute the same arithmetic and store the
  * same bits; they differ in how the pull sources reach the registers.
- * LBM_STEP_AUTO (0) picks the staged kernel for 16-bit storage wherever it
- * applies, enough shared memory holds its pipeline and at most 2% of the
- * 4-node chunks touch a wall, solid or padding; else the register-tiled one.
- * LBM_STEP_REGISTER (1): every thread loads its vectors straight from HBM.
- * LBM_STEP_STAGED (2): a persistent kernel stages each tile's source rows in
- * shared memory with bulk asynchronous copies; it applies to boxes periodic
- * on every axis, FP32 or 16-bit storage, and none of lorentz, maxwell, les,
- * stokes, darcy, curved, insulating, induced (else LBM_ERR_ARG); where its
- * pipeline does not fit in shared memory (rows of more than about 1,100
- * 16-bit or 550 FP32 nodes) the register-tiled kernel runs instead. */
+ * LBM_STEP_AUTO (0) picks the staged kernel for 16-bit storage in boxes
+ * periodic on every axis with the plain node code (no lorentz, maxwell, les,
+ * stokes, darcy) wherever enough shared memory holds its pipeline and at most
+ * 2% of the 4-node chunks touch a solid or padding; else the register-tiled
+ * one.  LBM_STEP_REGISTER (1): every thread loads its vectors straight from
+ * HBM.  LBM_STEP_STAGED (2): a persistent kernel stages each tile's source
+ * rows in shared memory with bulk asynchronous copies; it serves FP32 and
+ * 16-bit storage with closed or periodic faces and every node code except
+ * curved walls, insulating walls and the induced field (those: LBM_ERR_ARG);
+ * where its pipeline does not fit in shared memory (rows of more than about
+ * 1,100 16-bit or 550 FP32 nodes) the register-tiled kernel runs instead. */
 enum { LBM_STEP_AUTO = 0, LBM_STEP_REGISTER = 1, LBM_STEP_STAGED = 2 };
 
 /* Induced magnetic field (Sec. 4 cites Dellar's vector lattice Boltzmann
@@ -394,7 +395,8 @@ lbm_status lbm_wall_force_noalloc(lbm_ctx* ctx, int wall, unsigned flags, double
  * call), then T -> T+1.  Arguments, flags and outputs as for lbm_wall_force
  * (LBM_MAXWELL_REMOVE adds nothing: the kernel that fuses the force serves
  * contexts without the Maxwell term).  Needs T >= 1.  With the staged step
- * kernel the links are summed inside the step kernel (FP64 per link and
+ * kernel in a box periodic on every axis with the plain node code the links
+ * are summed inside the step kernel (FP64 per link and
  * lane, a fixed shuffle tree, one row per block, then the fixed-order pass
  * over the rows by the block that finishes last: deterministic, but in
  * another order than lbm_wall_force, so the two agree to rounding, not bit

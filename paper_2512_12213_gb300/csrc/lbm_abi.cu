@@ -37,13 +37,22 @@ size_t elem_of(int storage)
     }
 }
 
-// the staged step serves periodic boxes with the plain node code
+// the staged step serves 16-bit and FP32 storage with halfway walls and the
+// node code of the imposed field (not walls off the half-grid, insulating
+// walls or the induced field, whose state the staged kernel does not carry)
 bool staged_applies(const lbm_config* c)
 {
-    const bool periodic = c->periodic[0] && c->periodic[1] && (c->lattice == LBM_D2Q9 || c->periodic[2]);
-    const bool plain = !c->lorentz && !c->maxwell && !c->les && !c->stokes && !(c->darcy > 0.0) && !c->curved &&
-                       !c->insulating && !c->induced;
-    return periodic && plain && c->storage != LBM_STORE_F64;
+    return !c->curved && !c->insulating && !c->induced && c->storage != LBM_STORE_F64;
+}
+
+bool all_periodic(const lbm_config* c)
+{
+    return c->periodic[0] && c->periodic[1] && (c->lattice == LBM_D2Q9 || c->periodic[2]);
+}
+
+bool plain_node_code(const lbm_config* c)
+{
+    return !c->lorentz && !c->maxwell && !c->les && !c->stokes && !(c->darcy > 0.0);
 }
 
 bool validate(const lbm_config* c, const uint8_t* wid, std::string& err)
@@ -100,8 +109,7 @@ bool validate(const lbm_config* c, const uint8_t* wid, std::string& err)
     }
     if (c->step_kernel < LBM_STEP_AUTO || c->step_kernel > LBM_STEP_STAGED) return fail("step_kernel must be 0..2");
     if (c->step_kernel == LBM_STEP_STAGED && !staged_applies(c))
-        return fail("the staged step kernel needs a box periodic on every axis, FP32 or 16-bit storage and none of "
-                    "lorentz, maxwell, les, stokes, darcy, curved, insulating, induced");
+        return fail("the staged step kernel needs FP32 or 16-bit storage and none of curved, insulating, induced");
     if (!wid) return fail("wall_id is NULL");
     const long long N = nodes_of(c);
     for (long long n = 0; n < N; ++n)
@@ -192,13 +200,15 @@ void build_geometry(const lbm_config* c, const uint8_t* wid, int nxp, std::vecto
 }
 
 // the 4-node chunks of the padded layout that hold a node other than a bulk
-// fluid node (a wall or face neighbour, a solid node, padding): the first
-// node of each, in order.  The staged step leaves them to its boundary warps.
+// fluid node or a node whose only wall links cross a closed box face (a
+// solid neighbour, a solid node, padding): the first node of each, in order.
+// The staged step leaves them to its boundary warps.
 std::vector<uint32_t> special_chunks(const std::vector<uint8_t>& cls)
 {
     std::vector<uint32_t> out;
+    auto plain = [](uint8_t c) { return c == NC_BULK || c == NC_FACE; };
     for (size_t i = 0; i + 3 < cls.size(); i += 4)
-        if (cls[i] != NC_BULK || cls[i + 1] != NC_BULK || cls[i + 2] != NC_BULK || cls[i + 3] != NC_BULK)
+        if (!plain(cls[i]) || !plain(cls[i + 1]) || !plain(cls[i + 2]) || !plain(cls[i + 3]))
             out.push_back((uint32_t)i);
     return out;
 }
@@ -428,11 +438,14 @@ void choose_stage(Ctx& x)
     // keeps enough bytes in flight (measured on the sphere box: 0.84 of HBM
     // against 0.81 staged), with 16-bit it does not (0.52 against 0.80)
     if (x.cfg.step_kernel == LBM_STEP_AUTO && x.elem != 2) return;
+    // ... in periodic boxes with the plain node code (closed faces and the
+    // EXT node code run staged when asked for)
+    if (x.cfg.step_kernel == LBM_STEP_AUTO && (!all_periodic(&x.cfg) || !plain_node_code(&x.cfg))) return;
     const size_t Q = x.cfg.lattice, nxp = x.geo.nxp;
     const size_t row_bytes = nxp * x.elem;
     const int R = (int)std::max<size_t>(1, std::min<size_t>((STG_COPY_BYTES + row_bytes - 1) / row_bytes,
                                                             (size_t)x.cfg.ny));
-    const size_t stage = (Q * R * nxp * x.elem + R * nxp + 127) / 128 * 128;
+    const size_t stage = stg_stage_bytes((int)Q, R, (int)nxp, (int)x.elem);
     const size_t budget = (size_t)x.smem_optin - 1024;
     // an even count: each consumer group owns every other stage
     const int n = (int)std::min<size_t>(8, budget / (stage + 2 * sizeof(uint64_t))) & ~1;
@@ -1025,8 +1038,10 @@ lbm_status lbm_step_force(lbm_ctx* ctx, int wall, unsigned flags, double weight,
     GUARD(x);
     if (!out_mode_ok(out_on_host, (flags & LBM_ACCUMULATE) != 0, out, x.err)) return LBM_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    if (x.stage_R <= 0) {
-        // the register-tiled step: the two calls in sequence
+    if (x.stage_R <= 0 || !all_periodic(&x.cfg) || x.ext) {
+        // the register-tiled step, or a staged step with closed faces (whose
+        // face links the boundary warps do not see) or the EXT node code: the
+        // two calls in sequence
         const lbm_status s = lbm_wall_force(ctx, wall, flags, weight, out, out_on_host, stream);
         if (s != LBM_OK) return s;
         return lbm_step(ctx, 1, stream);

@@ -177,11 +177,15 @@ template <class T, int V> union VecN {
 };
 
 // ------------------------------------------------- counter-based random bits
-// 32-bit integer hash (a multiply-xorshift finaliser) of a counter, and the
-// per-node stream: one hash of (node, step seed), then a linear congruential
-// step per random word.  bits(a) gives a node's populations 16 bits each
-// (two per word); word() gives one 32-bit word, whose two halves round the
-// same direction of the two nodes of a packed pair.
+// 32-bit integer hash of a counter: a multiply-xorshift finaliser with the
+// published "lowbias32" shifts and multipliers found by C. Wellons' hash
+// prospector; and the per-node stream: one hash of (node, step seed), then
+// a linear congruential step per random word with the multiplier and
+// increment of M. O'Neill's PCG32 (as in the pcg_hash of Jarzynski and
+// Olano, JCGT 2020), output xor-shifted.  bits(a) gives a node's
+// populations 16 bits each (two per word); word() gives one 32-bit word,
+// whose two halves round the same direction of the two nodes of a packed
+// pair.
 __host__ __device__ inline uint32_t hash32(uint32_t x)
 {
     x ^= x >> 16;
@@ -760,6 +764,37 @@ __device__ __forceinline__ void pair_collide_ext(F2 (&d)[Q], const KP<float>& p)
         d[a] = f2fma(om1, d[a], f2add(ps, pa));
         d[b] = f2fma(om1, d[b], f2sub(ps, pa));
     }
+}
+
+// ---------------------------------------------------- closed box faces
+// Ladd term w_a E_a . LW[wall] of an incoming population
+template <int Q, typename R>
+__device__ __forceinline__ R ladd_of(const KP<R>& p, int a, int wall)
+{
+    return R(WD<Q>(a)) * (R(EX<Q>(a)) * p.LW[wall][0] + R(EY<Q>(a)) * p.LW[wall][1] + R(EZ<Q>(a)) * p.LW[wall][2]);
+}
+
+// Box-face bounce-back inside the vectorised path (FACES = some axis is
+// closed).  For direction a at a chunk of row (y, z): the pull-source row is
+// outside a closed y or z face -> every node of the chunk bounces (own value
+// of opp(a)); the first / last node of a row with a closed x face bounces the
+// directions that pull across it.  The wall of a link follows the rule
+// "first closed axis crossed, in x, y, z order".
+struct FaceInfo {
+    bool closed_x;
+    bool yo_lo, yo_hi, zo_lo, zo_hi;     // pull rows y-(+1), y-(-1), z-(+1), z-(-1) outside
+    int wy_lo, wy_hi, wz_lo, wz_hi, wx_lo, wx_hi;
+};
+
+template <int Q>
+__device__ __forceinline__ bool row_out(const FaceInfo& fi, int a, int& wall)
+{
+    const int ey = EY<Q>(a), ez = EZ<Q>(a);
+    if (ey == 1 && fi.yo_lo) { wall = fi.wy_lo; return true; }
+    if (ey == -1 && fi.yo_hi) { wall = fi.wy_hi; return true; }
+    if (ez == 1 && fi.zo_lo) { wall = fi.wz_lo; return true; }
+    if (ez == -1 && fi.zo_hi) { wall = fi.wz_hi; return true; }
+    return false;
 }
 
 // -------------------------------------------------------- addressing helpers

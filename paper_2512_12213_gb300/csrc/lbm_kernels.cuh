@@ -83,36 +83,6 @@ __device__ __forceinline__ void block_sum(double (&v)[W], double* smem /* >= W *
 // boundary, solid or padding node is recomputed node by node with explicit
 // bounce-back.  Populations are in storage units (kernel parameters scaled
 // to match).
-// Ladd term w_a E_a . LW[wall] of an incoming population
-template <int Q, typename R>
-__device__ __forceinline__ R ladd_of(const KP<R>& p, int a, int wall)
-{
-    return R(WD<Q>(a)) * (R(EX<Q>(a)) * p.LW[wall][0] + R(EY<Q>(a)) * p.LW[wall][1] + R(EZ<Q>(a)) * p.LW[wall][2]);
-}
-
-// Box-face bounce-back inside the vectorised path (FACES = some axis is
-// closed).  For direction a at a chunk of row (y, z): the pull-source row is
-// outside a closed y or z face -> every node of the chunk bounces (own value
-// of opp(a)); the first / last node of a row with a closed x face bounces the
-// directions that pull across it.  The wall of a link follows the rule
-// "first closed axis crossed, in x, y, z order".
-struct FaceInfo {
-    bool closed_x;
-    bool yo_lo, yo_hi, zo_lo, zo_hi;     // pull rows y-(+1), y-(-1), z-(+1), z-(-1) outside
-    int wy_lo, wy_hi, wz_lo, wz_hi, wx_lo, wx_hi;
-};
-
-template <int Q>
-__device__ __forceinline__ bool row_out(const FaceInfo& fi, int a, int& wall)
-{
-    const int ey = EY<Q>(a), ez = EZ<Q>(a);
-    if (ey == 1 && fi.yo_lo) { wall = fi.wy_lo; return true; }
-    if (ey == -1 && fi.yo_hi) { wall = fi.wy_hi; return true; }
-    if (ez == 1 && fi.zo_lo) { wall = fi.wz_lo; return true; }
-    if (ez == -1 && fi.zo_hi) { wall = fi.wz_hi; return true; }
-    return false;
-}
-
 // blocks of 128 threads per SM the register allocation must allow: FP64 3
 // (168 registers), else 4 (128; for 16-bit storage measured faster than 5
 // blocks at 96 registers, which spill with the FP32x2 node pairs)
@@ -1196,22 +1166,36 @@ cudaError_t launch_step_q(const Ctx& c, const void* src, void* dst, uint32_t see
 
 // the staged step (periodic boxes with the plain node code, 16-bit or FP32
 // storage; the host chose the tile rows and stage count at create)
-template <int Q, class S, bool SR>
-cudaError_t launch_step_staged(const Ctx& c, const void* src, void* dst, uint32_t seed, cudaStream_t st,
-                               const StgForce& fw)
+template <int Q, class S, bool SR, bool EXT, bool FACES>
+cudaError_t launch_step_staged_k(const Ctx& c, const void* src, void* dst, uint32_t seed, cudaStream_t st,
+                                 const StgForce& fw)
 {
     using T = typename S::T;
-    auto kern = k_step_staged<Q, S, SR>;
+    auto kern = k_step_staged<Q, S, SR, EXT, FACES>;
+    // a context always launches the same instantiation: set its shared
+    // memory limit on the first launch
     if (!c.stage_ready) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.stage_smem);
         if (e != cudaSuccess) return e;
         c.stage_ready = true;
     }
-    const int blocks = staged_blocks(c);
-    kern<<<blocks, STG_THREADS, c.stage_smem, st>>>((const T*)src, (T*)dst, c.cls, c.special, c.n_special, c.geo,
-                                                     kp_step_of<S>(c), seed, c.stage_R, c.stage_tiles, c.stage_n,
-                                                     c.errflag, fw);
+    kern<<<staged_blocks(c), STG_THREADS, c.stage_smem, st>>>((const T*)src, (T*)dst, c.cls, c.special, c.n_special,
+                                                              c.geo, kp_step_of<S>(c), seed, c.stage_R,
+                                                              c.stage_tiles, c.stage_n, c.errflag, fw);
     return cudaGetLastError();
+}
+
+// the staged step (the host chose the tile rows and stage count at create)
+template <int Q, class S, bool SR>
+cudaError_t launch_step_staged(const Ctx& c, const void* src, void* dst, uint32_t seed, cudaStream_t st,
+                               const StgForce& fw)
+{
+    const bool faces = !c.geo.periodic[0] || !c.geo.periodic[1] || (Q == 19 && !c.geo.periodic[2]);
+    if (c.ext)
+        return faces ? launch_step_staged_k<Q, S, SR, true, true>(c, src, dst, seed, st, fw)
+                     : launch_step_staged_k<Q, S, SR, true, false>(c, src, dst, seed, st, fw);
+    return faces ? launch_step_staged_k<Q, S, SR, false, true>(c, src, dst, seed, st, fw)
+                 : launch_step_staged_k<Q, S, SR, false, false>(c, src, dst, seed, st, fw);
 }
 
 template <int Q, class S>

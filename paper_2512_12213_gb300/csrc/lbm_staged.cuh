@@ -1,8 +1,9 @@
-// lbm_staged.cuh -- the fused collide-stream step (Eq. 2 with Eqs. 1 and 3)
-// as a persistent kernel whose input rows are staged in shared memory by the
-// bulk asynchronous copies of the tensor memory accelerator, for periodic
-// boxes whose nodes need the plain node code (no Lorentz force, Maxwell
-// term, LES, curved or insulating walls) and 16-bit or FP32 storage.
+// lbm_staged.cuh -- the fused collide-stream step (Eq. 2 with Eqs. 1 and 3,
+// and Eq. 10 with the Maxwell term) as a persistent kernel whose input rows
+// are staged in shared memory by the bulk asynchronous copies of the tensor
+// memory accelerator, for 16-bit or FP32 storage with halfway walls, closed
+// or periodic box faces and every node code but curved walls, insulating
+// walls and the induced field.
 //
 // Pull scheme: a tile is R consecutive rows (y0 .. y0+R-1) of one z plane;
 // for direction a the tile reads the R source rows shifted by (E_y, E_z),
@@ -26,9 +27,14 @@
 // then only wait on the phase of a use whose predecessor its group has
 // finished, and a parity wait cannot mistake a phase two uses old for the
 // current one (with an odd count a stage alternates between the groups and
-// a group running ahead could do exactly that); a thread relaxes one pair of nodes of a 64-node warp task at a time
-// (one 32-bit word per direction for 16-bit storage, one float2 for FP32)
-// with the FP32x2 node code of k_step.  The 4-node chunks that touch a solid
+// a group running ahead could do exactly that).  A thread relaxes one pair
+// of nodes of a 64-node warp task at a time (one 32-bit word per direction
+// for 16-bit storage, one float2 for FP32) with k_step's node code for the
+// configuration.  Closed faces follow k_step: a source row outside a closed
+// y or z face is the node's own row of the opposite direction (the producer
+// copies that row instead), the element outside a closed x face is the
+// node's own opposite population (the producer stages these face values),
+// and moving faces add Ladd's term.  The 4-node chunks that touch a solid
 // node, a wall or the padding are not the pipeline's: a boundary warp per
 // block takes its share of their list (built on the host) and computes them
 // node by node from global memory with explicit bounce-back, exactly as
@@ -113,21 +119,32 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 __host__ __device__ inline size_t stg_round128(size_t b) { return (b + 127) / 128 * 128; }
 
-// bytes of one stage: Q directions x R rows x nxp values, then R x nxp class bytes
-template <int Q, class S>
-__host__ __device__ inline size_t stg_stage_bytes(int R, int nxp)
+// layout of one stage: Q directions x R rows x nxp values; R x nxp class
+// bytes; at a 16-byte boundary the face values, [2][Q][R] values (the
+// node's own opposite population at x = 0 and x = nx - 1, for boxes closed
+// in x)
+__host__ __device__ inline size_t stg_cls_off(int Q, int R, int nxp, int elem) { return (size_t)Q * R * nxp * elem; }
+__host__ __device__ inline size_t stg_face_off(int Q, int R, int nxp, int elem)
 {
-    return stg_round128((size_t)Q * R * nxp * sizeof(typename S::T) + (size_t)R * nxp);
+    return (stg_cls_off(Q, R, nxp, elem) + (size_t)R * nxp + 15) / 16 * 16;
+}
+__host__ __device__ inline size_t stg_stage_bytes(int Q, int R, int nxp, int elem)
+{
+    return stg_round128(stg_face_off(Q, R, nxp, elem) + (size_t)2 * Q * R * elem);
 }
 
 // producer warp: stage the source rows of tile t (plane z, rows y0 .. y0+nr-1).
-// Lane 0 arms the full barrier with the tile's bytes; then lane a < Q copies
-// direction a's rows (shift ey, ez of that lane) and lane Q the class bytes,
-// so the copies of a tile are issued in parallel
-template <int Q, class S>
+// Lane 0 arms the full barrier with the tile's copy bytes (its first
+// arrival); lane a < Q copies direction a's rows and lane Q the class bytes,
+// so the copies of a tile are issued in parallel.  A source row outside a
+// closed y or z face is replaced by the node's own row of the opposite
+// direction (the bounced population, k_step's rule).  With a closed x face
+// the lanes then load the face values (plain loads) and lane 0 arrives a
+// second time once they are in the stage.
+template <int Q, class S, bool FACES>
 __device__ __forceinline__ void stg_issue(const typename S::T* __restrict__ src, const uint8_t* __restrict__ cls,
                                           const Geo& g, int R, int nty, int t, unsigned char* stage, uint64_t* bar,
-                                          int lane, int ey, int ez)
+                                          int lane, int ey, int ez, int oa)
 {
     using T = typename S::T;
     const int z = t / nty, y0 = (t - z * nty) * R;
@@ -136,48 +153,83 @@ __device__ __forceinline__ void stg_issue(const typename S::T* __restrict__ src,
     if (lane == 0) mbar_expect_tx(bar, (uint32_t)Q * nr * rowb + (uint32_t)nr * g.nxp);
     __syncwarp();
     if (lane < Q) {
-        const int zs = wrapi(z - ez, g.nz);
-        const int ys0 = y0 - ey;
         T* d = reinterpret_cast<T*>(stage) + (size_t)lane * R * g.nxp;
-        const T* s = src + (long long)lane * g.sq + (long long)zs * g.ny * g.nxp;
-        if (ys0 < 0) {                       // row -1 is row ny-1
-            bulk_g2s(d, s + (long long)(g.ny - 1) * g.nxp, rowb, bar);
-            if (nr > 1) bulk_g2s(d + g.nxp, s, (uint32_t)(nr - 1) * rowb, bar);
-        } else if (ys0 + nr > g.ny) {        // row ny is row 0
-            const int n1 = g.ny - ys0;
-            if (n1 > 0) bulk_g2s(d, s + (long long)ys0 * g.nxp, (uint32_t)n1 * rowb, bar);
-            bulk_g2s(d + (size_t)n1 * g.nxp, s, (uint32_t)(nr - n1) * rowb, bar);
+        // the node's own rows of the opposite direction (closed faces)
+        const T* so = src + (long long)oa * g.sq + (long long)z * g.ny * g.nxp;
+        const int zr = z - ez;
+        if (FACES && !g.periodic[2] && (zr < 0 || zr >= g.nz)) {
+            bulk_g2s(d, so + (long long)y0 * g.nxp, (uint32_t)nr * rowb, bar);
         } else {
-            bulk_g2s(d, s + (long long)ys0 * g.nxp, (uint32_t)nr * rowb, bar);
+            const T* s = src + (long long)lane * g.sq + (long long)wrapi(zr, g.nz) * g.ny * g.nxp;
+            const int ys0 = y0 - ey;
+            const bool cy = FACES && !g.periodic[1];
+            if (ys0 < 0) {                       // row -1: row ny-1, or out of a closed face
+                bulk_g2s(d, cy ? so + (long long)y0 * g.nxp : s + (long long)(g.ny - 1) * g.nxp, rowb, bar);
+                if (nr > 1) bulk_g2s(d + g.nxp, s, (uint32_t)(nr - 1) * rowb, bar);
+            } else if (ys0 + nr > g.ny) {        // row ny: row 0, or out of a closed face
+                const int n1 = g.ny - ys0;
+                if (n1 > 0) bulk_g2s(d, s + (long long)ys0 * g.nxp, (uint32_t)n1 * rowb, bar);
+                bulk_g2s(d + (size_t)n1 * g.nxp, cy ? so + (long long)(y0 + n1) * g.nxp : s,
+                         (uint32_t)(nr - n1) * rowb, bar);
+            } else {
+                bulk_g2s(d, s + (long long)ys0 * g.nxp, (uint32_t)nr * rowb, bar);
+            }
         }
     } else if (lane == Q) {
-        bulk_g2s(stage + (size_t)Q * R * g.nxp * sizeof(T), cls + ((long long)z * g.ny + y0) * g.nxp,
+        bulk_g2s(stage + stg_cls_off(Q, R, g.nxp, sizeof(T)), cls + ((long long)z * g.ny + y0) * g.nxp,
                  (uint32_t)nr * g.nxp, bar);
     }
+    if (FACES && !g.periodic[0]) {
+        // face values: own opposite population at x = 0 (side 0) and nx - 1
+        T* fa = reinterpret_cast<T*>(stage + stg_face_off(Q, R, g.nxp, sizeof(T)));
+        for (int i = lane; i < 2 * Q * nr; i += 32) {
+            const int side = i / (Q * nr), rem = i - side * Q * nr, a = rem / nr, r = rem - a * nr;
+            const long long row = ((long long)z * g.ny + y0 + r) * g.nxp;
+            fa[(side * Q + a) * R + r] = src[(long long)OPP<Q>(a) * g.sq + row + (side ? g.nx - 1 : 0)];
+        }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar);
 }
 
 // the pair (x0, x0+1) of direction a from a staged row: the pull sources
-// x0 - E_x and x0 + 1 - E_x, wrapped at the row ends (periodic x)
-template <int Q, class S>
-__device__ __forceinline__ float2 stg_pair(const typename S::T* __restrict__ row, int a, int x0, int nx)
+// x0 - ex and x0 + 1 - ex (ex = E_x, or 0 for a row that holds the node's own
+// opposite populations), wrapped at the row ends of a periodic x axis; at a
+// closed x face the element outside the box is the face value fl (x = 0) or
+// fr (x = nx - 1)
+template <class S>
+__device__ __forceinline__ float2 stg_pair(const typename S::T* __restrict__ row, int ex, int x0, int nx,
+                                           bool closed_x, typename S::T fl, typename S::T fr)
 {
     using T = typename S::T;
-    const int ex = EX<Q>(a);
     if constexpr (sizeof(T) == 2) {
         const uint32_t w = *reinterpret_cast<const uint32_t*>(row + x0);
         if (ex == 0) return S::unpack2(w);
         const unsigned short* h = reinterpret_cast<const unsigned short*>(row);
+        union { T t; unsigned short u; } cv;
         if (ex == 1) {                                    // values x0-1, x0
-            const uint32_t e = h[x0 == 0 ? nx - 1 : x0 - 1];
+            uint32_t e;
+            if (x0 == 0) {
+                cv.t = fl;
+                e = closed_x ? (uint32_t)cv.u : (uint32_t)h[nx - 1];
+            } else {
+                e = h[x0 - 1];
+            }
             return S::unpack2(__byte_perm(e, w, 0x5410));
         }
-        const uint32_t e = h[x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2];   // values x0+1, x0+2
+        uint32_t e;                                       // values x0+1, x0+2
+        if (x0 + 2 >= nx) {
+            cv.t = fr;
+            e = closed_x ? (uint32_t)cv.u : (uint32_t)h[x0 + 2 - nx];
+        } else {
+            e = h[x0 + 2];
+        }
         return S::unpack2(__byte_perm(w, e, 0x5432));
     } else {
         const float2 v = *reinterpret_cast<const float2*>(row + x0);
         if (ex == 0) return v;
-        if (ex == 1) return make_float2(row[x0 == 0 ? nx - 1 : x0 - 1], v.x);
-        return make_float2(v.y, row[x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2]);
+        if (ex == 1) return make_float2(x0 == 0 ? (closed_x ? fl : row[nx - 1]) : row[x0 - 1], v.x);
+        return make_float2(v.y, x0 + 2 >= nx ? (closed_x ? fr : row[x0 + 2 - nx]) : row[x0 + 2]);
     }
 }
 
@@ -253,7 +305,12 @@ __device__ __forceinline__ void gather_periodic(const typename S::T* __restrict_
     }
 }
 
-template <int Q, class S, bool SR>
+// EXT: the node code with the Lorentz force, Maxwell term, LES, linear
+// equilibrium or Darcy resistance; FACES: some box axis is closed.  The node
+// code of each configuration is k_step's: the FP32x2 pair code without EXT,
+// the FP32x2 EXT pair code for FP32 storage with closed faces, else the
+// scalar EXT code node by node.
+template <int Q, class S, bool SR, bool EXT = false, bool FACES = false>
 __global__ void __launch_bounds__(STG_THREADS, 1)
 k_step_staged(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
               const uint8_t* __restrict__ cls, const uint32_t* __restrict__ special, long long nspecial, const Geo g,
@@ -263,8 +320,9 @@ k_step_staged(const typename S::T* __restrict__ src, typename S::T* __restrict__
     using T = typename S::T;
     using Rt = typename S::R;
     static_assert(sizeof(Rt) == 4, "the staged step computes in FP32");
+    constexpr bool PAIRX = EXT && FACES && sizeof(T) == 4;
     extern __shared__ __align__(128) unsigned char smem[];
-    const size_t stage_bytes = stg_stage_bytes<Q, S>(R, g.nxp);
+    const size_t stage_bytes = stg_stage_bytes(Q, R, g.nxp, sizeof(T));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)nstages * stage_bytes);
     uint64_t* empty = full + nstages;
     const int nty = (g.ny + R - 1) / R;
@@ -277,7 +335,7 @@ k_step_staged(const typename S::T* __restrict__ src, typename S::T* __restrict__
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < nstages; ++s) {
-            mbar_init(&full[s], 1);
+            mbar_init(&full[s], 2);          // the producer's two arrivals (copies armed, face values in)
             mbar_init(&empty[s], STG_GROUP_WARPS);
         }
         mbar_fence_init();
@@ -287,12 +345,13 @@ k_step_staged(const typename S::T* __restrict__ src, typename S::T* __restrict__
 
     if (warp == STG_CWARPS) {
         // producer warp: refill a stage once the group that read it released it
-        int ey = 0, ez = 0;                  // the pull shift of this lane's direction
+        int ey = 0, ez = 0, oa = 0;          // the pull shift and opposite of this lane's direction
 #pragma unroll
         for (int b = 0; b < Q; ++b)
             if (b == lane) {
                 ey = EY<Q>(b);
                 ez = EZ<Q>(b);
+                oa = OPP<Q>(b);
             }
         int k = 0;
         for (; k < my_tiles; ++k) {
@@ -306,8 +365,8 @@ k_step_staged(const typename S::T* __restrict__ src, typename S::T* __restrict__
                     break;
                 }
             }
-            stg_issue<Q, S>(src, cls, g, R, nty, (int)blockIdx.x + k * (int)gridDim.x, smem + (size_t)s * stage_bytes,
-                            &full[s], lane, ey, ez);
+            stg_issue<Q, S, FACES>(src, cls, g, R, nty, (int)blockIdx.x + k * (int)gridDim.x,
+                                   smem + (size_t)s * stage_bytes, &full[s], lane, ey, ez, oa);
         }
         if (k < my_tiles && lane == 0) {
             // stopped early: let the copies already issued land before leaving
@@ -335,10 +394,11 @@ k_step_staged(const typename S::T* __restrict__ src, typename S::T* __restrict__
                 continue;
             }
             Rt d[Q];
-            gather_periodic<Q, S>(src, cls, g, p, x, y, z, node, d, fw, acc);
+            if constexpr (FACES) gather_node<Q, S, true, false>(src, cls, g, p, x, y, z, d);
+            else gather_periodic<Q, S>(src, cls, g, p, x, y, z, node, d, fw, acc);
             NodeM<Rt> m;
-            node_macro<Rt, Q, false, false>(d, p, m);
-            node_relax<Rt, Q, false>(d, p, m);
+            node_macro<Rt, Q, EXT, false>(d, p, m);
+            node_relax<Rt, Q, EXT>(d, p, m);
             if constexpr (SR) {
                 NodeRng rng((uint32_t)node, seed);
 #pragma unroll
@@ -348,7 +408,7 @@ k_step_staged(const typename S::T* __restrict__ src, typename S::T* __restrict__
                 for (int a = 0; a < Q; ++a) dst[(long long)a * g.sq + node] = S::from_raw(d[a]);
             }
         }
-        if (fw.out) {
+        if (!FACES && fw.out) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
 #pragma unroll
@@ -381,6 +441,7 @@ k_step_staged(const typename S::T* __restrict__ src, typename S::T* __restrict__
     const int group = warp / STG_GROUP_WARPS, gw = warp % STG_GROUP_WARPS;
     const int tasks_per_row = g.nxp / STG_TASK_NODES;
     const long long sq = g.sq;
+    const bool closed_x = FACES && !g.periodic[0];
     for (int k = group; k < my_tiles; k += STG_GROUPS) {
         const int s = k % nstages, use = k / nstages;
         if (!mbar_wait_bounded(&full[s], (uint32_t)use & 1u)) {
@@ -391,41 +452,97 @@ k_step_staged(const typename S::T* __restrict__ src, typename S::T* __restrict__
         const int z = t / nty, y0 = (t - z * nty) * R;
         const int nr = min(R, g.ny - y0);
         const T* sp = reinterpret_cast<const T*>(smem + (size_t)s * stage_bytes);
-        const uint8_t* sc = smem + (size_t)s * stage_bytes + (size_t)Q * R * g.nxp * sizeof(T);
+        const uint8_t* sc = smem + (size_t)s * stage_bytes + stg_cls_off(Q, R, g.nxp, sizeof(T));
+        const T* fa = reinterpret_cast<const T*>(smem + (size_t)s * stage_bytes + stg_face_off(Q, R, g.nxp, sizeof(T)));
         for (int task = gw; task < nr * tasks_per_row; task += STG_GROUP_WARPS) {
             const int r = task / tasks_per_row;
             const int x0 = (task - r * tasks_per_row) * STG_TASK_NODES + 2 * lane;
             const int y = y0 + r;
             const long long base = ((long long)z * g.ny + y) * g.nxp + x0;
-            // the pair path serves pairs whose aligned 4-node chunk is all bulk,
-            // as in k_step (whose vector chunks are 4 nodes), so both kernels
-            // run the same code on every node
+            // the pair path serves pairs whose aligned 4-node chunk holds only
+            // bulk (and, with closed faces, face) nodes, as in k_step, whose
+            // vector chunks are 4 nodes: both kernels run the same code on
+            // every node
             const uint32_t cb = *reinterpret_cast<const uint32_t*>(sc + (size_t)r * g.nxp + (x0 & ~3));
-            if (cb == 0u) {
-                F2 dd[Q];
+            if ((cb & (FACES ? ~0x02020202u : ~0u)) != 0u) continue;   // the boundary warps' (listed on the host)
+            FaceInfo fi;
+            if constexpr (FACES) {
+                fi.closed_x = closed_x;
+                fi.yo_lo = !g.periodic[1] && y == 0;
+                fi.yo_hi = !g.periodic[1] && y == g.ny - 1;
+                fi.zo_lo = (Q == 19) && !g.periodic[2] && z == 0;
+                fi.zo_hi = (Q == 19) && !g.periodic[2] && z == g.nz - 1;
+                fi.wx_lo = g.face_wall[0]; fi.wx_hi = g.face_wall[1];
+                fi.wy_lo = g.face_wall[2]; fi.wy_hi = g.face_wall[3];
+                fi.wz_lo = g.face_wall[4]; fi.wz_hi = g.face_wall[5];
+            }
+            F2 dd[Q];
 #pragma unroll
-                for (int a = 0; a < Q; ++a)
-                    dd[a] = F2{stg_pair<Q, S>(sp + ((size_t)a * R + r) * g.nxp, a, x0, g.nx)};
-                pair_collide<Q>(dd, p);
-                if constexpr (sizeof(T) == 2) {
-                    if constexpr (SR) {
-                        NodeRng rp((uint32_t)base, seed);
+            for (int a = 0; a < Q; ++a) {
+                int wall = 0;
+                const bool rout = FACES && row_out<Q>(fi, a, wall);
+                const T fl = closed_x ? fa[a * R + r] : T(0);
+                const T fr = closed_x ? fa[(Q + a) * R + r] : T(0);
+                dd[a] = F2{stg_pair<S>(sp + ((size_t)a * R + r) * g.nxp, rout ? 0 : EX<Q>(a), x0, g.nx, closed_x, fl,
+                                       fr)};
+            }
+            if (FACES && p.face_ladd && (cb & 0x02020202u)) {
+                // Ladd terms of moving face walls (k_step's add_ladd2)
 #pragma unroll
-                        for (int a = 0; a < Q; ++a)
-                            *reinterpret_cast<uint32_t*>(dst + (long long)a * sq + base) =
-                                S::pack2_sr(dd[a].v.x, dd[a].v.y, rp.word());
-                    } else {
-#pragma unroll
-                        for (int a = 0; a < Q; ++a)
-                            *reinterpret_cast<uint32_t*>(dst + (long long)a * sq + base) =
-                                S::pack2(dd[a].v.x, dd[a].v.y);
+                for (int a = 1; a < Q; ++a) {
+                    int wall = 0;
+                    const bool hit = row_out<Q>(fi, a, wall);
+                    int w0 = wall, w1 = wall;
+                    bool h0 = hit, h1 = hit;
+                    if (fi.closed_x) {
+                        if (EX<Q>(a) == 1 && x0 == 0) { h0 = true; w0 = fi.wx_lo; }
+                        if (EX<Q>(a) == -1 && x0 == g.nx - 1) { h0 = true; w0 = fi.wx_hi; }
+                        if (EX<Q>(a) == -1 && x0 + 1 == g.nx - 1) { h1 = true; w1 = fi.wx_hi; }
                     }
-                } else {
-#pragma unroll
-                    for (int a = 0; a < Q; ++a) *reinterpret_cast<float2*>(dst + (long long)a * sq + base) = dd[a].v;
+                    if (h0) dd[a].v.x += ladd_of<Q, float>(p, a, w0);
+                    if (h1) dd[a].v.y += ladd_of<Q, float>(p, a, w1);
                 }
             }
-            // other chunks are the boundary warps' (listed on the host)
+            if constexpr (!EXT || PAIRX) {
+                if constexpr (PAIRX) pair_collide_ext<Q>(dd, p);
+                else pair_collide<Q>(dd, p);
+            } else {
+                // the scalar EXT node code, node by node
+                Rt d0[Q], d1[Q];
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    d0[a] = dd[a].v.x;
+                    d1[a] = dd[a].v.y;
+                }
+                {
+                    NodeM<Rt> m;
+                    node_macro<Rt, Q, true, false>(d0, p, m);
+                    node_relax<Rt, Q, true>(d0, p, m);
+                }
+                {
+                    NodeM<Rt> m;
+                    node_macro<Rt, Q, true, false>(d1, p, m);
+                    node_relax<Rt, Q, true>(d1, p, m);
+                }
+#pragma unroll
+                for (int a = 0; a < Q; ++a) dd[a].v = make_float2(d0[a], d1[a]);
+            }
+            if constexpr (sizeof(T) == 2) {
+                if constexpr (SR) {
+                    NodeRng rp((uint32_t)base, seed);
+#pragma unroll
+                    for (int a = 0; a < Q; ++a)
+                        *reinterpret_cast<uint32_t*>(dst + (long long)a * sq + base) =
+                            S::pack2_sr(dd[a].v.x, dd[a].v.y, rp.word());
+                } else {
+#pragma unroll
+                    for (int a = 0; a < Q; ++a)
+                        *reinterpret_cast<uint32_t*>(dst + (long long)a * sq + base) = S::pack2(dd[a].v.x, dd[a].v.y);
+                }
+            } else {
+#pragma unroll
+                for (int a = 0; a < Q; ++a) *reinterpret_cast<float2*>(dst + (long long)a * sq + base) = dd[a].v;
+            }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);     // this warp is done with stage s

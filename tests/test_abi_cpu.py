@@ -224,8 +224,9 @@ def test_header_is_plain_c(tmp_path):
     assert r.returncode == 0, r.stderr
 
 
-@pytest.mark.parametrize("change", [dict(periodic=(1, 0, 1)), dict(storage="f64"), dict(les=1),
-                                    dict(maxwell=1), dict(lorentz=1, sigma_e=0.1)])
+@pytest.mark.parametrize("change", [dict(storage="f64"), dict(curved=1),
+                                    dict(lorentz=1, sigma_e=0.1, insulating=1, B=(0, 0.01, 0)),
+                                    dict(induced=1, maxwell=1, eta=0.05, B=(0, 0.01, 0))])
 def test_staged_kernel_refused_where_it_does_not_apply(lib, change):
     cfg, mask = workloads.sphere(nx=32, ny=16, nz=16, radius=4, center=(8, 8, 8), storage="f16s")
     c = lbm.make_config(**dict(cfg, step_kernel="staged", face_wall=(1, 1, 1, 1, 1, 1), **change))
