@@ -166,11 +166,9 @@ typedef struct lbm_config {
 
 /* Kernel of the fused step.  Both compute the same arithmetic and store the
  * same bits; they differ in how the pull sources reach the registers.
- * LBM_STEP_AUTO (0) picks the staged kernel for 16-bit storage in boxes
- * periodic on every axis with the plain node code (no lorentz, maxwell, les,
- * stokes, darcy) wherever enough shared memory holds its pipeline and at most
- * 2% of the 4-node chunks touch a solid or padding; else the register-tiled
- * one.  LBM_STEP_REGISTER (1): every thread loads its vectors straight from
+ * LBM_STEP_AUTO (0) picks the staged kernel for 16-bit storage wherever it
+ * applies, enough shared memory holds its pipeline and at most 2% of the
+ * 4-node chunks touch a solid or padding; else the register-tiled one.  LBM_STEP_REGISTER (1): every thread loads its vectors straight from
  * HBM.  LBM_STEP_STAGED (2): a persistent kernel stages each tile's source
  * rows in shared memory with bulk asynchronous copies; it serves FP32 and
  * 16-bit storage with closed or periodic faces and every node code except
