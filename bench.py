@@ -53,6 +53,7 @@ def parse():
                    help="storage of the headline run (profiling)")
     p.add_argument("--rounding", default="stochastic", choices=["nearest", "stochastic"],
                    help="rounding of 16-bit stores in the headline run")
+    p.add_argument("--size", type=int, default=256, help="edge of the cavity workload (profiling)")
     p.add_argument("--workload", default="sphere", choices=["sphere", "cavity"] + list(EXTENSIONS),
                    help="headline workload (profiling): sphere 256x128x128, cavity 256^3 LES, or the "
                         "sphere box with one extension (curved walls, insulating walls, Brinkman, induced field)")
@@ -192,13 +193,13 @@ EXTENSIONS = {
 }
 
 
-def make_workload(workloads, name, storage):
+def make_workload(workloads, name, storage, size=256):
     """(cfg, mask, phi or None) of a named workload."""
     if name == "sphere":
         c, m = workloads.sphere(storage=storage)
         return c, m, None
     if name == "cavity":
-        c, m = workloads.cavity(n=256, storage=storage)
+        c, m = workloads.cavity(n=size, storage=storage)
         return c, m, None
     out = getattr(workloads, EXTENSIONS[name][0])(storage=storage)
     return out if len(out) == 3 else (out[0], out[1], None)
@@ -296,7 +297,7 @@ def run_ours(args):
     out = {}
 
     # ---- headline: sphere, shifted binary16 storage
-    cfg, mask, phi = make_workload(workloads, args.workload, args.storage)
+    cfg, mask, phi = make_workload(workloads, args.workload, args.storage, args.size)
     hwall = 2 if args.workload == "cavity" else 1
     sr = args.storage in ("f16s", "bf16s") and args.rounding == "stochastic"
     if sr:
@@ -379,7 +380,7 @@ def run_ours(args):
             "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": {"sphere": WORKLOAD, "cavity": "D3Q19 LES cavity 256^3"}.get(
+            "config": {"workload": {"sphere": WORKLOAD, "cavity": f"D3Q19 LES cavity {args.size}^3"}.get(
                            args.workload, WORKLOAD + "; " + EXTENSIONS.get(args.workload, ("", "", ""))[2]),
                        "nodes": N, "fluid_nodes": fluid,
                        "storage": args.storage + (" (shifted x2^12, stochastic rounding)" if sr and args.storage == "f16s"

@@ -447,9 +447,16 @@ void choose_stage(Ctx& x)
     // an even count: each consumer group owns every other stage
     const int n = (int)std::min<size_t>(8, budget / (stage + 2 * sizeof(uint64_t))) & ~1;
     if (n < 4) return;
+    const long long tiles = (long long)((x.cfg.ny + R - 1) / R) * x.cfg.nz;
+    // automatic choice with closed faces or the EXT node code (longer tiles):
+    // at least 16 tiles per block, else the tail of the persistent grid costs
+    // more than the pipeline gains (LES cavity 128^3: 13 tiles per block,
+    // 16.0k staged against 19.6k MLUPS register-tiled)
+    const bool long_tiles = !all_periodic(&x.cfg) || x.ext;
+    if (x.cfg.step_kernel == LBM_STEP_AUTO && long_tiles && tiles < 16ll * x.sm_count) return;
     x.stage_R = R;
     x.stage_n = n;
-    x.stage_tiles = (long long)((x.cfg.ny + R - 1) / R) * x.cfg.nz;
+    x.stage_tiles = tiles;
     x.stage_smem = n * stage + 2 * n * sizeof(uint64_t);
 }
 
