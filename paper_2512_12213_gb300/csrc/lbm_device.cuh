@@ -243,6 +243,12 @@ constexpr int MAXW = 16;
 
 template <typename R> struct KP {
     R rho0, tau0, om0;
+    // momentum-consistent relaxation of the odd part (FP32 node codes): the
+    // axis directions' 3 w om as one constant wax, the diagonal ones' an
+    // exact power-of-two fraction of it, and om1 = 1 - K wax (K = 1/(3 w) of
+    // the axis directions: 6 for D3Q19, 3 for D2Q9) exact in this format
+    R wax, om1j;
+    int kmom;         // K
     R AG[3];          // dt g / c
     int model;
     int lorentz;
@@ -267,9 +273,10 @@ template <typename R> struct KP {
     int face_ladd;    // some closed face of the box is a moving wall
     R LW[MAXW + 1][3];  // 6 rho0 u_w / c per wall id (Ladd term = w_a E_a . LW)
     // per-launch constants of the node-pair path (uniform body force only):
-    // u^eq = u + ueq_c, u^F = uf_u u + uf_c, C = Cf, E_a . A = pe[a]
+    // u^eq = u + ueq_c, u^F = uf_u u + uf_c, C = Cf, E_a . A = pe[a],
+    // E_a . ueq_c = peq[a], E_a . uf_c = pf[a]
     R ueq_c[3], uf_u, uf_c[3], Cf;
-    R pe[19];
+    R pe[19], peq[19], pf[19];
     // insulating walls: the force coefficient dt sigma_e (E x B) / c of the
     // current field, kept on the device (replaces AEB), and the per-thread
     // rows of the step kernel's flow-velocity sums; null otherwise
@@ -295,6 +302,7 @@ __device__ __forceinline__ R maxwell_at(R k, const R (&B)[3], int a)
 template <typename R> struct NodeM {
     R Bl[3];              // the node's field (induced field only)
     R rho, drho;
+    R j[3];               // momentum sum E d (storage units)
     R u[3], A[3], v[3];   // in units of c (A: velocity increment per step)
     R weq[3], wf[3];      // u^eq / c and u^F / c (wf = 0 for model [a])
     R C, tau, om;
@@ -345,13 +353,17 @@ __device__ __forceinline__ void macro_from_moments(const Mom<R>& mo, const KP<R>
     const R rho = p.rho0 + drho, ir = R(1) / rho;
     m.rho = rho;
     m.drho = drho;
+    m.j[0] = mo.j[0]; m.j[1] = mo.j[1]; m.j[2] = (D == 3) ? mo.j[2] : R(0);
     m.u[0] = mo.j[0] * ir; m.u[1] = mo.j[1] * ir; m.u[2] = (D == 3) ? mo.j[2] * ir : R(0);
     m.A[0] = p.AG[0]; m.A[1] = p.AG[1]; m.A[2] = (D == 3) ? p.AG[2] : R(0);
     if (EXT && (p.lorentz || p.darcy_h != R(0))) {
         // v = u + A/2 with A = A_g + (kappa/rho)[(v.B)B - B^2 v] - dt darcy v in
         // the D simulated components: (1 + h + k B^2) v - k B_p (B_p . v) = w,
         // k = kappa/(2 rho), h = dt darcy/2, w = u + (A_g + A_EB/rho)/2,
-        // solved with the Sherman-Morrison formula.
+        // solved with the Sherman-Morrison formula; A itself is formed as
+        // 2 (v - u) = 2 (A_w/2 + s B - (h + k B^2) u) / (1 + h + k B^2), the
+        // small terms directly (v - u taken as a difference would lose the
+        // increment to the rounding of u and v in FP32).
         R wv[3], Ag[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -364,11 +376,9 @@ __device__ __forceinline__ void macro_from_moments(const Mom<R>& mo, const KP<R>
         const R al = R(1) + p.darcy_h;
         const R den = R(1) / (al + kk * p.B2);
         const R s = kk * Bw / (al + kk * (p.B2 - p.Bp2));
+        const R hk = p.darcy_h + kk * p.B2;
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-            const R vk = (wv[k] + s * p.B[k]) * den;
-            m.A[k] = R(2) * (vk - m.u[k]);
-        }
+        for (int k = 0; k < D; ++k) m.A[k] = R(2) * den * (R(0.5) * Ag[k] + s * p.B[k] - hk * m.u[k]);
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) m.v[k] = m.u[k] + R(0.5) * m.A[k];
@@ -426,57 +436,21 @@ __device__ __forceinline__ void node_macro(const R (&d)[Q], const KP<R>& p, Node
     macro_from_moments<R, Q, EXT, INS>(mo, p, m);
 }
 
-// what the relaxation of one node needs, compactly
-template <typename R> struct Coef {
-    R drho, rho, om, usq, fa, Crho;
-    R weq[3], wf[3], A[3];
-};
-
-template <typename R, int Q>
-__device__ __forceinline__ void coef_of(const NodeM<R>& m, Coef<R>& c)
+// The odd part's relaxation carries the momentum, and in FP32 a relative
+// error e in its coefficient shifts the momentum that a node gains in a step
+// by e om j against rho A: at |u| = 0.05 and a body force of 3e-7 one unit
+// in the last place of the coefficient (6e-8) is a 1.5% error.  So the odd
+// part relaxes with W_a = 3 w_a om per direction, W_axis rounded once and
+// every other W_a an exact power-of-two fraction of it (w_diag / w_axis =
+// 1/2 in D3Q19, 1/4 in D2Q9), and the population itself with
+// om1 = 1 - K W_axis (one rounding, exact for om in (0.75, 2)): the
+// momentum of (om1 d + W E.j) is then om1 j + K W_axis j = j exactly.
+template <int Q, typename R>
+__device__ __forceinline__ void momentum_coefs(R om, R& Wax, R& om1)
 {
-    constexpr int D = LatDim<Q>::D;
-    c.drho = m.drho;
-    c.rho = m.rho;
-    c.om = m.om;
-    c.usq = R(1.5) * (m.weq[0] * m.weq[0] + m.weq[1] * m.weq[1] + ((D == 3) ? m.weq[2] * m.weq[2] : R(0)));
-    c.fa = m.wf[0] * m.A[0] + m.wf[1] * m.A[1] + ((D == 3) ? m.wf[2] * m.A[2] : R(0));
-    c.Crho = m.C * m.rho;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        c.weq[k] = m.weq[k];
-        c.wf[k] = m.wf[k];
-        c.A[k] = m.A[k];
-    }
-}
-
-// Eq. (2) for the rest population
-template <typename R, int Q, bool EXT>
-__device__ __forceinline__ R relax_rest(R d0, const Coef<R>& c, const KP<R>& p)
-{
-    constexpr R w0 = R(WD<Q>(0));
-    const R deq = w0 * (c.drho - c.rho * c.usq) + ((EXT && p.maxwell) ? p.mx[0] : R(0));
-    return d0 + c.om * (deq - d0) - R(3) * w0 * c.Crho * c.fa;
-}
-
-// Eq. (2) for the opposite pair (a, opp(a)): equilibrium of Eq. (1) (+ Eq. 10)
-// split into its even and odd parts, force term of Eq. (3)
-template <typename R, int Q, bool EXT>
-__device__ __forceinline__ void relax_pair(int a, R& da, R& db, const Coef<R>& c, const KP<R>& p)
-{
-    constexpr int D = LatDim<Q>::D;
-    const R w = R(WD<Q>(a));
-    const int ex = EX<Q>(a), ey = EY<Q>(a), ez = EZ<Q>(a);
-    const R eu = R(ex) * c.weq[0] + R(ey) * c.weq[1] + ((D == 3) ? R(ez) * c.weq[2] : R(0));
-    const R ea = R(ex) * c.A[0] + R(ey) * c.A[1] + ((D == 3) ? R(ez) * c.A[2] : R(0));
-    const R ef = R(ex) * c.wf[0] + R(ey) * c.wf[1] + ((D == 3) ? R(ez) * c.wf[2] : R(0));
-    const R sym_eq = w * (c.drho + c.rho * (R(4.5) * eu * eu - c.usq)) + ((EXT && p.maxwell) ? p.mx[a] : R(0));
-    const R anti_eq = w * c.rho * R(3) * eu;
-    const R sym_f = w * c.Crho * (R(9) * ef * ea - R(3) * c.fa);
-    const R anti_f = w * c.Crho * R(3) * ea;
-    const R a0 = da, b0 = db;
-    da = a0 + c.om * (sym_eq + anti_eq - a0) + sym_f + anti_f;
-    db = b0 + c.om * (sym_eq - anti_eq - b0) + sym_f - anti_f;
+    constexpr R c = R(3 * WD<Q>(1)), K = R(Q == 19 ? 6 : 3);
+    Wax = om * c;
+    om1 = fma(-K, Wax, R(1));
 }
 
 // Eq. (2): d <- d + om (d^eq - d) + F for all populations of a node, in the
@@ -486,11 +460,22 @@ __device__ __forceinline__ void relax_pair(int a, R& da, R& db, const Coef<R>& c
 //        + 9 w C rho (E_a.W^F)(E_a.A)   (+ om Maxwell term)
 // and the odd part Pa = om 3 w rho t + 3 w C rho (E_a.A), the coefficients
 // taken once per speed class (Eqs. 1-3).
+//
+// The odd part is evaluated as Pa = 3 w (om E_a.j + rho E_a.A): with
+// rho u = j, W^eq = u + A/2 and C = 1 - om/2 (model [e]) or W^eq = u and
+// C = 1 (models [a]-[d]), om rho t + C rho E_a.A equals om E_a.j + rho E_a.A
+// exactly.  The odd part alone carries momentum, and in this form the
+// momentum that a node gains in a step is om j + rho A - om j = rho A up to
+// the rounding of the small terms themselves: u = j / rho and u + A/2,
+// rounded in FP32, never enter it.  (Rounded to nearest, u + A/2 misstates
+// the increment by the same fraction of a unit in the last place at every
+// node whose u shares a binade, which biases the momentum balance of a
+// whole flow by ~0.5% in FP32 at a body force of 3e-7.)
 template <typename R, int Q, bool EXT, bool MAGF = false>
 __device__ __forceinline__ void node_relax(R (&d)[Q], const KP<R>& p, const NodeM<R>& m)
 {
     constexpr int D = LatDim<Q>::D;
-    const R om = m.om, om1 = R(1) - om;
+    const R om = m.om;
     const R rho = m.rho, Crho = m.C * m.rho;
     const bool sto = EXT && p.stokes;        // linear equilibrium: no u^eq u^eq terms
     const R usq = sto ? R(0) : R(1.5) * (m.weq[0] * m.weq[0] + m.weq[1] * m.weq[1] + ((D == 3) ? m.weq[2] * m.weq[2] : R(0)));
@@ -503,11 +488,15 @@ __device__ __forceinline__ void node_relax(R (&d)[Q], const KP<R>& p, const Node
         if constexpr (MAGF) return maxwell_at<Q, R>(p.mxk, m.Bl, a);
         else return p.mx[a];
     };
+    // odd part: d_a' = om1 d_a + w (ps + 3 rho E_a.A) + W_a E_a.j with
+    // W_a = 3 w_a om and om1 = 1 - K W_axis (see momentum_coefs)
+    R Wax, om1j;
+    momentum_coefs<Q, R>(om, Wax, om1j);
     {
         constexpr R w0 = R(WD<Q>(0));
-        d[0] = om1 * d[0] + w0 * base + (mxw ? om * mx_of(0) : R(0));
+        d[0] = om1j * d[0] + w0 * base + (mxw ? om * mx_of(0) : R(0));
     }
-    const R k1 = sto ? R(0) : R(4.5) * om * rho, k2 = R(9) * Crho, kl = R(3) * om * rho, kf = R(3) * Crho;
+    const R k1 = sto ? R(0) : R(4.5) * om * rho, k2 = R(9) * Crho, kf = R(3) * rho;
 #pragma unroll
     for (int k = 0; k < LatDim<Q>::NP; ++k) {
         const int a = PAIR<Q>(k), b = OPP<Q>(a);
@@ -516,12 +505,14 @@ __device__ __forceinline__ void node_relax(R (&d)[Q], const KP<R>& p, const Node
         const R t = R(ex) * m.weq[0] + R(ey) * m.weq[1] + ((D == 3) ? R(ez) * m.weq[2] : R(0));
         const R ea = R(ex) * m.A[0] + R(ey) * m.A[1] + ((D == 3) ? R(ez) * m.A[2] : R(0));
         const R ef = R(ex) * m.wf[0] + R(ey) * m.wf[1] + ((D == 3) ? R(ez) * m.wf[2] : R(0));
+        const R ej = R(ex) * m.j[0] + R(ey) * m.j[1] + ((D == 3) ? R(ez) * m.j[2] : R(0));
         R ps = w * (base + k1 * t * t + k2 * ef * ea);
         if (mxw) ps += om * mx_of(a);
-        const R pa = w * (kl * t + kf * ea);
+        const R pa = w * (kf * ea);
+        const R Wa = Wax * R(WD<Q>(a) / WD<Q>(1));      // a power of two times Wax
         const R da = d[a], db = d[b];
-        d[a] = om1 * da + (ps + pa);
-        d[b] = om1 * db + (ps - pa);
+        d[a] = fma(Wa, ej, om1j * da + (ps + pa));
+        d[b] = fma(-Wa, ej, om1j * db + (ps - pa));
     }
 }
 
@@ -563,22 +554,36 @@ __device__ __forceinline__ F2 f2dot(int a, const F2 (&x)[3])
     return s;
 }
 
+__device__ __forceinline__ F2 f2rcp(F2 a) { return F2{make_float2(__frcp_rn(a.v.x), __frcp_rn(a.v.y))}; }
+__device__ __forceinline__ F2 f2sqrt(F2 a) { return F2{make_float2(__fsqrt_rn(a.v.x), __fsqrt_rn(a.v.y))}; }
+
 // Eq. (2) with Eqs. (1) and (3) for two nodes: d <- (1 - om) d + om d^eq + F,
 // per opposite pair d_a' = (1 - om) d_a + w (X + Y), d_opp' = (1 - om) d_opp
 // + w (X - Y) with X = base + 9/2 om rho t^2 + 9 C rho (E_a.u^F)(E_a.A),
-// Y = 3 om rho t + 3 C rho (E_a.A), t = E_a.u^eq
-template <int Q>
+// t = E_a.u^eq, and the odd part Y = 3 om rho t + 3 C rho (E_a.A) evaluated
+// as 3 om E_a.j + 3 rho E_a.A (equal for every model; node_relax says why).
+// LES: the Smagorinsky relaxation time of each node (the arithmetic of
+// macro_from_moments without the Maxwell term and the linear equilibrium),
+// so om, C and (model [c]) u^F become per-node pairs; the uniform body force
+// stays per launch.  GUO: a second relaxation loop for model [e] (u^F =
+// u^eq), taken by the 16-bit storage paths (it measured faster there and
+// cost the FP32 register-tiled kernel spills).
+template <int Q, bool LES = false, bool GUO = false>
 __device__ __forceinline__ void pair_collide(F2 (&d)[Q], const KP<float>& p)
 {
     constexpr int D = LatDim<Q>::D, NP = LatDim<Q>::NP;
-    // moments, from the even and odd parts of each opposite pair
+    // moments, from the even and odd parts of each opposite pair; LES adds
+    // sum E_i E_j d (xx yy zz xy xz yz)
     F2 drho = d[0];
     F2 j[3] = {f2s(0.0f), f2s(0.0f), f2s(0.0f)};
     bool has[3] = {false, false, false};
+    F2 P[6] = {f2s(0.0f), f2s(0.0f), f2s(0.0f), f2s(0.0f), f2s(0.0f), f2s(0.0f)};
+    bool hp[6] = {false, false, false, false, false, false};
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         const int a = PAIR<Q>(k), b = OPP<Q>(a);
-        drho = f2add(drho, f2add(d[a], d[b]));
+        const F2 sm = f2add(d[a], d[b]);
+        drho = f2add(drho, sm);
         const F2 t = f2sub(d[a], d[b]);
         const int e[3] = {EX<Q>(a), EY<Q>(a), EZ<Q>(a)};
 #pragma unroll
@@ -588,46 +593,154 @@ __device__ __forceinline__ void pair_collide(F2 (&d)[Q], const KP<float>& p)
             else j[c] = (e[c] > 0) ? f2add(j[c], t) : f2sub(j[c], t);
             has[c] = true;
         }
-    }
-    // macroscopic quantities (text after Eq. 1, Sec. 2)
-    const F2 rho = f2add(f2s(p.rho0), drho);
-    const F2 ir = F2{make_float2(__frcp_rn(rho.v.x), __frcp_rn(rho.v.y))};
-    F2 weq[3], wf[3];
+        if constexpr (LES) {
+            const int sg[6] = {e[0] * e[0], e[1] * e[1], e[2] * e[2], e[0] * e[1], e[0] * e[2], e[1] * e[2]};
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        if (c < D) {
-            const F2 u = f2mul(j[c], ir);
-            weq[c] = f2add(u, f2s(p.ueq_c[c]));
-            wf[c] = f2fma(f2s(p.uf_u), u, f2s(p.uf_c[c]));
-        } else {
-            weq[c] = f2s(0.0f);
-            wf[c] = f2s(0.0f);
+            for (int c = 0; c < 6; ++c) {
+                if (sg[c] == 0) continue;
+                if (!hp[c]) P[c] = (sg[c] > 0) ? sm : f2mul(sm, f2s(-1.0f));
+                else P[c] = (sg[c] > 0) ? f2add(P[c], sm) : f2sub(P[c], sm);
+                hp[c] = true;
+            }
         }
     }
-    const float om = p.om0, om1 = 1.0f - om;
-    F2 q = f2mul(weq[0], weq[0]);
-    F2 fa = f2mul(wf[0], f2s(p.AG[0]));
+    // macroscopic quantities (text after Eq. 1, Sec. 2): the node scalars
+    // u^eq.u^eq and u^F.A here; per direction below, E_a.u = (E_a.j) / rho,
+    // E_a.u^eq = E_a.u + E_a.ueq_c and E_a.u^F = uf_u E_a.u + E_a.uf_c, so
+    // that only j stays live through the relaxation
+    const F2 rho = f2add(f2s(p.rho0), drho);
+    const F2 ir = f2rcp(rho);
+    F2 q, fa, weq[3];
+    F2 om2, om12, C2, htau, wax2;      // per node with LES (htau = tau/2)
+    {
+        F2 u[3];
 #pragma unroll
-    for (int c = 1; c < D; ++c) {
-        q = f2fma(weq[c], weq[c], q);
-        fa = f2fma(wf[c], f2s(p.AG[c]), fa);
+        for (int c = 0; c < 3; ++c) {
+            u[c] = (c < D) ? f2mul(j[c], ir) : f2s(0.0f);
+            weq[c] = (c < D) ? f2add(u[c], f2s(p.ueq_c[c])) : f2s(0.0f);
+        }
+        if constexpr (LES) {
+            // tau_eff = (tau0 + sqrt(tau0^2 + 18 Cs^2 |Pi| / rho)) / 2 with
+            // |Pi| = sqrt(2 Pi:Pi), Pi = sum E E d - (drho/3 I + rho u^eq u^eq)
+            F2 PP = f2s(0.0f);
+            const F2 dr3 = f2mul(drho, f2s(1.0f / 3.0f));
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const int i = (c < 3) ? c : (c == 5 ? 1 : 0);
+                const int jj = (c < 3) ? c : (c == 3 ? 1 : 2);
+                if (D == 2 && (i == 2 || jj == 2)) continue;
+                F2 Pc = f2sub(P[c], f2mul(rho, f2mul(weq[i], weq[jj])));
+                if (i == jj) Pc = f2sub(Pc, dr3);
+                PP = f2fma(f2s(i == jj ? 1.0f : 2.0f), f2mul(Pc, Pc), PP);
+            }
+            const F2 inner = f2fma(f2mul(f2s(p.lesc), f2sqrt(f2mul(f2s(2.0f), PP))), ir, f2s(p.tau0 * p.tau0));
+            const F2 tau = f2mul(f2s(0.5f), f2add(f2s(p.tau0), f2sqrt(inner)));
+            om2 = f2rcp(tau);
+            // W_axis and om1 = 1 - K W_axis per node (momentum_coefs)
+            wax2 = f2mul(om2, f2s((float)(3 * WD<Q>(1))));
+            om12 = f2fma(f2s(Q == 19 ? -6.0f : -3.0f), wax2, f2s(1.0f));
+            C2 = (p.model == MODEL_E) ? f2fma(f2s(-0.5f), om2, f2s(1.0f)) : f2s(1.0f);
+            htau = f2mul(f2s(0.5f), tau);
+        }
+        q = f2mul(weq[0], weq[0]);
+#pragma unroll
+        for (int c = 1; c < D; ++c) q = f2fma(weq[c], weq[c], q);
+        // u^F (model [c] with LES: u + tau A / 2 at the node's tau)
+        auto wf = [&](int c) -> F2 {
+            if (LES && p.model == MODEL_C) return f2fma(htau, f2s(p.AG[c]), u[c]);
+            return f2fma(f2s(p.uf_u), u[c], f2s(p.uf_c[c]));
+        };
+        fa = f2mul(wf(0), f2s(p.AG[0]));
+#pragma unroll
+        for (int c = 1; c < D; ++c) fa = f2fma(wf(c), f2s(p.AG[c]), fa);
     }
-    const F2 Crho = f2mul(f2s(p.Cf), rho);
+    // relaxation constants: per node with LES, per launch otherwise
+    F2 omv, om1v, Crho, Wax, nWax, Wdg, nWdg;
+    constexpr float wr = (float)(WD<Q>(Q == 19 ? 7 : 5) / WD<Q>(1));   // w_diag / w_axis: 1/2 or 1/4
+    if constexpr (LES) {
+        omv = om2;
+        om1v = om12;
+        Crho = f2mul(C2, rho);
+        Wax = wax2;
+        nWax = f2mul(wax2, f2s(-1.0f));
+        Wdg = f2mul(wax2, f2s(wr));
+        nWdg = f2mul(wax2, f2s(-wr));
+    } else {
+        omv = f2s(p.om0);
+        om1v = f2s(p.om1j);
+        Crho = f2mul(f2s(p.Cf), rho);
+        Wax = f2s(p.wax);
+        nWax = f2s(-p.wax);
+        Wdg = f2s(p.wax * wr);
+        nWdg = f2s(-p.wax * wr);
+    }
     // base = om (drho - 3/2 rho u^eq.u^eq) - 3 C rho u^F.A
     F2 base = f2fma(rho, f2mul(q, f2s(-1.5f)), drho);
-    base = f2fma(f2s(om), base, f2mul(Crho, f2mul(fa, f2s(-3.0f))));
-    d[0] = f2fma(f2s(om1), d[0], f2mul(f2s((float)WD<Q>(0)), base));
-    const F2 k1 = f2mul(rho, f2s(4.5f * om)), kl = f2mul(rho, f2s(3.0f * om));
+    base = f2fma(omv, base, f2mul(Crho, f2mul(fa, f2s(-3.0f))));
+    d[0] = f2fma(om1v, d[0], f2mul(f2s((float)WD<Q>(0)), base));
+    const F2 k1 = LES ? f2mul(rho, f2mul(f2s(4.5f), omv)) : f2mul(rho, f2s(4.5f * p.om0));
+    if (GUO && p.model == MODEL_E) {
+        // u^F = u^eq: E_a.u^F = t, and the even part w X = w base +
+        // t (9/2 w om rho t + 9 w C rho E_a.A) with its node scalars scaled
+        // once per speed class
+        constexpr float wax_w = (float)WD<Q>(1), wdg_w = (float)WD<Q>(Q == 19 ? 7 : 5);
+        const F2 wb_ax = f2mul(f2s(wax_w), base), wb_dg = f2mul(f2s(wdg_w), base);
+        const F2 wk_ax = f2mul(f2s(wax_w), k1), wk_dg = f2mul(f2s(wdg_w), k1);
 #pragma unroll
-    for (int k = 0; k < NP; ++k) {
-        const int a = PAIR<Q>(k), b = OPP<Q>(a);
-        const float w = (float)WD<Q>(a);
-        const F2 t = f2dot<Q>(a, weq), ef = f2dot<Q>(a, wf);
-        F2 X = f2fma(k1, f2mul(t, t), base);
-        X = f2fma(f2mul(Crho, f2s(9.0f * p.pe[a])), ef, X);
-        const F2 Y = f2fma(kl, t, f2mul(Crho, f2s(3.0f * p.pe[a])));
-        d[a] = f2fma(f2s(w), f2add(X, Y), f2mul(f2s(om1), d[a]));
-        d[b] = f2fma(f2s(w), f2sub(X, Y), f2mul(f2s(om1), d[b]));
+        for (int k = 0; k < NP; ++k) {
+            const int a = PAIR<Q>(k), b = OPP<Q>(a);
+            const float w = (float)WD<Q>(a);
+            const bool axis = SPEED2<Q>(a) == 1;
+            const F2 t = f2dot<Q>(a, weq), ej = f2dot<Q>(a, j);
+            const F2 wX = f2fma(t, f2fma(axis ? wk_ax : wk_dg, t, f2mul(Crho, f2s(9.0f * w * p.pe[a]))),
+                                axis ? wb_ax : wb_dg);
+            const F2 wY = f2mul(rho, f2s(3.0f * w * p.pe[a]));
+            // the odd part's W_a E_a.j last (momentum_coefs)
+            d[a] = f2fma(axis ? Wax : Wdg, ej, f2fma(om1v, d[a], f2add(wX, wY)));
+            d[b] = f2fma(axis ? nWax : nWdg, ej, f2fma(om1v, d[b], f2sub(wX, wY)));
+        }
+        return;
+    }
+    // E_a.j, E_a.u^eq = (E_a.j)/rho + E_a.ueq_c, E_a.u^F = uf_u (E_a.j)/rho
+    // + E_a.uf_c (model [c] with LES: (E_a.j)/rho + tau/2 E_a.A)
+    auto dots = [&](int a, F2& t, F2& ef, F2& ej) {
+        ej = f2dot<Q>(a, j);
+        const F2 eu = f2mul(ej, ir);
+        t = f2add(eu, f2s(p.peq[a]));
+        if (LES && p.model == MODEL_C) ef = f2fma(htau, f2s(p.pe[a]), eu);
+        else ef = f2fma(f2s(p.uf_u), eu, f2s(p.pf[a]));
+    };
+    if constexpr (LES) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const int a = PAIR<Q>(k), b = OPP<Q>(a);
+            const float w = (float)WD<Q>(a);
+            const bool axis = SPEED2<Q>(a) == 1;
+            F2 t, ef, ej;
+            dots(a, t, ef, ej);
+            F2 X = f2fma(k1, f2mul(t, t), base);
+            X = f2fma(f2mul(Crho, f2s(9.0f * p.pe[a])), ef, X);
+            const F2 Y = f2mul(rho, f2s(3.0f * p.pe[a]));
+            // the odd part's W_a E_a.j last (momentum_coefs)
+            d[a] = f2fma(axis ? Wax : Wdg, ej, f2fma(f2s(w), f2add(X, Y), f2mul(om1v, d[a])));
+            d[b] = f2fma(axis ? nWax : nWdg, ej, f2fma(f2s(w), f2sub(X, Y), f2mul(om1v, d[b])));
+        }
+    } else {
+        const float om1 = p.om1j;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const int a = PAIR<Q>(k), b = OPP<Q>(a);
+            const float w = (float)WD<Q>(a);
+            F2 t, ef, ej;
+            dots(a, t, ef, ej);
+            // W_a = p.wax times an exact power of two (momentum_coefs)
+            const float Wa = p.wax * (float)(WD<Q>(a) / WD<Q>(1));
+            F2 X = f2fma(k1, f2mul(t, t), base);
+            X = f2fma(f2mul(Crho, f2s(9.0f * p.pe[a])), ef, X);
+            const F2 Y = f2mul(rho, f2s(3.0f * p.pe[a]));
+            d[a] = f2fma(f2s(Wa), ej, f2fma(f2s(w), f2add(X, Y), f2mul(f2s(om1), d[a])));
+            d[b] = f2fma(f2s(-Wa), ej, f2fma(f2s(w), f2sub(X, Y), f2mul(f2s(om1), d[b])));
+        }
     }
 }
 
@@ -637,9 +750,6 @@ __device__ __forceinline__ void pair_collide(F2 (&d)[Q], const KP<float>& p)
 // and node_relax lane by lane, with the per-node relaxation rate as a pair;
 // square roots and reciprocals per lane in IEEE FP32.  Not for insulating
 // walls (their coefficient lives on the device) or the induced field.
-__device__ __forceinline__ F2 f2rcp(F2 a) { return F2{make_float2(__frcp_rn(a.v.x), __frcp_rn(a.v.y))}; }
-__device__ __forceinline__ F2 f2sqrt(F2 a) { return F2{make_float2(__fsqrt_rn(a.v.x), __fsqrt_rn(a.v.y))}; }
-
 template <int Q>
 __device__ __forceinline__ void pair_collide_ext(F2 (&d)[Q], const KP<float>& p)
 {
@@ -690,10 +800,13 @@ __device__ __forceinline__ void pair_collide_ext(F2 (&d)[Q], const KP<float>& p)
         const float al = 1.0f + p.darcy_h;
         const F2 den = f2rcp(f2fma(kk, f2s(p.B2), f2s(al)));
         const F2 sB = f2mul(f2mul(kk, Bw), f2rcp(f2fma(kk, f2s(p.B2 - p.Bp2), f2s(al))));
+        // A = 2 (A_w/2 + s B - (h + k B^2) u) / (1 + h + k B^2): the small
+        // terms directly, as in macro_from_moments
+        const F2 hk = f2fma(kk, f2s(p.B2), f2s(p.darcy_h));
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            const F2 vk = f2mul(f2fma(sB, f2s(p.B[c]), wv[c]), den);
-            A[c] = f2mul(f2s(2.0f), f2sub(vk, u[c]));
+            const F2 vu = f2fma(f2mul(hk, f2s(-1.0f)), u[c], f2fma(sB, f2s(p.B[c]), f2mul(f2s(0.5f), Ag[c])));
+            A[c] = f2mul(f2mul(f2s(2.0f), den), vu);
         }
     }
     F2 v[3], weq[3];
@@ -733,8 +846,10 @@ __device__ __forceinline__ void pair_collide_ext(F2 (&d)[Q], const KP<float>& p)
         default: wf[c] = v[c]; break;
         }
     }
-    // Eq. (2) with the equilibrium of Eq. (1) (+ Eq. 10) and the force of Eq. (3)
-    const F2 om1 = f2sub(f2s(1.0f), om), Crho = f2mul(C, rho);
+    // Eq. (2) with the equilibrium of Eq. (1) (+ Eq. 10) and the force of Eq. (3);
+    // the odd part relaxes with W_axis and om1 = 1 - K W_axis (momentum_coefs)
+    const F2 wax = f2mul(om, f2s((float)(3 * WD<Q>(1))));
+    const F2 om1 = f2fma(f2s(Q == 19 ? -6.0f : -3.0f), wax, f2s(1.0f)), Crho = f2mul(C, rho);
     F2 usq = f2s(0.0f), fa = f2s(0.0f);
 #pragma unroll
     for (int c = 0; c < D; ++c) {
@@ -750,19 +865,25 @@ __device__ __forceinline__ void pair_collide_ext(F2 (&d)[Q], const KP<float>& p)
         d[0] = r0;
     }
     const F2 k1 = p.stokes ? f2s(0.0f) : f2mul(f2mul(f2s(4.5f), om), rho);
-    const F2 k2 = f2mul(f2s(9.0f), Crho), kl = f2mul(f2mul(f2s(3.0f), om), rho), kf = f2mul(f2s(3.0f), Crho);
+    // odd part W_a E_a.j + 3 w rho E_a.A (node_relax says why)
+    const F2 k2 = f2mul(f2s(9.0f), Crho);
+    constexpr float wr = (float)(WD<Q>(Q == 19 ? 7 : 5) / WD<Q>(1));   // w_diag / w_axis
+    const F2 wdg = f2mul(wax, f2s(wr)), nax = f2mul(wax, f2s(-1.0f)), ndg = f2mul(wax, f2s(-wr));
+    // 3 w rho per speed class (the odd force term 3 w rho E_a.A)
+    const F2 kf_ax = f2mul(f2s((float)(3 * WD<Q>(1))), rho), kf_dg = f2mul(kf_ax, f2s(wr));
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         const int a = PAIR<Q>(k), b = OPP<Q>(a);
         const float w = (float)WD<Q>(a);
-        const F2 t = f2dot<Q>(a, weq), ea = f2dot<Q>(a, A), ef = f2dot<Q>(a, wf);
+        const bool axis = SPEED2<Q>(a) == 1;
+        const F2 t = f2dot<Q>(a, weq), ea = f2dot<Q>(a, A), ef = f2dot<Q>(a, wf), ej = f2dot<Q>(a, j);
         F2 ps = f2fma(k1, f2mul(t, t), base);
         ps = f2fma(k2, f2mul(ef, ea), ps);
         ps = f2mul(f2s(w), ps);
         if (p.maxwell) ps = f2fma(om, f2s(p.mx[a]), ps);
-        const F2 pa = f2mul(f2s(w), f2fma(kl, t, f2mul(kf, ea)));
-        d[a] = f2fma(om1, d[a], f2add(ps, pa));
-        d[b] = f2fma(om1, d[b], f2sub(ps, pa));
+        const F2 pa = f2mul(axis ? kf_ax : kf_dg, ea);
+        d[a] = f2fma(axis ? wax : wdg, ej, f2fma(om1, d[a], f2add(ps, pa)));
+        d[b] = f2fma(axis ? nax : ndg, ej, f2fma(om1, d[b], f2sub(ps, pa)));
     }
 }
 

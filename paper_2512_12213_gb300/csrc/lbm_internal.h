@@ -117,6 +117,7 @@ struct Ctx {
     lbm_config cfg;
     int device;
     int ext;                 // Lorentz force, Maxwell equilibrium or LES present
+    int les_pair;            // LES alone among the EXT terms, FP32 compute: the FP32x2 LES pair code
     int sr;                  // stochastic rounding of 16-bit stores
     Geo geo;
     KP<double> kpd;          // physical units

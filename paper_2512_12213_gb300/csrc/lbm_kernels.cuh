@@ -88,8 +88,8 @@ __device__ __forceinline__ void block_sum(double (&v)[W], double* smem /* >= W *
 // blocks at 96 registers, which spill with the FP32x2 node pairs)
 // (the EXT node code in FP32x2 node pairs, 32-bit storage with closed faces:
 // 3, where it needs 158 registers without spill)
-template <class S, bool EXT, bool FACES = false, bool FULL = false> struct StepOcc {
-    static constexpr bool PAIRX = EXT && !FULL && FACES && sizeof(typename S::T) == 4;
+template <class S, bool EXT, bool FACES = false, bool FULL = false, bool LP = false> struct StepOcc {
+    static constexpr bool PAIRX = EXT && !FULL && !LP && FACES && sizeof(typename S::T) == 4;
     static constexpr int value = (sizeof(typename S::T) == 8 || PAIRX) ? 3 : 4;
 };
 
@@ -99,8 +99,12 @@ template <class S, bool EXT, bool FACES = false, bool FULL = false> struct StepO
 // insulating walls).  Kept out of the other instantiations: even as one
 // out-of-line call the interpolation cost the fused step ~3% (inlined ~5%),
 // and the insulating-wall code cost the LES cavity 8%.
-template <int Q, class S, bool EXT, bool FACES, bool SR, bool FULL = false>
-__global__ void __launch_bounds__(STEP_THREADS, StepOcc<S, EXT, FACES, FULL>::value)
+// LP: the LES-only contexts with 16-bit storage (Smagorinsky with a uniform
+// body force and no other EXT term) relax their all-fluid chunks with the
+// FP32x2 pair code specialised for LES; chunks with a wall keep the scalar
+// EXT node code.
+template <int Q, class S, bool EXT, bool FACES, bool SR, bool FULL = false, bool LP = false>
+__global__ void __launch_bounds__(STEP_THREADS, StepOcc<S, EXT, FACES, FULL, LP>::value)
 k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
        const uint8_t* __restrict__ cls, const Geo g, const KP<typename S::R> p, uint32_t seed)
 {
@@ -363,11 +367,11 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
         };
         // two nodes at a time in packed FP32x2 arithmetic (FP32 compute without
         // the Lorentz force, Maxwell term or LES)
-        constexpr bool PAIR2 = !EXT && sizeof(R) == 4;
+        constexpr bool PAIR2 = (!EXT || LP) && sizeof(R) == 4;
     // the EXT node code in node pairs too: FP32 storage with closed faces (the
     // LES cavity 24.7k -> 26.6k MLUPS); measured slower for 16-bit storage
     // (-3.7%) and periodic FP32 boxes (-2.5%, spills), which keep the scalar code
-    constexpr bool PAIRX = StepOcc<S, EXT, FACES, FULL>::PAIRX;
+    constexpr bool PAIRX = StepOcc<S, EXT, FACES, FULL, LP>::PAIRX;
 
         const long long base = row * g.nxp + x0;
         if (!special) {
@@ -378,7 +382,7 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
 #pragma unroll
                     for (int a = 0; a < Q; ++a) dd[a] = F2{S::unpack2(w[a][i])};
                     if (ladd) add_ladd2(dd, 2 * i);
-                    if constexpr (PAIR2) pair_collide<Q>(dd, p);
+                    if constexpr (PAIR2) pair_collide<Q, LP, true>(dd, p);
                     else pair_collide_ext<Q>(dd, p);
                     if constexpr (SR) {
                         NodeRng rp((uint32_t)(base + 2 * i), seed);     // the pair's first node
@@ -458,7 +462,7 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                             f[a][V - 1] = S::from_raw(dd[a].v.y);
                         }
                     }
-                } else if constexpr (EXT) {
+                } else if constexpr (EXT && !LP) {
                     // larger node code (Lorentz / Maxwell / LES): the same rolled queue
 #pragma unroll 1
                     for (int k = 0; k < V; ++k) {
@@ -484,7 +488,7 @@ k_step(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
 #pragma unroll
                         for (int a = 0; a < Q; ++a) dd[a] = F2{make_float2(S::to_raw(f[a][2 * i]), S::to_raw(f[a][2 * i + 1]))};
                         if (ladd) add_ladd2(dd, 2 * i);
-                        pair_collide<Q>(dd, p);
+                        pair_collide<Q, LP>(dd, p);
 #pragma unroll
                         for (int a = 0; a < Q; ++a) {
                             f[a][2 * i] = S::from_raw(dd[a].v.x);
@@ -1149,6 +1153,17 @@ cudaError_t launch_step_q(const Ctx& c, const void* src, void* dst, uint32_t see
     const long long nch = (long long)(c.geo.nxp / S::V) * c.geo.ny * c.geo.nz;
     const int blocks = grid_for(nch, STEP_THREADS, 1ll << 31);
     const bool faces = !c.geo.periodic[0] || !c.geo.periodic[1] || (Q == 19 && !c.geo.periodic[2]);
+    if constexpr (EXT && sizeof(typename S::T) == 2) {
+        if (c.les_pair) {
+            if (faces)
+                k_step<Q, S, EXT, true, SR, false, true><<<blocks, STEP_THREADS, 0, st>>>(
+                    (const T*)src, (T*)dst, c.cls, c.geo, kp_step_of<S>(c), seed);
+            else
+                k_step<Q, S, EXT, false, SR, false, true><<<blocks, STEP_THREADS, 0, st>>>(
+                    (const T*)src, (T*)dst, c.cls, c.geo, kp_step_of<S>(c), seed);
+            return cudaGetLastError();
+        }
+    }
     if ((c.cfg.curved || c.insulating) && faces)
         k_step<Q, S, EXT, true, SR, true><<<blocks, STEP_THREADS, 0, st>>>((const T*)src, (T*)dst, c.cls, c.geo,
                                                                            kp_step_of<S>(c), seed);
@@ -1166,12 +1181,12 @@ cudaError_t launch_step_q(const Ctx& c, const void* src, void* dst, uint32_t see
 
 // the staged step (periodic boxes with the plain node code, 16-bit or FP32
 // storage; the host chose the tile rows and stage count at create)
-template <int Q, class S, bool SR, bool EXT, bool FACES>
+template <int Q, class S, bool SR, bool EXT, bool FACES, bool LP = false>
 cudaError_t launch_step_staged_k(const Ctx& c, const void* src, void* dst, uint32_t seed, cudaStream_t st,
                                  const StgForce& fw)
 {
     using T = typename S::T;
-    auto kern = k_step_staged<Q, S, SR, EXT, FACES>;
+    auto kern = k_step_staged<Q, S, SR, EXT, FACES, LP>;
     // a context always launches the same instantiation: set its shared
     // memory limit on the first launch
     if (!c.stage_ready) {
@@ -1191,6 +1206,11 @@ cudaError_t launch_step_staged(const Ctx& c, const void* src, void* dst, uint32_
                                const StgForce& fw)
 {
     const bool faces = !c.geo.periodic[0] || !c.geo.periodic[1] || (Q == 19 && !c.geo.periodic[2]);
+    if constexpr (sizeof(typename S::T) == 2) {
+        if (c.les_pair)
+            return faces ? launch_step_staged_k<Q, S, SR, true, true, true>(c, src, dst, seed, st, fw)
+                         : launch_step_staged_k<Q, S, SR, true, false, true>(c, src, dst, seed, st, fw);
+    }
     if (c.ext)
         return faces ? launch_step_staged_k<Q, S, SR, true, true>(c, src, dst, seed, st, fw)
                      : launch_step_staged_k<Q, S, SR, true, false>(c, src, dst, seed, st, fw);

@@ -309,8 +309,9 @@ __device__ __forceinline__ void gather_periodic(const typename S::T* __restrict_
 // equilibrium or Darcy resistance; FACES: some box axis is closed.  The node
 // code of each configuration is k_step's: the FP32x2 pair code without EXT,
 // the FP32x2 EXT pair code for FP32 storage with closed faces, else the
-// scalar EXT code node by node.
-template <int Q, class S, bool SR, bool EXT = false, bool FACES = false>
+// scalar EXT code node by node; LP: the FP32x2 pair code specialised for
+// LES (LES-only contexts).
+template <int Q, class S, bool SR, bool EXT = false, bool FACES = false, bool LP = false>
 __global__ void __launch_bounds__(STG_THREADS, 1)
 k_step_staged(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
               const uint8_t* __restrict__ cls, const uint32_t* __restrict__ special, long long nspecial, const Geo g,
@@ -320,7 +321,7 @@ k_step_staged(const typename S::T* __restrict__ src, typename S::T* __restrict__
     using T = typename S::T;
     using Rt = typename S::R;
     static_assert(sizeof(Rt) == 4, "the staged step computes in FP32");
-    constexpr bool PAIRX = EXT && FACES && sizeof(T) == 4;
+    constexpr bool PAIRX = EXT && !LP && FACES && sizeof(T) == 4;
     extern __shared__ __align__(128) unsigned char smem[];
     const size_t stage_bytes = stg_stage_bytes(Q, R, g.nxp, sizeof(T));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)nstages * stage_bytes);
@@ -503,9 +504,9 @@ k_step_staged(const typename S::T* __restrict__ src, typename S::T* __restrict__
                     if (h1) dd[a].v.y += ladd_of<Q, float>(p, a, w1);
                 }
             }
-            if constexpr (!EXT || PAIRX) {
+            if constexpr (!EXT || LP || PAIRX) {
                 if constexpr (PAIRX) pair_collide_ext<Q>(dd, p);
-                else pair_collide<Q>(dd, p);
+                else pair_collide<Q, LP, sizeof(T) == 2>(dd, p);
             } else {
                 // the scalar EXT node code, node by node
                 Rt d0[Q], d1[Q];

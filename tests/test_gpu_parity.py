@@ -172,6 +172,28 @@ def test_force_models_fp32_paths(orc, name, model, storage):
     assert err < TOL[storage], err
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s"])
+@pytest.mark.parametrize("model", "abcde")
+@pytest.mark.parametrize("name", ["d2q9", "d3q19", "periodic_ragged"])
+def test_les_with_body_force_every_model(orc, name, model, storage):
+    """Smagorinsky LES with a uniform body force and no other EXT term, every
+    force model: 16-bit storage takes the FP32x2 pair code specialised for
+    LES (per-node relaxation rate, C and, for model [c], u^F), FP32 storage
+    the EXT node code (in pairs where a box face is closed), FP64 the scalar
+    EXT code; each against the oracle."""
+    cfg, mask = _case(name, model, storage)
+    cfg = dict(cfg, les=1, cs=0.18)
+    ocfg, f0, _, _ = _initial(orc, cfg, mask, amp=3e-3)
+    sim = lbm.Sim(cfg, mask)
+    sim.import_f(f0)
+    steps = 10
+    sim.step(steps)
+    f_ref = orc.run(ocfg, mask, f0, steps)
+    err = _rel(sim.export_f().cpu().numpy(), f_ref)
+    assert err < TOL[storage], err
+    assert sim.device_status() == 0
+
+
 @pytest.mark.parametrize("name,model", [("d2q9", "e"), ("d2q9_mhd", "d"), ("d3q19", "c"), ("d3q19_ext", "e")])
 def test_init_equilibrium_matches_oracle(orc, name, model):
     cfg, mask = _case(name, model)

@@ -169,6 +169,11 @@ def _closed_box(name):
         nx, ny = 131, 24
         return dict(lattice=9, nx=nx, ny=ny, nz=1, periodic=(1, 0, 1), tau=0.8, force_model="d", g=(1e-4, 0, 0),
                     wall_u=((0, 0, 0), (0.05, 0, 0)), face_wall=(1, 1, 1, 2, 1, 1)), inputs.empty_mask(nx, ny)
+    if name == "les_periodic_c":   # periodic box with a sphere, LES alone with model [c] and a body force
+        nx, ny, nz = 64, 12, 10
+        mask = inputs.sphere_mask(nx, ny, nz, (30.6, 5.9, 4.7), 2.9, wall=1)
+        return dict(lattice=19, nx=nx, ny=ny, nz=nz, periodic=(1, 1, 1), tau=0.56, force_model="c",
+                    g=(2e-4, -1e-4, 5e-5), les=1, cs=0.14, wall_u=((0, 0, 0),)), mask
     if name == "brinkman_periodic":  # periodic box, linear equilibrium and Darcy resistance (EXT)
         nx, ny, nz = 64, 12, 10
         mask = inputs.sphere_mask(nx, ny, nz, (20.3, 6.1, 5.2), 3.1, wall=1)
@@ -178,13 +183,15 @@ def _closed_box(name):
 
 
 @pytest.mark.parametrize("storage,rounding", [("f16s", "stochastic"), ("bf16s", "nearest"), ("f32", "nearest")])
-@pytest.mark.parametrize("name", ["cavity_les", "closed_x_moving", "mhd_channel", "channel_2d", "brinkman_periodic"])
+@pytest.mark.parametrize("name", ["cavity_les", "closed_x_moving", "mhd_channel", "channel_2d", "brinkman_periodic",
+                                  "les_periodic_c"])
 def test_staged_closed_faces_and_ext_equal_register(orc, name, storage, rounding):
     """The staged kernel with closed box faces (rows outside a closed face
     replaced by the node's own opposite populations, the x-face values staged
     by the producer, Ladd's term of moving faces) and with the EXT node code
     (LES, Lorentz force, Maxwell term, linear equilibrium, Darcy) stores the
-    register-tiled kernel's bits."""
+    register-tiled kernel's bits (LES alone with 16-bit storage runs the
+    FP32x2 LES pair code in both)."""
     base, mask = _closed_box(name)
     cfg = dict(base, storage=storage, rounding=rounding, seed=23)
     nz, ny, nx = mask.shape
