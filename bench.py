@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--rounding", default="stochastic", choices=["nearest", "stochastic"],
                    help="rounding of 16-bit stores in the headline run")
     p.add_argument("--size", type=int, default=256, help="edge of the cavity workload (profiling)")
+    p.add_argument("--step-kernel", default="auto", choices=["auto", "register", "staged"],
+                   help="ask the context for one step kernel (comparisons; the default lets the library choose)")
     p.add_argument("--workload", default="sphere", choices=["sphere", "cavity"] + list(EXTENSIONS),
                    help="headline workload (profiling): sphere 256x128x128, cavity 256^3 LES, or the "
                         "sphere box with one extension (curved walls, insulating walls, Brinkman, induced field)")
@@ -302,6 +304,8 @@ def run_ours(args):
     sr = args.storage in ("f16s", "bf16s") and args.rounding == "stochastic"
     if sr:
         cfg = dict(cfg, rounding="stochastic", seed=2024)
+    if args.step_kernel != "auto":
+        cfg = dict(cfg, step_kernel=args.step_kernel)
     sim = lbm.Sim(cfg, mask)
     if phi is not None:
         sim.set_wall_distance(phi)

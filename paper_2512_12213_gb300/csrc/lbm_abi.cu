@@ -626,8 +626,9 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* host_wall_id, void* 
     if (x.cfg.lattice == LBM_D2Q9) x.cfg.periodic[2] = 1;
     x.ext = (cfg->lorentz || cfg->maxwell || cfg->les || cfg->stokes || cfg->darcy > 0.0 || cfg->induced) ? 1 : 0;
     // the FP32x2 LES pair code: 16-bit storage only (LES cavity 256^3 with
-    // binary16 and stochastic rounding 26.4k -> 30.2k MLUPS; with FP32
-    // storage it measured 3% slower than the EXT pair code)
+    // binary16 and stochastic rounding 26.4k -> 30.3k MLUPS, 512^3 27.8k ->
+    // 36.8k); with FP32 storage it measured slower than the EXT pair code
+    // (22.1k register-tiled, 19.7k staged against 25.2k at 256^3)
     x.les_pair = (cfg->les && !cfg->lorentz && !cfg->maxwell && !cfg->stokes && !(cfg->darcy > 0.0) &&
                   !cfg->induced && !cfg->insulating && !cfg->curved &&
                   (cfg->storage == LBM_STORE_F16S || cfg->storage == LBM_STORE_BF16S)) ? 1 : 0;
