@@ -494,7 +494,7 @@ __device__ __forceinline__ void node_relax(R (&d)[Q], const KP<R>& p, const Node
     momentum_coefs<Q, R>(om, Wax, om1j);
     {
         constexpr R w0 = R(WD<Q>(0));
-        d[0] = om1j * d[0] + w0 * base + (mxw ? om * mx_of(0) : R(0));
+        d[0] = (sizeof(R) == 8 ? R(1) - om : om1j) * d[0] + w0 * base + (mxw ? om * mx_of(0) : R(0));
     }
     const R k1 = sto ? R(0) : R(4.5) * om * rho, k2 = R(9) * Crho, kf = R(3) * rho;
 #pragma unroll
@@ -505,14 +505,23 @@ __device__ __forceinline__ void node_relax(R (&d)[Q], const KP<R>& p, const Node
         const R t = R(ex) * m.weq[0] + R(ey) * m.weq[1] + ((D == 3) ? R(ez) * m.weq[2] : R(0));
         const R ea = R(ex) * m.A[0] + R(ey) * m.A[1] + ((D == 3) ? R(ez) * m.A[2] : R(0));
         const R ef = R(ex) * m.wf[0] + R(ey) * m.wf[1] + ((D == 3) ? R(ez) * m.wf[2] : R(0));
-        const R ej = R(ex) * m.j[0] + R(ey) * m.j[1] + ((D == 3) ? R(ez) * m.j[2] : R(0));
+        const R ej = (sizeof(R) == 8) ? R(0) : R(ex) * m.j[0] + R(ey) * m.j[1] + ((D == 3) ? R(ez) * m.j[2] : R(0));
         R ps = w * (base + k1 * t * t + k2 * ef * ea);
         if (mxw) ps += om * mx_of(a);
-        const R pa = w * (kf * ea);
-        const R Wa = Wax * R(WD<Q>(a) / WD<Q>(1));      // a power of two times Wax
         const R da = d[a], db = d[b];
-        d[a] = fma(Wa, ej, fma(om1j, da, ps + pa));
-        d[b] = fma(-Wa, ej, fma(om1j, db, ps - pa));
+        if constexpr (sizeof(R) == 8) {
+            // FP64: the odd part in the paper's form om rho t + C rho E_a.A
+            // (its rounding, 1e-16 relative, is far below any balance, and
+            // the FP64 pipe bounds this path: no E_a.j and one FMA less)
+            const R pa = w * (R(3) * om * rho * t + R(3) * Crho * ea);
+            d[a] = fma(R(1) - om, da, ps + pa);
+            d[b] = fma(R(1) - om, db, ps - pa);
+        } else {
+            const R pa = w * (kf * ea);
+            const R Wa = Wax * R(WD<Q>(a) / WD<Q>(1));      // a power of two times Wax
+            d[a] = fma(Wa, ej, fma(om1j, da, ps + pa));
+            d[b] = fma(-Wa, ej, fma(om1j, db, ps - pa));
+        }
     }
 }
 
