@@ -34,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "D3Q19 MLUPS & % HBM roofline, mixed vs FP64 at stated drag error; adjoint MLUPS"
-WORKLOAD = "D3Q19 sphere r=12 in 256x128x128 periodic box, Re~20, body force, model [e], halfway bounce-back"
+WORKLOAD = ("D3Q19 sphere r=12 in 256x128x128 periodic box, Re 20 configuration (tau 0.68, calibrated body force; steady Re 19.9), started from rest, model [e], halfway bounce-back")
 FALLBACK_HBM = 6800.0
 
 
