@@ -367,6 +367,7 @@ def run_ours(args):
                                "achieved_gbs": roof["achieved"], "frac": roof["frac"]}
         out["storage_variants"] = variants
         out["drag_error_vs_f64"] = drag_errors(torch, lbm, workloads, args.drag_steps)
+        out["momentum_defect"] = momentum_defect(torch, lbm, workloads)
         out["near_steady_vs_f64"] = {f"re{re}": near_steady(torch, lbm, workloads, re) for re in (20, 100)}
         out["steady_state_study"] = steady_record()
         out["cavity_les_f32"] = cavity_bench(torch, lbm, workloads, hbm, args)
@@ -438,6 +439,36 @@ def _sphere_sim(lbm, workloads, key, Re=20):
     if key.endswith("_sr"):
         c = dict(c, rounding="stochastic", seed=2024)
     return c, m, lbm.Sim(c, m)
+
+
+def momentum_defect(torch, lbm, workloads, keys=("f32", "f16s_sr", "bf16s_sr"), warm=1000, steps=2000):
+    """The per-step momentum balance of the step in each FP32-compute storage
+    on the sphere box (Re 20 configuration) from a uniform stream at
+    U = 0.05: after `warm` steps, over `steps` more, the defect
+    (M(T) - M(0) + sum_t F_wall(t)) / (T sum rho a) - 1, which every force
+    model makes exactly zero in exact arithmetic (the discrete form of
+    Eq. 32).  The wall force is summed on the device step by step."""
+    out = {"workload": "sphere 256x128x128, Re 20 configuration, from a uniform stream at U = 0.05",
+           "warm_steps": warm, "steps": steps}
+    for key in keys:
+        c, m, s = _sphere_sim(lbm, workloads, key)
+        nz, ny, nx = m.shape
+        u = np.zeros((3, nz, ny, nx))
+        u[0] = 0.05 * (m == 0)
+        s.init_equilibrium(np.ones((nz, ny, nx)), u)
+        s.step(warm)
+        _, M0, ra = s.balance()
+        st = s.stream
+        F = torch.zeros(3, dtype=torch.float64, device=s.device)
+        for _ in range(steps):
+            lbm.lbm_step(s.ctx, 1, st)
+            lbm.lbm_wall_force(s.ctx, 1, lbm.ACCUMULATE, 1.0, F, 0, st)
+        _, M1, _ = s.balance()
+        out[key] = float((M1[0] - M0[0] + F[0].item()) / (steps * ra[0]) - 1)
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    return out
 
 
 def drag_errors(torch, lbm, workloads, steps, checkpoints=(1000, 5000, 20000), radius=12):
