@@ -8,7 +8,10 @@ mathematics fix (no GPU).
 * the total momentum increment dt rho a of every model (Sec. 2);
 * the implicit flow velocity v = u + dt a/2 under the Lorentz force;
 * the artefact term E_ij (Eq. 9) against its closed forms per model;
-* the Smagorinsky relaxation time against the eddy-viscosity relation.
+* the Smagorinsky relaxation time against the eddy-viscosity relation;
+* the odd part of the collision written from the momentum j, the form the
+  FP32 node codes evaluate, for every model, with the Lorentz force, LES and
+  the Maxwell term.
 """
 import itertools
 
@@ -250,3 +253,40 @@ def test_smagorinsky_relation(orc, q):
         lhs = dt * c * c * (te - cfg.tau) / 3
         assert te > cfg.tau
         assert np.isclose(lhs, (cfg.cs * cfg.dx) ** 2 * Smag, rtol=1e-12)
+
+
+@pytest.mark.parametrize("q,model,extra", list(itertools.product(
+    [9, 19], "abcde", ["plain", "lorentz", "les", "maxwell"])))
+def test_odd_part_from_the_momentum(orc, q, model, extra):
+    """The odd part of the collision, per opposite pair (a, opp a),
+    (f'_a - f'_opp)/2 = (1 - om)(f_a - f_opp)/2 + 3 w_a (om E_a.j + rho dt E_a.a / c)
+    with j = sum_b E_b f_b: for every model of Sec. 2, om rho E_a.u^eq / c +
+    C rho dt E_a.a / c equals om E_a.j + rho dt E_a.a / c (u^eq = u + dt a/2
+    with C = 1 - om/2 for [e], u^eq = u with C = 1 for [a]-[d]).  The GPU's
+    FP32 node codes evaluate the odd part in this form; here the oracle's
+    collision (Eqs. 1-3 as the paper writes them) is checked against it, with
+    the Lorentz force (a from the implicit v), Smagorinsky LES (the node's own
+    relaxation time) and the Maxwell term (even, so absent from the odd part)."""
+    kw = {}
+    if extra == "lorentz":
+        kw = dict(lorentz=1, B=(0.02, 0.05, 0.03 if q == 19 else 0.0), sigma_e=0.7, E=(1e-3, 0.0, 2e-3))
+    elif extra == "les":
+        kw = dict(les=1, cs=0.2)
+    elif extra == "maxwell":
+        kw = dict(maxwell=1, B=(0.03, -0.02, 0.04 if q == 19 else 0.0), mu=1.3)
+    cfg = _random_cfg(orc, q, model, **kw)
+    c = cfg.dx / cfg.dt
+    e, w, opp = orc.lattice(q)
+    E = e.astype(float)
+    for _ in range(4):
+        f = _random_f(orc, cfg)
+        nm = orc.node_macro(cfg, f)
+        om = 1.0 / nm["tau"]
+        fr = orc.collide_node(cfg, f)
+        j = E.T @ f
+        rho = f.sum()
+        for a in range(1, q):
+            b = opp[a]
+            got = 0.5 * (fr[a] - fr[b])
+            want = (1 - om) * 0.5 * (f[a] - f[b]) + 3 * w[a] * (om * (E[a] @ j) + rho * cfg.dt * (E[a] @ nm["a"]) / c)
+            assert np.isclose(got, want, rtol=0, atol=1e-14 * max(abs(f).max(), 1.0)), (a, got, want)
