@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--repeats", type=int, default=5, help="timed blocks of --steps steps; the median is reported")
     p.add_argument("--study", default=None, choices=["steady"],
                    help="instead of the benchmark: run the sphere to steady state in every storage (long)")
+    p.add_argument("--study-out", default=None,
+                   help="also write the study's JSON line to this file (profiles/steady_sphere.json keeps the record)")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--drag-steps", type=int, default=2000)
     p.add_argument("--no-extras", action="store_true", help="headline only")
@@ -988,9 +990,10 @@ def run_study(args):
     res["command"] = "python bench.py --study steady"
     line = json.dumps(res, default=float)
     print(line, flush=True)
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    with open(os.path.join(ROOT, "gpurun_out", "steady_sphere.json"), "w") as fh:
-        fh.write(line + "\n")
+    if args.study_out:
+        os.makedirs(os.path.dirname(os.path.abspath(args.study_out)), exist_ok=True)
+        with open(args.study_out, "w") as fh:
+            fh.write(line + "\n")
 
 
 # --------------------------------------------------------- reference arm
